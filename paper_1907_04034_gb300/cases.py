@@ -1,0 +1,300 @@
+"""Seeded synthetic problem generators (particle lattices, rings, initial fields).
+
+This module is the only code shared by the CUDA path and the CPU oracle. It holds
+no arithmetic of the SPH method itself: it places particles, draws the seeded
+jitter, fills the initial velocity/pressure fields the workload prescribes, and
+collects the run parameters. Both sides receive its output as plain arrays.
+
+Workloads (all 2D, rho0 = 1, U = 1, c_s = 10 U, h = 1.2 dx, support 3h):
+
+* ``channel``   -- the pulse channel: [0,1]x[0,0.5], periodic in y, dx = 0.02,
+  3 inlet layers at x<0, 5 hybrid-outlet layers at x>1, nu = 0.01, Gaussian
+  pressure pulse p = 0.1 exp(-((x-0.5)^2+(y-0.25)^2)/0.005), fluid jitter of
+  +-0.01 dx (uniform, seeded).
+* ``cylinder``  -- flow past a circular cylinder D = 1 centred 5D behind the
+  inlet of a 15D x 10D channel, slip walls top and bottom (4 layers), 3 solid
+  rings in the cylinder (the paper's ring fill, Sec. 4.6), uniform inlet U = 1,
+  hybrid outlet; dx = D/40 (~245k particles), D/100 (~1.5M), D/25 (~95k).
+* ``taylor_green`` -- doubly periodic unit box (used to pin the scheme).
+* ``poiseuille``   -- x-periodic channel between no-slip walls, body force g.
+* ``random_box``   -- small seeded boxes with random tags (property tests).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, Optional
+
+import numpy as np
+
+FLUID, INLET, OUTLET, WALL, SLIPWALL = 0, 1, 2, 3, 4
+TAG_NAMES = {FLUID: "fluid", INLET: "inlet", OUTLET: "outlet", WALL: "wall", SLIPWALL: "slipwall"}
+
+
+@dataclasses.dataclass
+class Params:
+    """Run parameters (SI units, all floating point fp64)."""
+    x_min: float
+    x_max: float
+    y_min: float
+    y_max: float
+    periodic_x: int = 0
+    periodic_y: int = 0
+    dx: float = 0.02
+    hdx: float = 1.2
+    rho0: float = 1.0
+    U: float = 1.0
+    nu: float = 0.01
+    cs: float = 10.0
+    alpha: float = 0.5
+    pb: float = 100.0          # background pressure; rho0 * cs^2 by default
+    eta_reg: float = 0.01
+    gx: float = 0.0
+    gy: float = 0.0
+    dt: float = 0.0
+    use_pavg: int = 1
+    # inlet
+    has_inlet: int = 0
+    x_in: float = 0.0
+    n_in_layers: int = 3
+    inlet_modes: tuple = ()    # a_k of u(y) = U + sum a_k sin(k pi (y - inlet_y0) / inlet_h)
+    inlet_y0: float = 0.0
+    inlet_h: float = 1.0
+    # outlet (hybrid)
+    has_outlet: int = 0
+    x_out: float = 1.0
+    n_out_layers: int = 5
+    n_avg: int = 6
+    i_thresh: float = -1.0     # < 0: use the acoustic-intensity formula
+    # walls: per wall tag (WALL, SLIPWALL): slip flag, wall velocity, counted in drag
+    wall_slip: tuple = (0, 1)
+    wall_u: tuple = (0.0, 0.0)
+    wall_v: tuple = (0.0, 0.0)
+    wall_drag: tuple = (1, 0)
+    drag_length: float = 1.0   # reference length D of c_d = F / (0.5 rho U^2 D)
+
+    @property
+    def h(self) -> float:
+        return self.hdx * self.dx
+
+
+@dataclasses.dataclass
+class Case:
+    name: str
+    params: Params
+    x: np.ndarray
+    y: np.ndarray
+    u: np.ndarray
+    v: np.ndarray
+    p: np.ndarray
+    m: np.ndarray
+    tag: np.ndarray
+    id: np.ndarray
+    capacity: int
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+    def arrays(self) -> Dict[str, np.ndarray]:
+        return dict(x=self.x, y=self.y, u=self.u, v=self.v, p=self.p, m=self.m,
+                    tag=self.tag, id=self.id)
+
+    def count(self, tag: int) -> int:
+        return int(np.count_nonzero(self.tag == tag))
+
+
+def default_dt(dx: float, hdx: float, cs: float, U: float, nu: float) -> float:
+    """Time step recipe of the channel workload: min(0.25 h/(c+U), 0.125 h^2/nu)."""
+    h = hdx * dx
+    return min(0.25 * h / (cs + U), 0.125 * h * h / nu)
+
+
+def _lattice(x0: float, nx: int, y0: float, ny: int, dx: float):
+    """Cell-centred square lattice: x0 + (i+1/2) dx, y0 + (j+1/2) dx."""
+    xs = x0 + (np.arange(nx, dtype=np.float64) + 0.5) * dx
+    ys = y0 + (np.arange(ny, dtype=np.float64) + 0.5) * dx
+    X, Y = np.meshgrid(xs, ys, indexing="ij")
+    return X.ravel().copy(), Y.ravel().copy()
+
+
+def _assemble(name, params, parts, capacity_extra, seed_ids=0):
+    x = np.concatenate([q[0] for q in parts])
+    y = np.concatenate([q[1] for q in parts])
+    tag = np.concatenate([np.full(q[0].shape, q[2], dtype=np.uint8) for q in parts])
+    n = x.shape[0]
+    u = np.zeros(n)
+    v = np.zeros(n)
+    p = np.zeros(n)
+    m = np.full(n, params.rho0 * params.dx * params.dx)
+    ids = np.arange(seed_ids, seed_ids + n, dtype=np.uint64)
+    return Case(name, params, x, y, u, v, p, m, tag, ids, n + capacity_extra)
+
+
+def channel(dx: float = 0.02, nu: float = 0.01, seed: int = 0, jitter: float = 0.01,
+            pulse_amp: float = 0.1, pulse_xy=(0.5, 0.25), pulse_w: float = 0.005,
+            n_in: int = 3, n_out: int = 5, L: float = 1.0, H: float = 0.5,
+            U: float = 1.0) -> Case:
+    """The 2D pulse channel (periodic in y) with inlet at x=0 and hybrid outlet at x=L."""
+    cs = 10.0 * U
+    hdx = 1.2
+    rc = 3.0 * hdx * dx
+    nx, ny = int(round(L / dx)), int(round(H / dx))
+    params = Params(x_min=-n_in * dx - rc, x_max=L + n_out * dx + rc, y_min=0.0, y_max=H,
+                    periodic_y=1, dx=dx, hdx=hdx, rho0=1.0, U=U, nu=nu, cs=cs,
+                    pb=1.0 * cs * cs, dt=default_dt(dx, hdx, cs, U, nu),
+                    has_inlet=1, x_in=0.0, n_in_layers=n_in, inlet_y0=0.0, inlet_h=H,
+                    has_outlet=1, x_out=L, n_out_layers=n_out)
+    fx, fy = _lattice(0.0, nx, 0.0, ny, dx)
+    ix, iy = _lattice(-n_in * dx, n_in, 0.0, ny, dx)
+    ox, oy = _lattice(L, n_out, 0.0, ny, dx)
+    rng = np.random.default_rng(seed)
+    fx = fx + rng.uniform(-jitter * dx, jitter * dx, fx.shape)
+    fy = fy + rng.uniform(-jitter * dx, jitter * dx, fy.shape)
+    # the jitter may push a bottom-row particle below y=0: wrap into the periodic box
+    fy = np.where(fy < 0.0, fy + H, np.where(fy >= H, fy - H, fy))
+    c = _assemble("channel", params, [(fx, fy, FLUID), (ix, iy, INLET), (ox, oy, OUTLET)],
+                  capacity_extra=4 * ny + 64)
+    c.u[:] = U
+    c.p[:] = pulse_amp * np.exp(-((c.x - pulse_xy[0]) ** 2 + (c.y - pulse_xy[1]) ** 2) / pulse_w)
+    return c
+
+
+def cylinder(dx: float = 1.0 / 40.0, D: float = 1.0, Re: float = 200.0, Lx: float = 15.0,
+             H: float = 10.0, xc: float = 5.0, n_solid: int = 3, n_in: int = 3, n_out: int = 5,
+             n_wall: int = 4, U: float = 1.0, inlet_modes=()) -> Case:
+    """Flow past a cylinder: 15D x 10D channel, slip walls, hybrid outlet (Sec. 4.6)."""
+    cs = 10.0 * U
+    hdx = 1.2
+    rc = 3.0 * hdx * dx
+    nu = U * D / Re
+    R = 0.5 * D
+    yc = 0.5 * H
+    nx, ny = int(round(Lx / dx)), int(round(H / dx))
+    params = Params(x_min=-n_in * dx - rc, x_max=Lx + n_out * dx + rc,
+                    y_min=-n_wall * dx - rc, y_max=H + n_wall * dx + rc,
+                    periodic_y=0, dx=dx, hdx=hdx, rho0=1.0, U=U, nu=nu, cs=cs,
+                    pb=1.0 * cs * cs, dt=default_dt(dx, hdx, cs, U, nu),
+                    has_inlet=1, x_in=0.0, n_in_layers=n_in, inlet_y0=0.0, inlet_h=H,
+                    has_outlet=1, x_out=Lx, n_out_layers=n_out,
+                    inlet_modes=tuple(inlet_modes), drag_length=D)
+    fx, fy = _lattice(0.0, nx, 0.0, ny, dx)
+    keep = (fx - xc) ** 2 + (fy - yc) ** 2 >= (R + 0.5 * dx) ** 2
+    fx, fy = fx[keep], fy[keep]
+    ix, iy = _lattice(-n_in * dx, n_in, 0.0, ny, dx)
+    ox, oy = _lattice(Lx, n_out, 0.0, ny, dx)
+    # slip walls below and above, spanning inlet + fluid + outlet
+    nxw = n_in + nx + n_out
+    bx, by = _lattice(-n_in * dx, nxw, -n_wall * dx, n_wall, dx)
+    tx, ty = _lattice(-n_in * dx, nxw, H, n_wall, dx)
+    # solid rings: first on the circumference, then dx further in each time
+    sx, sy = [], []
+    for k in range(n_solid):
+        r = R - k * dx
+        if r <= 0.0:
+            break
+        npt = max(1, int(round(2.0 * math.pi * r / dx)))
+        th = 2.0 * math.pi * np.arange(npt) / npt
+        sx.append(xc + r * np.cos(th))
+        sy.append(yc + r * np.sin(th))
+    sx = np.concatenate(sx)
+    sy = np.concatenate(sy)
+    c = _assemble("cylinder", params,
+                  [(fx, fy, FLUID), (ix, iy, INLET), (ox, oy, OUTLET),
+                   (np.concatenate([bx, tx]), np.concatenate([by, ty]), SLIPWALL),
+                   (sx, sy, WALL)],
+                  capacity_extra=4 * ny + 1024)
+    c.u[:] = np.where((c.tag == WALL) | (c.tag == SLIPWALL), 0.0, U)
+    if inlet_modes:
+        sel = c.tag == INLET
+        c.u[sel] = inlet_profile(c.y[sel], U, inlet_modes, 0.0, H)
+    return c
+
+
+def inlet_profile(y, U, modes, y0, H):
+    """u(y) = U + sum_k a_k sin(k pi (y - y0)/H): the inlet-profile family of the workload."""
+    out = np.full(np.shape(y), U, dtype=np.float64)
+    for k, a in enumerate(modes, start=1):
+        out = out + a * np.sin(k * math.pi * (np.asarray(y) - y0) / H)
+    return out
+
+
+def taylor_green(n: int = 20, nu: float = 0.01, U: float = 1.0, L: float = 1.0,
+                 jitter: float = 0.0, seed: int = 0) -> Case:
+    """Doubly periodic box with the Taylor-Green vortex u=-U cos(2pi x) sin(2pi y), ..."""
+    dx = L / n
+    cs = 10.0 * U
+    params = Params(x_min=0.0, x_max=L, y_min=0.0, y_max=L, periodic_x=1, periodic_y=1,
+                    dx=dx, hdx=1.2, rho0=1.0, U=U, nu=nu, cs=cs, pb=cs * cs,
+                    dt=default_dt(dx, 1.2, cs, U, nu))
+    x, y = _lattice(0.0, n, 0.0, n, dx)
+    if jitter > 0:
+        rng = np.random.default_rng(seed)
+        x = np.mod(x + rng.uniform(-jitter * dx, jitter * dx, x.shape), L)
+        y = np.mod(y + rng.uniform(-jitter * dx, jitter * dx, y.shape), L)
+    c = _assemble("taylor_green", params, [(x, y, FLUID)], capacity_extra=0)
+    k = 2.0 * math.pi / L
+    c.u[:] = -U * np.cos(k * c.x) * np.sin(k * c.y)
+    c.v[:] = U * np.sin(k * c.x) * np.cos(k * c.y)
+    c.p[:] = -0.25 * U * U * (np.cos(2 * k * c.x) + np.cos(2 * k * c.y))
+    return c
+
+
+def poiseuille(n: int = 10, nu: float = 0.1, umax: float = 1.0, Lx: float = 0.5,
+               n_wall: int = 4) -> Case:
+    """x-periodic channel of width 1 between no-slip walls driven by g = 8 nu umax / W^2."""
+    W = 1.0
+    dx = W / n
+    cs = 10.0 * umax
+    g = 8.0 * nu * umax / (W * W)
+    nx = int(round(Lx / dx))
+    rc = 3.6 * dx
+    params = Params(x_min=0.0, x_max=Lx, y_min=-n_wall * dx - rc, y_max=W + n_wall * dx + rc,
+                    periodic_x=1, dx=dx, hdx=1.2, rho0=1.0, U=umax, nu=nu, cs=cs,
+                    pb=cs * cs, gx=g, dt=default_dt(dx, 1.2, cs, umax, nu),
+                    wall_slip=(0, 1), wall_drag=(0, 0))
+    fx, fy = _lattice(0.0, nx, 0.0, n, dx)
+    bx, by = _lattice(0.0, nx, -n_wall * dx, n_wall, dx)
+    tx, ty = _lattice(0.0, nx, W, n_wall, dx)
+    return _assemble("poiseuille", params,
+                     [(fx, fy, FLUID), (np.concatenate([bx, tx]), np.concatenate([by, ty]), WALL)],
+                     capacity_extra=0)
+
+
+def random_box(n: int = 300, seed: int = 0, periodic_y: int = 1, dx: float = 0.05,
+               tags=(FLUID, INLET, OUTLET, WALL, SLIPWALL), L: float = 1.0, H: float = 0.6) -> Case:
+    """Seeded random particles in [0,L]x[0,H] with random tags and fields (property tests).
+
+    Inlet/outlet particles are placed left of x_in = 0.2 / right of x_out = 0.8 so
+    that the zone semantics hold; walls and fluid are placed anywhere in between.
+    """
+    rng = np.random.default_rng(seed)
+    cs = 10.0
+    params = Params(x_min=-0.2, x_max=L + 0.2, y_min=0.0, y_max=H, periodic_y=periodic_y,
+                    dx=dx, hdx=1.2, rho0=1.0, U=1.0, nu=0.01, cs=cs, pb=cs * cs,
+                    dt=default_dt(dx, 1.2, cs, 1.0, 0.01),
+                    has_inlet=int(INLET in tags), x_in=0.2, n_in_layers=3, inlet_y0=0.0, inlet_h=H,
+                    has_outlet=int(OUTLET in tags), x_out=0.8, n_out_layers=3)
+    tag = rng.choice(np.array(tags, dtype=np.uint8), size=n)
+    x = rng.uniform(0.0, L, n)
+    x = np.where(tag == INLET, rng.uniform(0.2 - 3 * dx, 0.2, n), x)
+    x = np.where(tag == OUTLET, rng.uniform(0.8, 0.8 + 3 * dx, n), x)
+    x = np.where(tag == FLUID, rng.uniform(0.2, 0.8, n), x)
+    y = rng.uniform(0.0, H, n)
+    c = Case("random_box", params, x, y, rng.normal(1.0, 0.1, n), rng.normal(0.0, 0.1, n),
+             rng.normal(0.0, 0.2, n), rng.uniform(0.8, 1.2, n) * dx * dx, tag,
+             np.arange(n, dtype=np.uint64), capacity=2 * n + 64)
+    return c
+
+
+def by_name(name: str, **kw) -> Case:
+    """Named workloads: channel, cyl40 (dx=D/40), cyl100 (D/100), cyl25 (D/25)."""
+    if name == "channel":
+        return channel(**kw)
+    if name == "cyl40":
+        return cylinder(dx=1.0 / 40.0, **kw)
+    if name == "cyl100":
+        return cylinder(dx=1.0 / 100.0, **kw)
+    if name == "cyl25":
+        return cylinder(dx=1.0 / 25.0, **kw)
+    raise ValueError(f"unknown workload {name!r}")
