@@ -1,0 +1,206 @@
+/*
+ * edac.h -- C ABI of the GB300 (sm_103a) EDAC weakly-compressible SPH library
+ * with an inlet and the hybrid non-reflecting outlet of Negi, Ramachandran &
+ * Haftu, arXiv 1907.04034.
+ *
+ * One context = one 2D particle system on one GPU.  A time step is the paper's
+ * per-step particle pass: cell-list neighbour search, summation density
+ * (Eq. summation-density) with the quintic spline (Eq. quintic-spline), solid
+ * wall projection (Sec. 2), mirrored inlet pressure (Sec. 3.2, Eqs. matform and
+ * taylor2), the EDAC-TVF momentum and pressure rates (Eqs. tvf-momentum, pavg,
+ * tvf-p-ij-basa, p-edac, transport-vel), a midpoint predictor-corrector
+ * integrator, the hybrid outlet (Sec. 3.4, Eqs. timeevg, acouinten, acou with the
+ * characteristic variables of Eq. characteristic-vars), particle recycling (end
+ * of Sec. 3.4) and the solid force (Eq. tvf-momentum_solid).
+ *
+ * Conventions
+ *   - Every function returns an edac_status; nothing throws across the ABI.
+ *   - Host pointers ("h_") are caller-owned and only read or written during the
+ *     call; device pointers ("d_") are caller-owned device memory.
+ *   - The library never allocates device memory: the caller supplies one
+ *     device workspace of edac_workspace_bytes() bytes (256-byte aligned) that
+ *     the context owns the layout of until edac_destroy().
+ *   - All GPU work is issued on params.cuda_stream (a cudaStream_t; NULL means
+ *     the legacy default stream, which disables CUDA-graph replay).
+ *   - Device-side faults (capacity overflow, non-finite values, particles that
+ *     left the domain box, event-list overflow) set a sticky device error word.
+ *     It is read at every edac_get_* / edac_read_* call; once set, the call
+ *     returns the matching code and edac_step() returns EDAC_E_STATE until the
+ *     context is re-initialised with edac_set_particles().
+ *   - Not thread-safe per context; distinct contexts are independent.
+ */
+#ifndef EDAC_H
+#define EDAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct edac_ctx edac_ctx;
+
+typedef enum {
+    EDAC_OK = 0,
+    EDAC_E_INVALID = 1,   /* bad argument or parameter (host-side check)        */
+    EDAC_E_CAPACITY = 2,  /* particle capacity or an event list exceeded       */
+    EDAC_E_CUDA = 3,      /* a CUDA runtime call failed; see edac_last_error() */
+    EDAC_E_NONFINITE = 4, /* a NaN/Inf appeared in the integrated fields       */
+    EDAC_E_TIMEOUT = 5,   /* a bounded device wait gave up                     */
+    EDAC_E_STATE = 6,     /* call out of order, or the context is in error     */
+    EDAC_E_DOMAIN = 7     /* a particle left the domain box of the cell grid   */
+} edac_status;
+
+/* arithmetic of the pair sums */
+enum { EDAC_FP64 = 0, EDAC_MIXED = 1 };
+
+/* particle tags (uint8) */
+enum { EDAC_FLUID = 0, EDAC_INLET = 1, EDAC_OUTLET = 2, EDAC_WALL = 3, EDAC_SLIPWALL = 4 };
+
+/* field ids for edac_read_state() (all returned as fp64) */
+enum {
+    EDAC_F_X = 0, EDAC_F_Y, EDAC_F_U, EDAC_F_V, EDAC_F_UT, EDAC_F_VT, EDAC_F_P, EDAC_F_M,
+    EDAC_F_RHO, EDAC_F_VOL, EDAC_F_AU, EDAC_F_AV, EDAC_F_AP, EDAC_F_ABU, EDAC_F_ABV,
+    EDAC_F_FX, EDAC_F_FY, EDAC_F_NNB, EDAC_F_UBAR, EDAC_F_VBAR, EDAC_F_PBAR, EDAC_F_J2,
+    EDAC_F_J2P, EDAC_F_ADVP, EDAC_F_REDP, EDAC_F_RPOS, EDAC_NUM_FIELDS
+};
+
+/* kernels that edac_profile() can time with CUDA events */
+enum { EDAC_K_PASS_A = 0, EDAC_K_PASS_B = 1, EDAC_K_REBUILD = 2, EDAC_K_BOUNDARY = 3,
+       EDAC_K_STAGE = 4, EDAC_K_RECYCLE = 5, EDAC_NUM_KERNELS = 6 };
+
+/*
+ * Run parameters, SI units.  h = hdx * dx, support radius r_c = 3h.
+ * The cell grid covers the box [x_min, x_max) x [y_min, y_max) with cells of
+ * at least r_c; a periodic axis needs at least 3 cells.  Particles must stay
+ * inside the box (EDAC_E_DOMAIN otherwise).
+ */
+typedef struct {
+    double x_min, x_max, y_min, y_max;
+    int periodic_x, periodic_y;
+    double dx;       /* initial particle spacing                                  */
+    double hdx;      /* h / dx (1.2 in the paper)                                 */
+    double rho0;     /* reference density                                          */
+    double U;        /* inlet / reference speed                                    */
+    double nu;       /* kinematic viscosity                                        */
+    double cs;       /* artificial speed of sound c_s (10 u_max, Sec. 2)           */
+    double alpha;    /* EDAC damping coefficient of Eq. edac-nu (0.5)             */
+    double pb;       /* background pressure of Eq. transport-vel                   */
+    double eta_reg;  /* regulariser eta of Eqs. tvf-momentum / p-edac (0.01)       */
+    double gx, gy;   /* body force                                                  */
+    double dt;       /* time step (> 0)                                             */
+    int use_pavg;    /* 1: subtract p_avg (Eq. pavg); 0: plain p_ij average        */
+    int precision;   /* EDAC_FP64 or EDAC_MIXED                                     */
+    int capacity;    /* maximum live particles, recycling headroom included         */
+    int max_history; /* per-step history records kept on the device (ring)          */
+    int use_graphs;  /* 1: capture one step in a CUDA graph and replay it          */
+    void *cuda_stream;
+} edac_params;
+
+/* Bytes of device workspace a context with these parameters needs. */
+edac_status edac_workspace_bytes(const edac_params *params, size_t *bytes);
+
+/* Create a context on the current CUDA device.  d_workspace: caller-owned
+ * device memory of at least edac_workspace_bytes() bytes, 256-byte aligned,
+ * kept alive until edac_destroy().  No GPU work is issued. */
+edac_status edac_create(const edac_params *params, void *d_workspace, size_t bytes,
+                        edac_ctx **out);
+
+/* Inlet zone (Sec. 3): inlet particles sit in [x_in - n_layers dx, x_in) and move
+ * with u(y) = U + sum_{k=1..n_modes} a_k sin(k pi (y - y0) / H), v = 0; their
+ * pressure is mirrored from the fluid (Sec. 3.2).  n_modes <= 16.  Call before
+ * edac_set_particles(). */
+edac_status edac_set_inlet(edac_ctx *ctx, double x_in, int n_layers, int n_modes,
+                           const double *h_modes, double y0, double H);
+
+/* Outlet zone (Sec. 3.4): outlet particles sit in [x_out, x_out + n_layers dx);
+ * kind must be 0 (hybrid).  n_avg: length of the time average (Eq. timeevg; 6 in
+ * the paper, at most 8).  i_thresh < 0 selects I = (rho0 U^2/2)^2/(2 rho0 c_s)
+ * of Eq. acouinten.  Call before edac_set_particles(). */
+edac_status edac_set_outlet(edac_ctx *ctx, double x_out, int n_layers, int kind, int n_avg,
+                            double i_thresh);
+
+/* Solid-wall behaviour of tag EDAC_WALL or EDAC_SLIPWALL (Sec. 2 cites Adami et
+ * al. 2012): slip = 0 gives the ghost velocity 2 u_wall - <u_fluid>, slip = 1
+ * (normal along y) gives (<u>, -<v>); count_in_drag = 1 adds the particles'
+ * force (Eq. tvf-momentum_solid) to the drag/lift history.  Defaults: WALL
+ * no-slip counted in drag, SLIPWALL slip not counted. */
+edac_status edac_set_wall(edac_ctx *ctx, int tag, int slip, double uw, double vw,
+                          int count_in_drag);
+
+/* Upload n particles from host arrays (copied) and evaluate the rates at t = 0.
+ * ids must be unique; tags in [0, 4]; all particles inside the domain box;
+ * n <= capacity.  n = 0 is allowed (an empty system).  Resets the step counter,
+ * the history and the error word. */
+edac_status edac_set_particles(edac_ctx *ctx, int n, const double *h_x, const double *h_y,
+                               const double *h_u, const double *h_v, const double *h_p,
+                               const double *h_m, const uint8_t *h_tag, const uint64_t *h_id);
+
+/* Advance nsteps time steps.  Asynchronous on the context's stream: no host
+ * synchronisation; the live-particle count stays on the device. */
+edac_status edac_step(edac_ctx *ctx, int nsteps);
+
+/* Re-evaluate the rates (density, volume, accelerations, pressure rate, wall
+ * forces) at the current state without advancing time (asynchronous). */
+edac_status edac_evaluate(edac_ctx *ctx);
+
+/* Synchronise and return the live-particle count. */
+edac_status edac_get_count(edac_ctx *ctx, int *n_active);
+
+/* Synchronise and copy the live particles to host arrays in ascending id order:
+ * h_id and h_tag (either may be NULL) and nfields fields (ids in field_ids,
+ * EDAC_F_*) into h_out[f][0..n).  cap: length of every output array. */
+edac_status edac_read_state(edac_ctx *ctx, int cap, uint64_t *h_id, uint8_t *h_tag,
+                            int nfields, const int *field_ids, double *const *h_out, int *n);
+
+/* Synchronise and copy the per-step history (most recent min(steps, max_steps,
+ * max_history) records, oldest first): force on the drag walls (fx, fy), mass
+ * flux into the outlet (mass of fluid->outlet conversions / dt), live count,
+ * and the numbers of spawned, deleted and fluid->outlet particles.  Any output
+ * pointer may be NULL. */
+edac_status edac_read_history(edac_ctx *ctx, int max_steps, double *h_fx, double *h_fy,
+                              double *h_mass_flux, int *h_n_active, int *h_n_spawn,
+                              int *h_n_delete, int *h_n_to_outlet, int *nsteps);
+
+/* Debug: bytes of caller-owned device scratch that edac_read_neighbors() needs at
+ * the current positions (rebuilds the cell list and re-counts neighbours;
+ * synchronises; does not change the trajectory). */
+edac_status edac_neighbor_scratch_bytes(edac_ctx *ctx, size_t *bytes);
+
+/* Debug: neighbour lists at the current positions, built with the same
+ * membership test the pair kernels use.  d_scratch: caller-owned device memory of
+ * at least edac_neighbor_scratch_bytes() bytes.  Writes, in ascending id order of
+ * i, h_start[0..n] (CSR offsets) and h_nbr_ids[start[i]..start[i+1]) (neighbour
+ * ids of i, ascending, i itself included).  cap_n >= n, cap_ids >= total.
+ * Synchronises. */
+edac_status edac_read_neighbors(edac_ctx *ctx, void *d_scratch, size_t scratch_bytes, int cap_n,
+                                int64_t *h_start, int64_t cap_ids, uint64_t *h_nbr_ids, int *n,
+                                int64_t *total);
+
+/* Timing: enable (1) or disable (0) CUDA-event timing of one kernel group
+ * (EDAC_K_*).  While any group is enabled, edac_step() launches eagerly
+ * (no graph) and brackets each launch of the enabled groups with events. */
+edac_status edac_profile(edac_ctx *ctx, int kernel, int enable);
+
+/* Synchronise and return the summed device time (ms) and launch count of a
+ * timed kernel group since the last reset; reset = 1 clears them. */
+edac_status edac_read_profile(edac_ctx *ctx, int kernel, double *ms, int64_t *launches,
+                              int reset);
+
+/* Number of kernel launches (and memset nodes) issued by this context so far,
+ * graph replays included. */
+edac_status edac_launch_count(edac_ctx *ctx, int64_t *count);
+
+/* Text of the last error of this context (valid until the next call). */
+const char *edac_last_error(edac_ctx *ctx);
+
+/* Release the context (host memory, events, graphs).  The workspace stays the
+ * caller's.  Synchronises the stream first. */
+void edac_destroy(edac_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EDAC_H */

@@ -1,0 +1,316 @@
+"""ctypes binding of the C-ABI library ``libedac.so`` (declared in ``include/edac.h``).
+
+Argument marshalling only: every step of the particle pass runs in the library's
+CUDA kernels.  PyTorch provides the device workspace (``torch.empty`` on the CUDA
+device, handed to the library as a raw pointer) and the CUDA stream.  There is no
+CPU fallback: ``load()`` raises when the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+from typing import Dict, Iterable, Optional
+
+import numpy as np
+
+from . import cases as _cases
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+LIBDIR = os.path.join(HERE, "_lib")
+LIB = os.path.join(LIBDIR, "libedac.so")
+SOURCES = ("edac_capi.cu", "edac_cells.cu", "edac_pairs.cu")
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+
+EDAC_FP64, EDAC_MIXED = 0, 1
+STATUS = {0: "EDAC_OK", 1: "EDAC_E_INVALID", 2: "EDAC_E_CAPACITY", 3: "EDAC_E_CUDA",
+          4: "EDAC_E_NONFINITE", 5: "EDAC_E_TIMEOUT", 6: "EDAC_E_STATE", 7: "EDAC_E_DOMAIN"}
+FIELDS = ("x", "y", "u", "v", "ut", "vt", "p", "m", "rho", "vol", "au", "av", "ap", "abu", "abv",
+          "fx", "fy", "nnb", "ubar", "vbar", "pbar", "J2", "J2p", "advp", "redp", "rpos")
+FIELD_ID = {k: i for i, k in enumerate(FIELDS)}
+KERNELS = {"pass_a": 0, "pass_b": 1, "rebuild": 2, "boundary": 3, "stage": 4, "recycle": 5}
+
+# every symbol the header declares
+EXPORTS = ("edac_workspace_bytes", "edac_create", "edac_set_inlet", "edac_set_outlet",
+           "edac_set_wall", "edac_set_particles", "edac_step", "edac_evaluate", "edac_get_count",
+           "edac_read_state", "edac_read_history", "edac_neighbor_scratch_bytes",
+           "edac_read_neighbors", "edac_profile", "edac_read_profile", "edac_launch_count",
+           "edac_last_error", "edac_destroy")
+
+
+class EdacError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _nvcc():
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.sep not in c or os.path.exists(c)):
+            return c
+    return "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libedac.so for sm_103a (the translation units in parallel)."""
+    os.makedirs(LIBDIR, exist_ok=True)
+    deps = [os.path.join(CSRC, s) for s in SOURCES] + [
+        os.path.join(CSRC, "edac_internal.cuh"), os.path.join(INCLUDE, "edac.h")]
+    if not force and os.path.exists(LIB):
+        t = os.path.getmtime(LIB)
+        if all(os.path.getmtime(p) <= t for p in deps):
+            return LIB
+    nvcc = _nvcc()
+    flags = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
+             "-I" + CSRC]
+    objs = []
+
+    def comp(src):
+        obj = os.path.join(LIBDIR, os.path.splitext(src)[0] + ".o")
+        cmd = [nvcc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
+        if verbose and r.stderr:
+            print(r.stderr)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        objs = list(ex.map(comp, SOURCES))
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = [nvcc, ARCH, "-shared", "-o", tmp] + objs
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("x_min", C.c_double), ("x_max", C.c_double), ("y_min", C.c_double), ("y_max", C.c_double),
+        ("periodic_x", C.c_int), ("periodic_y", C.c_int),
+        ("dx", C.c_double), ("hdx", C.c_double), ("rho0", C.c_double), ("U", C.c_double),
+        ("nu", C.c_double), ("cs", C.c_double), ("alpha", C.c_double), ("pb", C.c_double),
+        ("eta_reg", C.c_double), ("gx", C.c_double), ("gy", C.c_double), ("dt", C.c_double),
+        ("use_pavg", C.c_int), ("precision", C.c_int), ("capacity", C.c_int),
+        ("max_history", C.c_int), ("use_graphs", C.c_int), ("cuda_stream", C.c_void_p),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = C.c_void_p
+_DP = C.POINTER(C.c_double)
+
+
+def load(path: Optional[str] = None):
+    """Load libedac.so.  Raises if it has not been built: there is no fallback."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB
+        if not os.path.exists(p):
+            raise RuntimeError(f"libedac.so not found at {p}: run build() (nvcc, sm_103a) first")
+        L = C.CDLL(p)
+        i32, i64, sz = C.c_int, C.c_int64, C.c_size_t
+        L.edac_workspace_bytes.argtypes = [C.POINTER(Params), C.POINTER(sz)]
+        L.edac_create.argtypes = [C.POINTER(Params), _P, sz, C.POINTER(_P)]
+        L.edac_set_inlet.argtypes = [_P, C.c_double, i32, i32, _DP, C.c_double, C.c_double]
+        L.edac_set_outlet.argtypes = [_P, C.c_double, i32, i32, i32, C.c_double]
+        L.edac_set_wall.argtypes = [_P, i32, i32, C.c_double, C.c_double, i32]
+        L.edac_set_particles.argtypes = [_P, i32] + [_DP] * 6 + [C.POINTER(C.c_uint8),
+                                                                 C.POINTER(C.c_uint64)]
+        L.edac_step.argtypes = [_P, i32]
+        L.edac_evaluate.argtypes = [_P]
+        L.edac_get_count.argtypes = [_P, C.POINTER(i32)]
+        L.edac_read_state.argtypes = [_P, i32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint8), i32,
+                                      C.POINTER(i32), C.POINTER(_DP), C.POINTER(i32)]
+        L.edac_read_history.argtypes = [_P, i32, _DP, _DP, _DP] + [C.POINTER(i32)] * 5
+        L.edac_neighbor_scratch_bytes.argtypes = [_P, C.POINTER(sz)]
+        L.edac_read_neighbors.argtypes = [_P, _P, sz, i32, C.POINTER(i64), i64,
+                                          C.POINTER(C.c_uint64), C.POINTER(i32), C.POINTER(i64)]
+        L.edac_profile.argtypes = [_P, i32, i32]
+        L.edac_read_profile.argtypes = [_P, i32, _DP, C.POINTER(i64), i32]
+        L.edac_launch_count.argtypes = [_P, C.POINTER(i64)]
+        L.edac_last_error.argtypes = [_P]
+        L.edac_last_error.restype = C.c_char_p
+        L.edac_destroy.argtypes = [_P]
+        L.edac_destroy.restype = None
+        for name in EXPORTS:
+            if name not in ("edac_last_error", "edac_destroy"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def make_params(p: "_cases.Params", precision: int, capacity: int, max_history: int,
+                use_graphs: bool, stream_ptr: int) -> Params:
+    q = Params()
+    for name in ("x_min", "x_max", "y_min", "y_max", "dx", "hdx", "rho0", "U", "nu", "cs", "alpha",
+                 "pb", "eta_reg", "gx", "gy", "dt"):
+        setattr(q, name, float(getattr(p, name)))
+    q.periodic_x = int(p.periodic_x)
+    q.periodic_y = int(p.periodic_y)
+    q.use_pavg = int(p.use_pavg)
+    q.precision = int(precision)
+    q.capacity = int(capacity)
+    q.max_history = int(max_history)
+    q.use_graphs = int(bool(use_graphs))
+    q.cuda_stream = stream_ptr or None
+    return q
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+class Solver:
+    """One particle system on one GPU, driven through the C ABI."""
+
+    def __init__(self, case, precision: str = "fp64", use_graphs: bool = True,
+                 max_history: int = 4096, capacity: Optional[int] = None, device: str = "cuda:0",
+                 stream=None, params=None):
+        import torch  # device memory and streams only
+
+        self.lib = load()
+        self.torch = torch
+        self.case = case
+        self.params = params if params is not None else case.params
+        self.precision = {"fp64": EDAC_FP64, "mixed": EDAC_MIXED}[precision]
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        cap = int(capacity if capacity is not None else case.capacity)
+        self.cparams = make_params(self.params, self.precision, cap, max_history, use_graphs,
+                                   self.stream.cuda_stream)
+        nbytes = C.c_size_t(0)
+        self._check(self.lib.edac_workspace_bytes(C.byref(self.cparams), C.byref(nbytes)), None)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        self.ctx = C.c_void_p()
+        with torch.cuda.device(self.device):
+            self._check(self.lib.edac_create(C.byref(self.cparams), C.c_void_p(self.workspace.data_ptr()),
+                                             nbytes.value, C.byref(self.ctx)), None)
+        p = self.params
+        if p.has_inlet:
+            modes = np.ascontiguousarray(p.inlet_modes, dtype=np.float64)
+            self._call("edac_set_inlet", p.x_in, p.n_in_layers, len(modes),
+                       _ptr(modes, C.c_double) if len(modes) else None, p.inlet_y0, p.inlet_h)
+        if p.has_outlet:
+            self._call("edac_set_outlet", p.x_out, p.n_out_layers, 0, p.n_avg, p.i_thresh)
+        for tagv, w in ((_cases.WALL, 0), (_cases.SLIPWALL, 1)):
+            self._call("edac_set_wall", tagv, int(p.wall_slip[w]), float(p.wall_u[w]),
+                       float(p.wall_v[w]), int(p.wall_drag[w]))
+        self.upload(case)
+
+    # -------------------------------------------------------------------------- plumbing
+    def _check(self, rc, ctx):
+        if rc != 0:
+            msg = self.lib.edac_last_error(ctx).decode() if ctx else ""
+            raise EdacError(rc, msg)
+
+    def _call(self, name, *args):
+        with self.torch.cuda.device(self.device):
+            rc = getattr(self.lib, name)(self.ctx, *args)
+        self._check(rc, self.ctx)
+        return rc
+
+    # ------------------------------------------------------------------------------- API
+    def upload(self, case):
+        a = {k: np.ascontiguousarray(getattr(case, k)) for k in ("x", "y", "u", "v", "p", "m")}
+        tag = np.ascontiguousarray(case.tag, dtype=np.uint8)
+        ids = np.ascontiguousarray(case.id, dtype=np.uint64)
+        self._call("edac_set_particles", int(case.n), *[_ptr(a[k].astype(np.float64), C.c_double)
+                                                        if a[k].dtype != np.float64 else _ptr(a[k], C.c_double)
+                                                        for k in ("x", "y", "u", "v", "p", "m")],
+                   _ptr(tag, C.c_uint8), _ptr(ids, C.c_uint64))
+
+    def step(self, n: int = 1):
+        self._call("edac_step", int(n))
+
+    def evaluate(self):
+        self._call("edac_evaluate")
+
+    def count(self) -> int:
+        n = C.c_int(0)
+        self._call("edac_get_count", C.byref(n))
+        return n.value
+
+    def state(self, fields: Iterable[str] = ("x", "y", "u", "v", "p")) -> Dict[str, np.ndarray]:
+        """Live particles in ascending id order: id, tag and the requested fields."""
+        fields = list(fields)
+        cap = int(self.cparams.capacity)
+        ids = np.zeros(cap, dtype=np.uint64)
+        tags = np.zeros(cap, dtype=np.uint8)
+        outs = [np.zeros(cap, dtype=np.float64) for _ in fields]
+        fid = (C.c_int * max(1, len(fields)))(*[FIELD_ID[f] for f in fields])
+        optr = (_DP * max(1, len(fields)))(*[_ptr(o, C.c_double) for o in outs])
+        n = C.c_int(0)
+        self._call("edac_read_state", cap, _ptr(ids, C.c_uint64), _ptr(tags, C.c_uint8),
+                   len(fields), fid, optr, C.byref(n))
+        k = n.value
+        out = {"id": ids[:k].copy(), "tag": tags[:k].copy()}
+        for f, o in zip(fields, outs):
+            out[f] = o[:k].copy()
+        return out
+
+    def history(self, max_steps: Optional[int] = None):
+        m = int(max_steps or self.cparams.max_history)
+        fx, fy, mf = (np.zeros(m) for _ in range(3))
+        na, sp, dl, to = (np.zeros(m, dtype=np.int32) for _ in range(4))
+        ns = C.c_int(0)
+        self._call("edac_read_history", m, _ptr(fx, C.c_double), _ptr(fy, C.c_double),
+                   _ptr(mf, C.c_double), _ptr(na, C.c_int), _ptr(sp, C.c_int), _ptr(dl, C.c_int),
+                   _ptr(to, C.c_int), C.byref(ns))
+        k = ns.value
+        return dict(fx=fx[:k], fy=fy[:k], mass_flux=mf[:k], n_active=na[:k], n_spawn=sp[:k],
+                    n_delete=dl[:k], n_to_outlet=to[:k])
+
+    def neighbors(self):
+        """(ids ascending, CSR start, neighbour ids) built with the pair kernels' test."""
+        nb = C.c_size_t(0)
+        self._call("edac_neighbor_scratch_bytes", C.byref(nb))
+        scratch = self.torch.empty(int(nb.value), dtype=self.torch.uint8, device=self.device)
+        cap_n = int(self.cparams.capacity)
+        start = np.zeros(cap_n + 1, dtype=np.int64)
+        cap_ids = max(1, (int(nb.value) - 8 * (cap_n + 1)) // 8 + cap_n + 64)
+        ids = np.zeros(cap_ids, dtype=np.uint64)
+        n = C.c_int(0)
+        tot = C.c_int64(0)
+        self._call("edac_read_neighbors", C.c_void_p(scratch.data_ptr()), nb.value, cap_n,
+                   _ptr(start, C.c_int64), cap_ids, _ptr(ids, C.c_uint64), C.byref(n), C.byref(tot))
+        del scratch
+        return start[: n.value + 1].copy(), ids[: tot.value].copy()
+
+    def profile(self, kernel: str, enable: bool = True):
+        self._call("edac_profile", KERNELS[kernel], int(enable))
+
+    def read_profile(self, kernel: str, reset: bool = True):
+        ms = C.c_double(0)
+        ln = C.c_int64(0)
+        self._call("edac_read_profile", KERNELS[kernel], C.byref(ms), C.byref(ln), int(reset))
+        return ms.value, ln.value
+
+    def launch_count(self) -> int:
+        c = C.c_int64(0)
+        self._call("edac_launch_count", C.byref(c))
+        return c.value
+
+    def close(self):
+        if getattr(self, "ctx", None) and self.ctx.value:
+            with self.torch.cuda.device(self.device):
+                self.lib.edac_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

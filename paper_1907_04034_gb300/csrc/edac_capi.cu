@@ -1,0 +1,770 @@
+// C ABI of the EDAC SPH library (declared in include/edac.h): parameter validation,
+// workspace layout, step orchestration (eager or one CUDA graph per step, replayed),
+// uploads and canonical (ascending-id) read-back.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "edac.h"
+#include "edac_internal.cuh"
+
+using namespace edac;
+
+struct EventPair {
+    cudaEvent_t a, b;
+};
+
+struct edac_ctx {
+    edac_params P;
+    Dev d;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    int mixed = 0;
+    bool loaded = false;   // particles uploaded
+    bool failed = false;   // device error seen
+    bool graph_ok = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int kernels_per_step = 0;
+    long long launches = 0;
+    bool prof_on[EDAC_NUM_KERNELS] = {};
+    std::vector<EventPair> prof_ev[EDAC_NUM_KERNELS];
+    size_t prof_used[EDAC_NUM_KERNELS] = {};
+    double prof_ms[EDAC_NUM_KERNELS] = {};
+    long long prof_launches[EDAC_NUM_KERNELS] = {};
+    std::string err;
+};
+
+namespace {
+
+edac_status fail(edac_ctx *c, edac_status st, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return st;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, EDAC_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+bool is_fin(double v) { return std::isfinite(v); }
+
+// ---------------------------------------------------------------- parameters -> device
+edac_status make_geo(const edac_params &P, Geo &g, std::string &why)
+{
+    const double h = P.hdx * P.dx;
+    const double rc = 3.0 * (P.hdx * P.dx);
+    g.x_min = P.x_min; g.x_max = P.x_max; g.y_min = P.y_min; g.y_max = P.y_max;
+    g.Lx = P.x_max - P.x_min;
+    g.Ly = P.y_max - P.y_min;
+    g.hLx = 0.5 * g.Lx;
+    g.hLy = 0.5 * g.Ly;
+    g.px = P.periodic_x ? 1 : 0;
+    g.py = P.periodic_y ? 1 : 0;
+    // cells a little wider than 3h: rounding of the cell index can then never put two
+    // particles closer than 3h more than one cell apart
+    const double s_min = rc * (1.0 + 1e-9);
+    double nxd = std::floor(g.Lx / s_min), nyd = std::floor(g.Ly / s_min);
+    if (nxd < 1) nxd = 1;
+    if (nyd < 1) nyd = 1;
+    if (nxd * nyd > 2.0e8) { why = "cell grid too large (> 2e8 cells)"; return EDAC_E_INVALID; }
+    g.nx = (int)nxd;
+    g.ny = (int)nyd;
+    if ((g.px && g.nx < 3) || (g.py && g.ny < 3)) {
+        why = "a periodic axis needs a box at least 3 support radii (9h) long";
+        return EDAC_E_INVALID;
+    }
+    g.ncells = g.nx * g.ny;
+    g.sx = g.Lx / g.nx;
+    g.sy = g.Ly / g.ny;
+    g.inv_sx = 1.0 / g.sx;
+    g.inv_sy = 1.0 / g.sy;
+    g.sxf = (float)g.sx;
+    g.syf = (float)g.sy;
+    g.rc2 = rc * rc;
+    g.rc2_lo = (float)(g.rc2 * (1.0 - 4e-5));
+    g.rc2_hi = (float)(g.rc2 * (1.0 + 4e-5));
+    (void)h;
+    return EDAC_OK;
+}
+
+void make_phys(const edac_params &P, Phys &ph)
+{
+    const double h = P.hdx * P.dx;
+    ph.h = h;
+    ph.inv_h = 1.0 / h;
+    ph.a2 = 7.0 / (478.0 * M_PI * h * h);
+    ph.a2h = ph.a2 / h;
+    ph.rho0 = P.rho0;
+    ph.cs = P.cs;
+    ph.c2 = P.cs * P.cs;
+    ph.nu = P.nu;
+    ph.nu_e = P.alpha * h * P.cs / 8.0;  // Eq. (edac-nu)
+    ph.eh2 = P.eta_reg * h * h;
+    ph.pb = P.pb;
+    ph.gx = P.gx;
+    ph.gy = P.gy;
+    ph.dt = P.dt;
+    ph.U = P.U;
+    ph.inv_hf = (float)ph.inv_h;
+    ph.a2f = (float)ph.a2;
+    ph.a2hf = (float)ph.a2h;
+    ph.c2f = (float)ph.c2;
+    ph.nuf = (float)ph.nu;
+    ph.nuef = (float)ph.nu_e;
+    ph.eh2f = (float)ph.eh2;
+    ph.use_pavg = P.use_pavg ? 1 : 0;
+    ph.has_inlet = 0;
+    ph.n_modes = 0;
+    ph.x_in = 0; ph.L_in = 0; ph.in_y0 = 0; ph.in_H = 1;
+    for (int k = 0; k < MAX_MODES; ++k) ph.modes[k] = 0.0;
+    ph.has_outlet = 0;
+    ph.n_avg = 6;
+    ph.x_out = 0; ph.L_out = 0;
+    const double q = 0.5 * P.rho0 * P.U * P.U;
+    ph.I_thr = q * q / (2.0 * P.rho0 * P.cs);  // Eq. (acouinten)
+    ph.wall_slip[0] = 0; ph.wall_slip[1] = 1;
+    ph.wall_drag[0] = 1; ph.wall_drag[1] = 0;
+    ph.wall_u[0] = ph.wall_u[1] = ph.wall_v[0] = ph.wall_v[1] = 0.0;
+}
+
+edac_status check_params(const edac_params *P, std::string &why)
+{
+    if (!P) { why = "params is NULL"; return EDAC_E_INVALID; }
+    const double vals[] = {P->x_min, P->x_max, P->y_min, P->y_max, P->dx, P->hdx, P->rho0, P->U,
+                           P->nu, P->cs, P->alpha, P->pb, P->eta_reg, P->gx, P->gy, P->dt};
+    for (double v : vals)
+        if (!is_fin(v)) { why = "non-finite parameter"; return EDAC_E_INVALID; }
+    if (!(P->x_max > P->x_min && P->y_max > P->y_min)) { why = "empty domain box"; return EDAC_E_INVALID; }
+    if (!(P->dx > 0 && P->hdx > 0 && P->rho0 > 0 && P->cs > 0 && P->dt > 0 && P->eta_reg > 0)) {
+        why = "dx, hdx, rho0, cs, dt and eta_reg must be > 0";
+        return EDAC_E_INVALID;
+    }
+    if (P->nu < 0 || P->alpha < 0) { why = "nu and alpha must be >= 0"; return EDAC_E_INVALID; }
+    if (P->precision != EDAC_FP64 && P->precision != EDAC_MIXED) {
+        why = "precision must be EDAC_FP64 or EDAC_MIXED";
+        return EDAC_E_INVALID;
+    }
+    if (P->capacity < 1 || P->capacity > (1 << 30)) { why = "capacity out of range"; return EDAC_E_INVALID; }
+    if (P->max_history < 1 || P->max_history > (1 << 26)) { why = "max_history out of range"; return EDAC_E_INVALID; }
+    return EDAC_OK;
+}
+
+// Carve the workspace (base may be null: size computation only).
+size_t layout(Dev &d, const Geo &g, int cap, int max_history, int mixed, char *base)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        off = (off + 255) & ~(size_t)255;
+        void *p = base ? (void *)(base + off) : nullptr;
+        off += bytes;
+        return p;
+    };
+    const size_t C = (size_t)cap;
+#define DARR(field, T, count) d.field = (T *)take(sizeof(T) * (count))
+    DARR(cnt, Counters, 1);
+    DARR(x, double, C); DARR(y, double, C); DARR(u, double, C); DARR(v, double, C);
+    DARR(ut, double, C); DARR(vt, double, C); DARR(p, double, C); DARR(m, double, C);
+    DARR(x0, double, C); DARR(y0, double, C); DARR(u0, double, C); DARR(v0, double, C);
+    DARR(p0, double, C);
+    DARR(au, double, C); DARR(av, double, C); DARR(ap, double, C); DARR(abu, double, C);
+    DARR(abv, double, C); DARR(fx, double, C); DARR(fy, double, C); DARR(rho, double, C);
+    DARR(vol, double, C);
+    DARR(nnb, int, C);
+    DARR(tag, uint8_t, C);
+    DARR(id, unsigned long long, C);
+    DARR(ring, double, C * NAVG_MAX * 3);
+    DARR(rpos, uint8_t, C);
+    DARR(ubar, double, C); DARR(vbar, double, C); DARR(pbar, double, C); DARR(J2, double, C);
+    DARR(J2p, double, C); DARR(advp, double, C);
+    DARR(redp, uint8_t, C);
+    DARR(cell_count, int, (size_t)g.ncells);
+    DARR(cell_start, int, (size_t)g.ncells + 1);
+    DARR(slot_cell, int, C);
+    DARR(within, int, C);
+    DARR(order, int, C);
+    DARR(cellk, int, C);
+    DARR(stag, uint8_t, C);
+    DARR(P, float4, C);
+    DARR(XY, double2, C);
+    DARR(AUX, double2, C);
+    DARR(snnb, int, C);
+    if (mixed) {
+        DARR(Bf, float4, C);
+        DARR(Qf, float4, C);
+        d.UV = d.DUV = d.PV = d.RM = nullptr;
+        d.Ms = nullptr;
+    } else {
+        DARR(UV, double2, C); DARR(DUV, double2, C); DARR(PV, double2, C); DARR(RM, double2, C);
+        DARR(Ms, double, C);
+        d.Bf = d.Qf = nullptr;
+    }
+    DARR(bnd, int, C);
+    DARR(free_stack, int, C);
+    DARR(ev_spawn_key, unsigned long long, LIST_MAX); DARR(ev_spawn_slot, int, LIST_MAX);
+    DARR(ev_del_key, unsigned long long, LIST_MAX); DARR(ev_del_slot, int, LIST_MAX);
+    DARR(ev_out_key, unsigned long long, LIST_MAX); DARR(ev_out_m, double, LIST_MAX);
+    DARR(drag_slots, int, C);
+    DARR(scratch_m, double, LIST_MAX);
+    DARR(hist, double, (size_t)max_history * 8);
+#undef DARR
+    return (off + 255) & ~(size_t)255;
+}
+
+// ------------------------------------------------------------------ step orchestration
+struct Group {
+    edac_ctx *c;
+    int k;
+    bool on;
+    size_t idx;
+    Group(edac_ctx *ctx, int kernel) : c(ctx), k(kernel), on(ctx->prof_on[kernel]), idx(0)
+    {
+        if (!on) return;
+        auto &v = c->prof_ev[k];
+        idx = c->prof_used[k]++;
+        if (idx >= v.size()) {
+            EventPair e;
+            cudaEventCreate(&e.a);
+            cudaEventCreate(&e.b);
+            v.push_back(e);
+        }
+        cudaEventRecord(v[idx].a, c->stream);
+    }
+    ~Group()
+    {
+        if (on) cudaEventRecord(c->prof_ev[k][idx].b, c->stream);
+    }
+};
+
+int issue_eval(edac_ctx *c, int end_of_step)
+{
+    int n = 0;
+    { Group g(c, EDAC_K_REBUILD); n += launch_rebuild(c->d, c->stream, c->mixed); }
+    { Group g(c, EDAC_K_PASS_A); n += launch_pass_a(c->d, c->stream, c->mixed); }
+    { Group g(c, EDAC_K_BOUNDARY); n += launch_boundary(c->d, c->stream, c->mixed, end_of_step); }
+    { Group g(c, EDAC_K_PASS_B); n += launch_pass_b(c->d, c->stream, c->mixed); }
+    return n;
+}
+
+int issue_step(edac_ctx *c)
+{
+    int n = 0;
+    { Group g(c, EDAC_K_STAGE); n += launch_stage(c->d, c->stream, 0); }
+    n += issue_eval(c, 0);
+    { Group g(c, EDAC_K_STAGE); n += launch_stage(c->d, c->stream, 1); }
+    n += issue_eval(c, 1);
+    { Group g(c, EDAC_K_RECYCLE); n += launch_recycle(c->d, c->stream); }
+    return n;
+}
+
+bool any_profiling(const edac_ctx *c)
+{
+    for (int k = 0; k < EDAC_NUM_KERNELS; ++k)
+        if (c->prof_on[k]) return true;
+    return false;
+}
+
+void drop_graph(edac_ctx *c)
+{
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+    c->graph_ok = false;
+}
+
+// Sticky device error word -> status.
+edac_status check_device(edac_ctx *ctx)
+{
+    Counters h;
+    CK(cudaMemcpyAsync(&h, ctx->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (h.err) {
+        ctx->failed = true;
+        if (h.err & ERR_NONFINITE) return fail(ctx, EDAC_E_NONFINITE, "non-finite value in the particle fields");
+        if (h.err & ERR_DOMAIN) return fail(ctx, EDAC_E_DOMAIN, "a particle left the domain box");
+        if (h.err & (ERR_CAPACITY | ERR_LIST)) return fail(ctx, EDAC_E_CAPACITY, "particle capacity or event list exceeded");
+        if (h.err & ERR_TIMEOUT) return fail(ctx, EDAC_E_TIMEOUT, "a device wait timed out");
+        return fail(ctx, EDAC_E_STATE, "device error");
+    }
+    return EDAC_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+edac_status edac_workspace_bytes(const edac_params *params, size_t *bytes)
+{
+    std::string why;
+    edac_status st = check_params(params, why);
+    if (st) return st;
+    if (!bytes) return EDAC_E_INVALID;
+    Geo g;
+    st = make_geo(*params, g, why);
+    if (st) return st;
+    Dev d;
+    *bytes = layout(d, g, params->capacity, params->max_history, params->precision == EDAC_MIXED, nullptr);
+    return EDAC_OK;
+}
+
+edac_status edac_create(const edac_params *params, void *d_workspace, size_t bytes, edac_ctx **out)
+{
+    if (!out) return EDAC_E_INVALID;
+    *out = nullptr;
+    std::string why;
+    edac_status st = check_params(params, why);
+    if (st) return st;
+    Geo g;
+    st = make_geo(*params, g, why);
+    if (st) return st;
+    Dev probe;
+    const size_t need = layout(probe, g, params->capacity, params->max_history,
+                               params->precision == EDAC_MIXED, nullptr);
+    if (!d_workspace || bytes < need || ((uintptr_t)d_workspace & 255u)) return EDAC_E_INVALID;
+    edac_ctx *c = new edac_ctx();
+    c->P = *params;
+    c->mixed = params->precision == EDAC_MIXED;
+    c->stream = (cudaStream_t)params->cuda_stream;
+    c->ws = (char *)d_workspace;
+    c->ws_bytes = bytes;
+    c->d.g = g;
+    make_phys(*params, c->d.ph);
+    c->d.cap = params->capacity;
+    c->d.max_history = params->max_history;
+    layout(c->d, g, params->capacity, params->max_history, c->mixed, c->ws);
+    *out = c;
+    return EDAC_OK;
+}
+
+edac_status edac_set_inlet(edac_ctx *ctx, double x_in, int n_layers, int n_modes,
+                           const double *h_modes, double y0, double H)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    if (!is_fin(x_in) || n_layers < 1 || n_modes < 0 || n_modes > MAX_MODES || !is_fin(y0) ||
+        !(H > 0) || (n_modes > 0 && !h_modes))
+        return fail(ctx, EDAC_E_INVALID, "bad inlet arguments");
+    Phys &ph = ctx->d.ph;
+    ph.has_inlet = 1;
+    ph.x_in = x_in;
+    ph.L_in = (double)n_layers * ctx->P.dx;
+    ph.n_modes = n_modes;
+    for (int k = 0; k < MAX_MODES; ++k) ph.modes[k] = k < n_modes ? h_modes[k] : 0.0;
+    for (int k = 0; k < n_modes; ++k)
+        if (!is_fin(ph.modes[k])) return fail(ctx, EDAC_E_INVALID, "non-finite inlet mode");
+    ph.in_y0 = y0;
+    ph.in_H = H;
+    drop_graph(ctx);
+    return EDAC_OK;
+}
+
+edac_status edac_set_outlet(edac_ctx *ctx, double x_out, int n_layers, int kind, int n_avg,
+                            double i_thresh)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    if (!is_fin(x_out) || n_layers < 1 || kind != 0 || n_avg < 1 || n_avg > NAVG_MAX ||
+        !is_fin(i_thresh))
+        return fail(ctx, EDAC_E_INVALID, "bad outlet arguments");
+    Phys &ph = ctx->d.ph;
+    ph.has_outlet = 1;
+    ph.x_out = x_out;
+    ph.L_out = (double)n_layers * ctx->P.dx;
+    ph.n_avg = n_avg;
+    if (i_thresh >= 0) ph.I_thr = i_thresh;
+    drop_graph(ctx);
+    return EDAC_OK;
+}
+
+edac_status edac_set_wall(edac_ctx *ctx, int tag, int slip, double uw, double vw, int count_in_drag)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    if ((tag != EDAC_WALL && tag != EDAC_SLIPWALL) || !is_fin(uw) || !is_fin(vw))
+        return fail(ctx, EDAC_E_INVALID, "bad wall arguments");
+    if (ctx->loaded) return fail(ctx, EDAC_E_STATE, "set walls before edac_set_particles");
+    const int w = tag == EDAC_WALL ? 0 : 1;
+    Phys &ph = ctx->d.ph;
+    ph.wall_slip[w] = slip ? 1 : 0;
+    ph.wall_u[w] = uw;
+    ph.wall_v[w] = vw;
+    ph.wall_drag[w] = count_in_drag ? 1 : 0;
+    drop_graph(ctx);
+    return EDAC_OK;
+}
+
+edac_status edac_set_particles(edac_ctx *ctx, int n, const double *h_x, const double *h_y,
+                               const double *h_u, const double *h_v, const double *h_p,
+                               const double *h_m, const uint8_t *h_tag, const uint64_t *h_id)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    const int cap = ctx->d.cap;
+    if (n < 0 || n > cap) return fail(ctx, EDAC_E_INVALID, "n out of range [0, capacity]");
+    if (n > 0 && (!h_x || !h_y || !h_u || !h_v || !h_p || !h_m || !h_tag || !h_id))
+        return fail(ctx, EDAC_E_INVALID, "NULL input array");
+    const Geo &g = ctx->d.g;
+    std::vector<uint64_t> ids(h_id, h_id + n);
+    for (int i = 0; i < n; ++i) {
+        if (h_tag[i] > EDAC_SLIPWALL) return fail(ctx, EDAC_E_INVALID, "tag out of range");
+        if (!(is_fin(h_x[i]) && is_fin(h_y[i]) && is_fin(h_u[i]) && is_fin(h_v[i]) &&
+              is_fin(h_p[i]) && is_fin(h_m[i])))
+            return fail(ctx, EDAC_E_INVALID, "non-finite input value");
+        if (!(h_m[i] > 0)) return fail(ctx, EDAC_E_INVALID, "masses must be > 0");
+        if (!(h_x[i] >= g.x_min && h_x[i] < g.x_max && h_y[i] >= g.y_min && h_y[i] < g.y_max))
+            return fail(ctx, EDAC_E_DOMAIN, "particle outside the domain box");
+        if (h_tag[i] == EDAC_INLET && !ctx->d.ph.has_inlet)
+            return fail(ctx, EDAC_E_INVALID, "inlet particles without edac_set_inlet");
+        if (h_tag[i] == EDAC_OUTLET && !ctx->d.ph.has_outlet)
+            return fail(ctx, EDAC_E_INVALID, "outlet particles without edac_set_outlet");
+    }
+    std::sort(ids.begin(), ids.end());
+    if (std::adjacent_find(ids.begin(), ids.end()) != ids.end())
+        return fail(ctx, EDAC_E_INVALID, "duplicate particle ids");
+    Dev &d = ctx->d;
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemsetAsync(ctx->ws, 0, ctx->ws_bytes, s));
+    std::vector<uint8_t> tag(cap, TAG_DEAD);
+    for (int i = 0; i < n; ++i) tag[i] = h_tag[i];
+    std::vector<int> free_stack(cap - n);
+    for (int i = 0; i < cap - n; ++i) free_stack[i] = cap - 1 - i;
+    std::vector<int> drag;
+    for (int i = 0; i < n; ++i) {
+        const int t = h_tag[i];
+        if ((t == EDAC_WALL && d.ph.wall_drag[0]) || (t == EDAC_SLIPWALL && d.ph.wall_drag[1]))
+            drag.push_back(i);
+    }
+    Counters hc;
+    std::memset(&hc, 0, sizeof(hc));
+    hc.n_alive = n;
+    hc.free_top = cap - n;
+    hc.n_drag = (int)drag.size();
+    hc.next_id = n ? (unsigned long long)ids.back() + 1ull : 0ull;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(d.x, h_x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d.y, h_y, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d.u, h_u, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d.v, h_v, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d.p, h_p, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d.m, h_m, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d.id, h_id, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaMemcpyAsync(d.tag, tag.data(), cap, cudaMemcpyHostToDevice, s));
+    if (cap - n > 0)
+        CK(cudaMemcpyAsync(d.free_stack, free_stack.data(), sizeof(int) * (cap - n),
+                           cudaMemcpyHostToDevice, s));
+    if (!drag.empty())
+        CK(cudaMemcpyAsync(d.drag_slots, drag.data(), sizeof(int) * drag.size(),
+                           cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d.cnt, &hc, sizeof(hc), cudaMemcpyHostToDevice, s));
+    ctx->launches += launch_init(d, s);
+    ctx->launches += issue_eval(ctx, 0);
+    CK(cudaGetLastError());
+    // the host vectors above must outlive the asynchronous copies
+    CK(cudaStreamSynchronize(s));
+    ctx->loaded = true;
+    ctx->failed = false;
+    return check_device(ctx);
+}
+
+edac_status edac_step(edac_ctx *ctx, int nsteps)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    if (nsteps < 0) return fail(ctx, EDAC_E_INVALID, "nsteps < 0");
+    if (!ctx->loaded) return fail(ctx, EDAC_E_STATE, "no particles: call edac_set_particles first");
+    if (ctx->failed) return fail(ctx, EDAC_E_STATE, "context in error: re-initialise with edac_set_particles");
+    if (nsteps == 0) return EDAC_OK;
+    const bool graphs = ctx->P.use_graphs && ctx->stream != nullptr && !any_profiling(ctx);
+    if (graphs) {
+        if (!ctx->graph_ok) {
+            drop_graph(ctx);
+            CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            const int k = issue_step(ctx);
+            cudaGraph_t gr = nullptr;
+            cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
+            if (e != cudaSuccess) return fail(ctx, EDAC_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            ctx->graph = gr;
+            CK(cudaGraphInstantiate(&ctx->exec, gr, 0));
+            ctx->kernels_per_step = k;
+            ctx->graph_ok = true;
+        }
+        for (int i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(ctx->exec, ctx->stream));
+        ctx->launches += (long long)ctx->kernels_per_step * nsteps;
+    } else {
+        for (int i = 0; i < nsteps; ++i) ctx->launches += issue_step(ctx);
+    }
+    CK(cudaGetLastError());
+    return EDAC_OK;
+}
+
+edac_status edac_evaluate(edac_ctx *ctx)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    if (!ctx->loaded) return fail(ctx, EDAC_E_STATE, "no particles");
+    if (ctx->failed) return fail(ctx, EDAC_E_STATE, "context in error");
+    ctx->launches += issue_eval(ctx, 0);
+    CK(cudaGetLastError());
+    return EDAC_OK;
+}
+
+edac_status edac_get_count(edac_ctx *ctx, int *n_active)
+{
+    if (!ctx || !n_active) return EDAC_E_INVALID;
+    if (!ctx->loaded) return fail(ctx, EDAC_E_STATE, "no particles");
+    Counters h;
+    CK(cudaMemcpyAsync(&h, ctx->d.cnt, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *n_active = h.n_alive;
+    return check_device(ctx);
+}
+
+edac_status edac_read_state(edac_ctx *ctx, int cap, uint64_t *h_id, uint8_t *h_tag, int nfields,
+                            const int *field_ids, double *const *h_out, int *n)
+{
+    if (!ctx || !n || nfields < 0 || (nfields > 0 && (!field_ids || !h_out)))
+        return EDAC_E_INVALID;
+    if (!ctx->loaded) return fail(ctx, EDAC_E_STATE, "no particles");
+    for (int f = 0; f < nfields; ++f)
+        if (field_ids[f] < 0 || field_ids[f] >= EDAC_NUM_FIELDS || !h_out[f])
+            return fail(ctx, EDAC_E_INVALID, "bad field id or output pointer");
+    edac_status st = check_device(ctx);
+    if (st) return st;
+    const Dev &d = ctx->d;
+    const int C = d.cap;
+    cudaStream_t s = ctx->stream;
+    std::vector<uint8_t> tag(C);
+    std::vector<unsigned long long> id(C);
+    CK(cudaMemcpyAsync(tag.data(), d.tag, C, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(id.data(), d.id, sizeof(unsigned long long) * C, cudaMemcpyDeviceToHost, s));
+    std::vector<std::vector<double>> cols(nfields, std::vector<double>(C));
+    std::vector<int> ibuf(C);
+    std::vector<uint8_t> bbuf(C);
+    for (int f = 0; f < nfields; ++f) {
+        const double *src = nullptr;
+        switch (field_ids[f]) {
+            case EDAC_F_X: src = d.x; break;
+            case EDAC_F_Y: src = d.y; break;
+            case EDAC_F_U: src = d.u; break;
+            case EDAC_F_V: src = d.v; break;
+            case EDAC_F_UT: src = d.ut; break;
+            case EDAC_F_VT: src = d.vt; break;
+            case EDAC_F_P: src = d.p; break;
+            case EDAC_F_M: src = d.m; break;
+            case EDAC_F_RHO: src = d.rho; break;
+            case EDAC_F_VOL: src = d.vol; break;
+            case EDAC_F_AU: src = d.au; break;
+            case EDAC_F_AV: src = d.av; break;
+            case EDAC_F_AP: src = d.ap; break;
+            case EDAC_F_ABU: src = d.abu; break;
+            case EDAC_F_ABV: src = d.abv; break;
+            case EDAC_F_FX: src = d.fx; break;
+            case EDAC_F_FY: src = d.fy; break;
+            case EDAC_F_UBAR: src = d.ubar; break;
+            case EDAC_F_VBAR: src = d.vbar; break;
+            case EDAC_F_PBAR: src = d.pbar; break;
+            case EDAC_F_J2: src = d.J2; break;
+            case EDAC_F_J2P: src = d.J2p; break;
+            case EDAC_F_ADVP: src = d.advp; break;
+            default: break;
+        }
+        if (src) {
+            CK(cudaMemcpyAsync(cols[f].data(), src, sizeof(double) * C, cudaMemcpyDeviceToHost, s));
+        } else if (field_ids[f] == EDAC_F_NNB) {
+            CK(cudaMemcpyAsync(ibuf.data(), d.nnb, sizeof(int) * C, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int i = 0; i < C; ++i) cols[f][i] = ibuf[i];
+        } else {
+            const uint8_t *b = field_ids[f] == EDAC_F_REDP ? d.redp : d.rpos;
+            CK(cudaMemcpyAsync(bbuf.data(), b, C, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int i = 0; i < C; ++i) cols[f][i] = bbuf[i];
+        }
+    }
+    CK(cudaStreamSynchronize(s));
+    std::vector<int> live;
+    live.reserve(C);
+    for (int i = 0; i < C; ++i)
+        if (tag[i] != TAG_DEAD) live.push_back(i);
+    std::sort(live.begin(), live.end(), [&](int a, int b) { return id[a] < id[b]; });
+    const int nl = (int)live.size();
+    *n = nl;
+    if (nl > cap) return fail(ctx, EDAC_E_INVALID, "output arrays too short");
+    for (int r = 0; r < nl; ++r) {
+        const int i = live[r];
+        if (h_id) h_id[r] = id[i];
+        if (h_tag) h_tag[r] = tag[i];
+        for (int f = 0; f < nfields; ++f) h_out[f][r] = cols[f][i];
+    }
+    return EDAC_OK;
+}
+
+edac_status edac_read_history(edac_ctx *ctx, int max_steps, double *h_fx, double *h_fy,
+                              double *h_mass_flux, int *h_n_active, int *h_n_spawn,
+                              int *h_n_delete, int *h_n_to_outlet, int *nsteps)
+{
+    if (!ctx || !nsteps || max_steps < 0) return EDAC_E_INVALID;
+    if (!ctx->loaded) return fail(ctx, EDAC_E_STATE, "no particles");
+    edac_status st = check_device(ctx);
+    if (st) return st;
+    Counters h;
+    CK(cudaMemcpyAsync(&h, ctx->d.cnt, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    const int H = ctx->d.max_history;
+    std::vector<double> hist((size_t)H * 8);
+    CK(cudaMemcpyAsync(hist.data(), ctx->d.hist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int avail = std::min(h.hist_len, H);
+    const int k = std::min(avail, max_steps);
+    for (int r = 0; r < k; ++r) {
+        const int stepi = h.step - k + r;
+        const double *rec = hist.data() + (size_t)(stepi % H) * 8;
+        if (h_fx) h_fx[r] = rec[0];
+        if (h_fy) h_fy[r] = rec[1];
+        if (h_mass_flux) h_mass_flux[r] = rec[2];
+        if (h_n_active) h_n_active[r] = (int)rec[3];
+        if (h_n_spawn) h_n_spawn[r] = (int)rec[4];
+        if (h_n_delete) h_n_delete[r] = (int)rec[5];
+        if (h_n_to_outlet) h_n_to_outlet[r] = (int)rec[6];
+    }
+    *nsteps = k;
+    return EDAC_OK;
+}
+
+edac_status edac_neighbor_scratch_bytes(edac_ctx *ctx, size_t *bytes)
+{
+    if (!ctx || !bytes) return EDAC_E_INVALID;
+    if (!ctx->loaded) return fail(ctx, EDAC_E_STATE, "no particles");
+    if (ctx->failed) return fail(ctx, EDAC_E_STATE, "context in error");
+    ctx->launches += launch_rebuild(ctx->d, ctx->stream, ctx->mixed);
+    ctx->launches += launch_pass_a(ctx->d, ctx->stream, ctx->mixed);
+    CK(cudaGetLastError());
+    Counters h;
+    CK(cudaMemcpyAsync(&h, ctx->d.cnt, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::vector<int> cntv(std::max(h.n_alive, 1));
+    if (h.n_alive > 0)
+        CK(cudaMemcpy(cntv.data(), ctx->d.snnb, sizeof(int) * h.n_alive, cudaMemcpyDeviceToHost));
+    long long tot = 0;
+    for (int k = 0; k < h.n_alive; ++k) tot += cntv[k];
+    *bytes = sizeof(long long) * ((size_t)h.n_alive + 1) + sizeof(unsigned long long) * (size_t)tot + 256;
+    return EDAC_OK;
+}
+
+edac_status edac_read_neighbors(edac_ctx *ctx, void *d_scratch, size_t scratch_bytes, int cap_n,
+                                int64_t *h_start, int64_t cap_ids, uint64_t *h_nbr_ids, int *n,
+                                int64_t *total)
+{
+    if (!ctx || !n || !total || !d_scratch || !h_start || (cap_ids > 0 && !h_nbr_ids))
+        return EDAC_E_INVALID;
+    if (!ctx->loaded) return fail(ctx, EDAC_E_STATE, "no particles");
+    if (ctx->failed) return fail(ctx, EDAC_E_STATE, "context in error");
+    cudaStream_t s = ctx->stream;
+    const Dev &d = ctx->d;
+    ctx->launches += launch_rebuild(d, s, ctx->mixed);
+    ctx->launches += launch_pass_a(d, s, ctx->mixed);
+    CK(cudaGetLastError());
+    Counters h;
+    CK(cudaMemcpyAsync(&h, d.cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int na = h.n_alive;
+    std::vector<int> cntv(std::max(na, 1)), order(std::max(na, 1));
+    std::vector<unsigned long long> id(d.cap);
+    if (na > 0) {
+        CK(cudaMemcpy(cntv.data(), d.snnb, sizeof(int) * na, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(order.data(), d.order, sizeof(int) * na, cudaMemcpyDeviceToHost));
+    }
+    CK(cudaMemcpy(id.data(), d.id, sizeof(unsigned long long) * d.cap, cudaMemcpyDeviceToHost));
+    std::vector<long long> start(na + 1, 0);
+    for (int k = 0; k < na; ++k) start[k + 1] = start[k] + cntv[k];
+    const long long tot = start[na];
+    const size_t need = sizeof(long long) * ((size_t)na + 1) + sizeof(unsigned long long) * (size_t)tot + 256;
+    if (scratch_bytes < need) return fail(ctx, EDAC_E_INVALID, "neighbour scratch too small");
+    if (cap_n < na || cap_ids < tot) return fail(ctx, EDAC_E_INVALID, "output arrays too short");
+    long long *d_start = (long long *)d_scratch;
+    unsigned long long *d_ids =
+        (unsigned long long *)(((uintptr_t)(d_start + na + 1) + 255) & ~(uintptr_t)255);
+    CK(cudaMemcpyAsync(d_start, start.data(), sizeof(long long) * (na + 1), cudaMemcpyHostToDevice, s));
+    ctx->launches += launch_neighbor_dump(d, s, ctx->mixed, d_start, d_ids);
+    CK(cudaGetLastError());
+    std::vector<unsigned long long> ids(std::max<long long>(tot, 1));
+    if (tot > 0)
+        CK(cudaMemcpyAsync(ids.data(), d_ids, sizeof(unsigned long long) * tot, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // canonical order: particles by ascending id, each list ascending
+    std::vector<int> ks(na);
+    std::iota(ks.begin(), ks.end(), 0);
+    std::sort(ks.begin(), ks.end(), [&](int a, int b) { return id[order[a]] < id[order[b]]; });
+    long long pos = 0;
+    h_start[0] = 0;
+    for (int r = 0; r < na; ++r) {
+        const int k = ks[r];
+        std::vector<unsigned long long> lst(ids.begin() + start[k], ids.begin() + start[k + 1]);
+        std::sort(lst.begin(), lst.end());
+        for (auto v : lst) h_nbr_ids[pos++] = v;
+        h_start[r + 1] = pos;
+    }
+    *n = na;
+    *total = tot;
+    return check_device(ctx);
+}
+
+edac_status edac_profile(edac_ctx *ctx, int kernel, int enable)
+{
+    if (!ctx || kernel < 0 || kernel >= EDAC_NUM_KERNELS) return EDAC_E_INVALID;
+    ctx->prof_on[kernel] = enable != 0;
+    return EDAC_OK;
+}
+
+edac_status edac_read_profile(edac_ctx *ctx, int kernel, double *ms, int64_t *launches, int reset)
+{
+    if (!ctx || kernel < 0 || kernel >= EDAC_NUM_KERNELS) return EDAC_E_INVALID;
+    CK(cudaStreamSynchronize(ctx->stream));
+    auto &v = ctx->prof_ev[kernel];
+    for (size_t i = 0; i < ctx->prof_used[kernel]; ++i) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, v[i].a, v[i].b));
+        ctx->prof_ms[kernel] += t;
+        ctx->prof_launches[kernel] += 1;
+    }
+    ctx->prof_used[kernel] = 0;
+    if (ms) *ms = ctx->prof_ms[kernel];
+    if (launches) *launches = ctx->prof_launches[kernel];
+    if (reset) {
+        ctx->prof_ms[kernel] = 0.0;
+        ctx->prof_launches[kernel] = 0;
+    }
+    return EDAC_OK;
+}
+
+edac_status edac_launch_count(edac_ctx *ctx, int64_t *count)
+{
+    if (!ctx || !count) return EDAC_E_INVALID;
+    *count = ctx->launches;
+    return EDAC_OK;
+}
+
+const char *edac_last_error(edac_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : "NULL context";
+}
+
+void edac_destroy(edac_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->loaded) cudaStreamSynchronize(ctx->stream);
+    drop_graph(ctx);
+    for (int k = 0; k < EDAC_NUM_KERNELS; ++k)
+        for (auto &e : ctx->prof_ev[k]) {
+            cudaEventDestroy(e.a);
+            cudaEventDestroy(e.b);
+        }
+    delete ctx;
+}
+
+}  // extern "C"

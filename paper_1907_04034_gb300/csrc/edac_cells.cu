@@ -1,0 +1,454 @@
+// Cell-list build, time-integration stages, particle recycling and the end-of-step
+// reduction of the EDAC SPH library (sm_103a).
+//
+// Cell build: a counting sort of live slots by cell (row-major, x fastest, cells of at
+// least 3h): per-cell counts by atomics, one exclusive scan, a scatter, and a per-cell
+// sort by slot that makes the order independent of the atomic order.  The gather then
+// writes the cell-ordered copies the pair kernels read (fp32 cell-relative positions
+// for the pre-test, fp64 positions, and the fields of the chosen precision).
+#include "edac_internal.cuh"
+
+namespace edac {
+
+namespace {
+
+constexpr int TPB = 256;
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Warp-aggregated append: every lane with `want` gets a distinct index into a list whose
+// length lives at *counter; one atomic per warp.  All 32 lanes must call it.
+__device__ __forceinline__ int warp_append(int *counter, bool want)
+{
+    const unsigned mask = __ballot_sync(0xffffffffu, want);
+    if (mask == 0u) return -1;
+    const int leader = __ffs(mask) - 1;
+    int base = 0;
+    if ((int)lane_id() == leader) base = atomicAdd(counter, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return want ? base + __popc(mask & ((1u << lane_id()) - 1u)) : -1;
+}
+
+// ------------------------------------------------------------------------- cell build
+__global__ void k_cell_count(Dev d)
+{
+    const Geo &g = d.g;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.cap; s += gridDim.x * blockDim.x) {
+        if (d.tag[s] == TAG_DEAD) {
+            d.slot_cell[s] = -1;
+            continue;
+        }
+        const double xs = d.x[s], ys = d.y[s];
+        if (!(xs >= g.x_min && xs < g.x_max && ys >= g.y_min && ys < g.y_max)) set_err(d, ERR_DOMAIN);
+        const int cx = cell_coord(xs, g.x_min, g.inv_sx, g.nx);
+        const int cy = cell_coord(ys, g.y_min, g.inv_sy, g.ny);
+        const int c = cy * g.nx + cx;
+        d.slot_cell[s] = c;
+        d.within[s] = atomicAdd(d.cell_count + c, 1);
+    }
+}
+
+// Exclusive scan of the per-cell counts into cell_start[0..ncells], one block of 1024
+// threads: each thread owns a contiguous chunk, block-scans the chunk totals, then writes
+// its chunk's prefix sums.  Also resets the boundary-list length for the gather.
+__global__ void __launch_bounds__(1024) k_cell_scan(Dev d)
+{
+    __shared__ int warp_tot[32];
+    const int n = d.g.ncells;
+    const int t = threadIdx.x;
+    const int chunk = (n + 1023) / 1024;
+    const int b = t * chunk, e = min(n, b + chunk);
+    int local = 0;
+    for (int c = b; c < e; ++c) local += d.cell_count[c];
+    // inclusive warp scan
+    int v = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, v, o);
+        if ((int)lane_id() >= o) v += y;
+    }
+    if (lane_id() == 31) warp_tot[t >> 5] = v;
+    __syncthreads();
+    if (t < 32) {
+        int w = warp_tot[t];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (t >= o) w += y;
+        }
+        warp_tot[t] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    int run = v - local + ((t >> 5) > 0 ? warp_tot[(t >> 5) - 1] : 0);
+    for (int c = b; c < e; ++c) {
+        d.cell_start[c] = run;
+        run += d.cell_count[c];
+    }
+    if (t == 1023) {
+        const int total = warp_tot[31];
+        d.cell_start[n] = total;
+        d.cnt->n_alive = total;
+        d.cnt->n_bnd = 0;
+    }
+}
+
+__global__ void k_cell_scatter(Dev d)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.cap; s += gridDim.x * blockDim.x) {
+        const int c = d.slot_cell[s];
+        if (c < 0) continue;
+        d.order[d.cell_start[c] + d.within[s]] = s;
+    }
+}
+
+// Sort each cell's slots ascending (insertion sort; a cell holds ~13 particles), and
+// clear the cell's count for the next build.
+__global__ void k_cell_sort(Dev d)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.g.ncells; c += gridDim.x * blockDim.x) {
+        d.cell_count[c] = 0;
+        const int j0 = d.cell_start[c], j1 = d.cell_start[c + 1];
+        for (int a = j0 + 1; a < j1; ++a) {
+            const int key = d.order[a];
+            int b = a - 1;
+            while (b >= j0 && d.order[b] > key) {
+                d.order[b + 1] = d.order[b];
+                --b;
+            }
+            d.order[b + 1] = key;
+        }
+    }
+}
+
+template <int MIXED>
+__global__ void k_gather(Dev d)
+{
+    const Geo &g = d.g;
+    const int n = d.cnt->n_alive;
+    const int stride = gridDim.x * blockDim.x;
+    // uniform trip count per warp so that warp_append sees all 32 lanes
+    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int k = base + threadIdx.x;
+        const bool valid = k < n;
+        bool is_bnd = false;
+        if (valid) {
+            const int s = d.order[k];
+            const int c = d.slot_cell[s];
+            d.cellk[k] = c;
+            const int cx = c % g.nx, cy = c / g.nx;
+            const double xs = d.x[s], ys = d.y[s];
+            const float rx = (float)(xs - (g.x_min + (double)cx * g.sx));
+            const float ry = (float)(ys - (g.y_min + (double)cy * g.sy));
+            const double ms = d.m[s];
+            d.P[k] = make_float4(rx, ry, (float)ms, 0.0f);
+            d.XY[k] = make_double2(xs, ys);
+            const uint8_t t = d.tag[s];
+            d.stag[k] = (uint8_t)(t | ((t == OUTLET && d.redp[s]) ? TAG_REDP : 0));
+            d.AUX[k] = make_double2(t == FLUID ? d.J2[s] : d.J2p[s], d.advp[s]);
+            const double us = d.u[s], vs = d.v[s];
+            const double dus = d.ut[s] - us, dvs = d.vt[s] - vs;
+            if (MIXED) {
+                d.Bf[k] = make_float4((float)us, (float)vs, (float)dus, (float)dvs);
+                d.Qf[k] = make_float4((float)d.p[s], 0.0f, 0.0f, 0.0f);
+            } else {
+                d.UV[k] = make_double2(us, vs);
+                d.DUV[k] = make_double2(dus, dvs);
+                d.PV[k] = make_double2(d.p[s], 0.0);
+                d.Ms[k] = ms;
+            }
+            is_bnd = (t != FLUID);
+        }
+        const int slot = warp_append(&d.cnt->n_bnd, is_bnd);
+        if (is_bnd) d.bnd[slot] = k;
+    }
+}
+
+// ---------------------------------------------------------------------------- stages
+// Midpoint predictor-corrector from the base state of the step (the integrator of the
+// EDAC paper is not restated in this paper; this is the library's reading):
+//   fluid:  u = u^n + tau du/dt,  u~ = u + tau a_bg (Eq. transport-vel),
+//           x = x^n + tau u~ (Eq. advection),  p = p^n + tau dp/dt;  periodic axes wrap;
+//   inlet:  u = u(y), v = 0, x = x^n + tau u(y);
+//   outlet: x = x^n + tau u_adv (y fixed), fields frozen within the step.
+// The predictor (tau = dt/2) saves the base state; the corrector (tau = dt) also takes
+// the time-average sample of the hybrid outlet (Eqs. timeevg, acouinten) and forms J2.
+template <bool CORR>
+__global__ void k_stage(Dev d, double tau)
+{
+    const Geo &g = d.g;
+    const Phys &ph = d.ph;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.cap; s += gridDim.x * blockDim.x) {
+        const uint8_t t = d.tag[s];
+        if (t == FLUID) {
+            double x0, y0, u0, v0, p0;
+            if (!CORR) {
+                x0 = d.x[s]; y0 = d.y[s]; u0 = d.u[s]; v0 = d.v[s]; p0 = d.p[s];
+                d.x0[s] = x0; d.y0[s] = y0; d.u0[s] = u0; d.v0[s] = v0; d.p0[s] = p0;
+            } else {
+                x0 = d.x0[s]; y0 = d.y0[s]; u0 = d.u0[s]; v0 = d.v0[s]; p0 = d.p0[s];
+            }
+            const double un = u0 + tau * d.au[s];
+            const double vn = v0 + tau * d.av[s];
+            const double utn = un + tau * d.abu[s];
+            const double vtn = vn + tau * d.abv[s];
+            double xn = x0 + tau * utn;
+            double yn = y0 + tau * vtn;
+            if (g.px) { if (xn >= g.x_max) xn -= g.Lx; else if (xn < g.x_min) xn += g.Lx; }
+            if (g.py) { if (yn >= g.y_max) yn -= g.Ly; else if (yn < g.y_min) yn += g.Ly; }
+            const double pn = p0 + tau * d.ap[s];
+            d.u[s] = un; d.v[s] = vn; d.ut[s] = utn; d.vt[s] = vtn;
+            d.x[s] = xn; d.y[s] = yn; d.p[s] = pn;
+            if (!(isfinite(xn) && isfinite(yn) && isfinite(un) && isfinite(vn) && isfinite(pn) &&
+                  isfinite(utn) && isfinite(vtn)))
+                set_err(d, ERR_NONFINITE);
+            if (CORR && ph.has_outlet) {
+                double *rg = d.ring + (size_t)s * NAVG_MAX * 3;
+                const double inten = pn * pn / (2.0 * ph.rho0 * ph.cs);
+                if (inten <= ph.I_thr) {
+                    const int k = d.rpos[s];
+                    rg[3 * k + 0] = un; rg[3 * k + 1] = vn; rg[3 * k + 2] = pn;
+                    d.rpos[s] = (uint8_t)((k + 1) % ph.n_avg);
+                }
+                double su = 0.0, sv = 0.0, sp = 0.0;
+                for (int k = 0; k < ph.n_avg; ++k) {
+                    su += rg[3 * k + 0]; sv += rg[3 * k + 1]; sp += rg[3 * k + 2];
+                }
+                const double ub = su / (double)ph.n_avg, vb = sv / (double)ph.n_avg,
+                             pbv = sp / (double)ph.n_avg;
+                d.ubar[s] = ub; d.vbar[s] = vb; d.pbar[s] = pbv;
+                d.J2[s] = ph.rho0 * ph.cs * (un - ub) + (pn - pbv);
+            }
+        } else if (t == INLET) {
+            double x0;
+            if (!CORR) { x0 = d.x[s]; d.x0[s] = x0; } else { x0 = d.x0[s]; }
+            const double uin = inlet_u(ph, d.y[s]);
+            d.u[s] = uin; d.v[s] = 0.0; d.ut[s] = uin; d.vt[s] = 0.0;
+            d.x[s] = x0 + tau * uin;
+        } else if (t == OUTLET) {
+            double x0;
+            if (!CORR) { x0 = d.x[s]; d.x0[s] = x0; } else { x0 = d.x0[s]; }
+            d.x[s] = x0 + tau * d.advp[s];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------- recycling
+// Ring buffer of a particle that becomes fluid: all samples = current (u, v, p).
+__device__ __forceinline__ void ring_fill(const Dev &d, int s)
+{
+    double *rg = d.ring + (size_t)s * NAVG_MAX * 3;
+    const double u = d.u[s], v = d.v[s], p = d.p[s];
+    for (int k = 0; k < d.ph.n_avg; ++k) { rg[3 * k] = u; rg[3 * k + 1] = v; rg[3 * k + 2] = p; }
+    d.rpos[s] = 0;
+    d.ubar[s] = u; d.vbar[s] = v; d.pbar[s] = p; d.J2[s] = 0.0;
+}
+
+// Transitions of the end of Sec. 3.4, taken once per step after the outlet update:
+// outlet past x_out + L_out -> deleted; fluid past x_out -> outlet (keeps its time
+// averages); inlet past x_in -> fluid (a new inlet particle is spawned by k_end_step).
+// Events go to per-kind lists by warp-aggregated appends; k_end_step puts them in
+// ascending id order before ids and slots are handed out.
+__global__ void k_recycle_mark(Dev d)
+{
+    const Phys &ph = d.ph;
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x; base < d.cap; base += stride) {
+        const int s = base + threadIdx.x;
+        bool del = false, out = false, spawn = false;
+        if (s < d.cap) {
+            const uint8_t t = d.tag[s];
+            if (t == OUTLET && ph.has_outlet) {
+                del = d.x[s] >= ph.x_out + ph.L_out;
+            } else if (t == FLUID && ph.has_outlet) {
+                out = d.x[s] >= ph.x_out;
+            } else if (t == INLET && ph.has_inlet) {
+                spawn = d.x[s] >= ph.x_in;
+            }
+        }
+        const int idel = warp_append(&d.cnt->n_del, del);
+        const int iout = warp_append(&d.cnt->n_out, out);
+        const int ispw = warp_append(&d.cnt->n_spawn, spawn);
+        if (del) {
+            d.tag[s] = TAG_DEAD;
+            if (idel < LIST_MAX) { d.ev_del_key[idel] = d.id[s]; d.ev_del_slot[idel] = s; }
+            else set_err(d, ERR_LIST);
+        }
+        if (out) {
+            d.tag[s] = OUTLET;
+            const double ub = d.ubar[s];
+            d.u[s] = ub; d.v[s] = d.vbar[s]; d.p[s] = d.pbar[s];
+            d.ut[s] = ub; d.vt[s] = d.vbar[s];
+            d.J2p[s] = 0.0; d.redp[s] = 0; d.advp[s] = ub;
+            if (iout < LIST_MAX) { d.ev_out_key[iout] = d.id[s]; d.ev_out_m[iout] = d.m[s]; }
+            else set_err(d, ERR_LIST);
+        }
+        if (spawn) {
+            d.tag[s] = FLUID;
+            ring_fill(d, s);
+            if (ispw < LIST_MAX) { d.ev_spawn_key[ispw] = d.id[s]; d.ev_spawn_slot[ispw] = s; }
+            else set_err(d, ERR_LIST);
+        }
+    }
+}
+
+// rank of key[i] among key[0..n) (keys are unique particle ids)
+__device__ __forceinline__ int rank_of(const unsigned long long *key, int n, int i)
+{
+    const unsigned long long k = key[i];
+    int r = 0;
+    for (int j = 0; j < n; ++j) r += (key[j] < k);
+    return r;
+}
+
+__device__ double block_sum_1024(double v, double *sh)
+{
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (t < o) sh[t] += sh[t + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// End of a step, one block of 1024 threads: the drag/lift sum over the solid particles
+// (Eq. tvf-momentum_solid summed over the body; fixed-shape tree), the canonical
+// ordering of the recycling events, slot and id hand-out for spawned inlet particles
+// (ascending parent id), the mass flux, and one history record.
+__global__ void __launch_bounds__(1024) k_end_step(Dev d, double *scratch_m)
+{
+    __shared__ double sh[1024];
+    Counters *C = d.cnt;
+    const int t = threadIdx.x;
+    const Phys &ph = d.ph;
+    // forces
+    double fx = 0.0, fy = 0.0;
+    for (int i = t; i < C->n_drag; i += 1024) {
+        const int s = d.drag_slots[i];
+        fx += d.fx[s];
+        fy += d.fy[s];
+    }
+    fx = block_sum_1024(fx, sh);
+    fy = block_sum_1024(fy, sh);
+    const int n_del = min(C->n_del, LIST_MAX);
+    const int n_out = min(C->n_out, LIST_MAX);
+    const int n_spawn = min(C->n_spawn, LIST_MAX);
+    // mass flux: converted masses summed in ascending id order
+    for (int i = t; i < n_out; i += 1024) scratch_m[rank_of(d.ev_out_key, n_out, i)] = d.ev_out_m[i];
+    __syncthreads();
+    double ms = 0.0;
+    for (int i = t; i < n_out; i += 1024) ms += scratch_m[i];
+    ms = block_sum_1024(ms, sh);
+    // freed slots pushed in ascending id order
+    const int top0 = C->free_top;
+    for (int i = t; i < n_del; i += 1024) {
+        const int r = rank_of(d.ev_del_key, n_del, i);
+        d.free_stack[top0 + r] = d.ev_del_slot[i];
+    }
+    __syncthreads();
+    const int top1 = top0 + n_del;
+    const int n_new = min(n_spawn, top1);
+    const unsigned long long id0 = C->next_id;
+    for (int i = t; i < n_spawn; i += 1024) {
+        const int r = rank_of(d.ev_spawn_key, n_spawn, i);
+        if (r >= n_new) continue;
+        const int ps = d.ev_spawn_slot[i];
+        const int s = d.free_stack[top1 - 1 - r];
+        const double yv = d.y[ps];
+        const double uin = inlet_u(ph, yv);
+        d.x[s] = d.x[ps] - ph.L_in;
+        d.y[s] = yv;
+        d.u[s] = uin; d.v[s] = 0.0; d.ut[s] = uin; d.vt[s] = 0.0;
+        d.p[s] = d.p[ps];
+        d.m[s] = d.m[ps];
+        d.id[s] = id0 + (unsigned long long)r;
+        d.au[s] = d.av[s] = d.ap[s] = d.abu[s] = d.abv[s] = 0.0;
+        d.fx[s] = d.fy[s] = 0.0;
+        d.rho[s] = d.vol[s] = 0.0;
+        d.nnb[s] = 0;
+        d.rpos[s] = 0;
+        d.ubar[s] = d.vbar[s] = d.pbar[s] = d.J2[s] = 0.0;
+        d.J2p[s] = d.advp[s] = 0.0;
+        d.redp[s] = 0;
+        d.x0[s] = d.y0[s] = d.u0[s] = d.v0[s] = d.p0[s] = 0.0;
+        __threadfence();
+        d.tag[s] = INLET;
+    }
+    __syncthreads();
+    if (t == 0) {
+        if (n_new < n_spawn) atomicOr(&C->err, ERR_CAPACITY);
+        C->free_top = top1 - n_new;
+        C->next_id = id0 + (unsigned long long)n_new;
+        C->n_alive = C->n_alive - n_del + n_new;
+        const int slot = C->step % d.max_history;
+        double *h = d.hist + (size_t)slot * 8;
+        h[0] = fx; h[1] = fy; h[2] = ms / ph.dt; h[3] = (double)C->n_alive;
+        h[4] = (double)n_spawn; h[5] = (double)n_del; h[6] = (double)n_out; h[7] = 0.0;
+        C->step += 1;
+        C->hist_len = min(C->hist_len + 1, d.max_history);
+        C->n_del = 0; C->n_out = 0; C->n_spawn = 0;
+    }
+}
+
+// Set-up after an upload: u~ = u, ring buffers and outlet memory from the initial fields.
+__global__ void k_init(Dev d)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.cap; s += gridDim.x * blockDim.x) {
+        if (d.tag[s] == TAG_DEAD) continue;
+        d.ut[s] = d.u[s];
+        d.vt[s] = d.v[s];
+        ring_fill(d, s);
+        d.J2p[s] = 0.0;
+        d.redp[s] = 0;
+        d.advp[s] = d.u[s];
+        d.au[s] = d.av[s] = d.ap[s] = d.abu[s] = d.abv[s] = 0.0;
+        d.fx[s] = d.fy[s] = 0.0;
+        d.x0[s] = d.x[s]; d.y0[s] = d.y[s]; d.u0[s] = d.u[s]; d.v0[s] = d.v[s]; d.p0[s] = d.p[s];
+    }
+}
+
+int grid_for(int n)
+{
+    int b = (n + TPB - 1) / TPB;
+    return b < 1 ? 1 : b;
+}
+
+}  // namespace
+
+// cell_count is all zero on entry: cleared by the workspace reset at upload and by
+// k_cell_sort of the previous build.
+int launch_rebuild(const Dev &d, cudaStream_t s, int mixed)
+{
+    k_cell_count<<<grid_for(d.cap), TPB, 0, s>>>(d);
+    k_cell_scan<<<1, 1024, 0, s>>>(d);
+    k_cell_scatter<<<grid_for(d.cap), TPB, 0, s>>>(d);
+    k_cell_sort<<<grid_for(d.g.ncells), TPB, 0, s>>>(d);
+    if (mixed) k_gather<1><<<grid_for(d.cap), TPB, 0, s>>>(d);
+    else k_gather<0><<<grid_for(d.cap), TPB, 0, s>>>(d);
+    return 5;
+}
+
+int launch_stage(const Dev &d, cudaStream_t s, int corrector)
+{
+    if (corrector) k_stage<true><<<grid_for(d.cap), TPB, 0, s>>>(d, d.ph.dt);
+    else k_stage<false><<<grid_for(d.cap), TPB, 0, s>>>(d, 0.5 * d.ph.dt);
+    return 1;
+}
+
+int launch_recycle(const Dev &d, cudaStream_t s)
+{
+    k_recycle_mark<<<grid_for(d.cap), TPB, 0, s>>>(d);
+    k_end_step<<<1, 1024, 0, s>>>(d, d.scratch_m);
+    return 2;
+}
+
+int launch_init(const Dev &d, cudaStream_t s)
+{
+    k_init<<<grid_for(d.cap), TPB, 0, s>>>(d);
+    return 1;
+}
+
+}  // namespace edac

@@ -1,0 +1,250 @@
+// Internal declarations of the EDAC SPH library: device-side parameter and
+// pointer bundles, the quintic-kernel and neighbour-walk device helpers shared
+// by the pair kernels, and the host launchers.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace edac {
+
+constexpr int NAVG_MAX = 8;       // longest time-average window of the hybrid outlet
+constexpr int MAX_MODES = 16;     // inlet profile modes
+constexpr int LIST_MAX = 16384;   // recycling events per step (per kind)
+constexpr uint8_t TAG_DEAD = 255; // free slot
+constexpr uint8_t TAG_REDP = 0x80; // sorted-tag flag: outlet particle red in the previous step
+
+enum : uint8_t { FLUID = 0, INLET = 1, OUTLET = 2, WALL = 3, SLIPWALL = 4 };
+
+// sticky device error bits
+enum : unsigned { ERR_CAPACITY = 1u, ERR_NONFINITE = 2u, ERR_DOMAIN = 4u, ERR_LIST = 8u,
+                  ERR_TIMEOUT = 16u };
+
+// Geometry of the cell grid and the support radius.
+struct Geo {
+    double x_min, x_max, y_min, y_max;
+    double Lx, Ly, hLx, hLy;  // box lengths and halves (minimum image)
+    int px, py;               // periodic axes
+    int nx, ny, ncells;
+    double sx, sy, inv_sx, inv_sy;
+    float sxf, syf;
+    double rc2;               // (3h)^2, the membership bound
+    float rc2_lo, rc2_hi;     // fp32 pre-test band around rc2
+};
+
+// Physical and zone parameters.
+struct Phys {
+    double h, inv_h, a2, a2h;        // alpha_2 = 7/(478 pi h^2), alpha_2 / h
+    double rho0, cs, c2, nu, nu_e, eh2, pb, gx, gy, dt, U;
+    float inv_hf, a2f, a2hf, c2f, nuf, nuef, eh2f;
+    int use_pavg;
+    int has_inlet, n_modes;
+    double x_in, L_in, in_y0, in_H;
+    double modes[MAX_MODES];
+    int has_outlet, n_avg;
+    double x_out, L_out, I_thr;
+    int wall_slip[2], wall_drag[2];
+    double wall_u[2], wall_v[2];
+};
+
+// Device counters (one struct in the workspace).
+struct Counters {
+    int n_alive;     // live particles
+    int n_bnd;       // boundary particles in the sorted order (rebuilt each gather)
+    int free_top;    // free-slot stack height
+    int n_spawn, n_del, n_out;  // recycling events of the current step
+    unsigned err;    // sticky error word
+    int step;        // completed steps
+    int n_drag;      // solid particles in the drag sum (static)
+    int hist_len;    // history records written (saturates at max_history)
+    unsigned long long next_id;
+};
+
+// Everything a kernel may touch.
+struct Dev {
+    Geo g;
+    Phys ph;
+    int cap;
+    int max_history;
+    Counters *cnt;
+    // master particle state, slot-indexed [cap]
+    double *x, *y, *u, *v, *ut, *vt, *p, *m;
+    double *x0, *y0, *u0, *v0, *p0;
+    double *au, *av, *ap, *abu, *abv, *fx, *fy, *rho, *vol;
+    int *nnb;
+    uint8_t *tag;
+    unsigned long long *id;
+    double *ring;   // [cap][NAVG_MAX][3]
+    uint8_t *rpos;
+    double *ubar, *vbar, *pbar, *J2, *J2p, *advp;
+    uint8_t *redp;
+    // cell list
+    int *cell_count;   // [ncells]
+    int *cell_start;   // [ncells + 1]
+    int *slot_cell;    // [cap]
+    int *within;       // [cap]
+    // sorted (cell-ordered) copies, index k < n_alive
+    int *order;        // slot of k
+    int *cellk;        // cell of k
+    uint8_t *stag;     // tag of k (| TAG_REDP)
+    float4 *P;         // (x - cell x0, y - cell y0, m, 0) fp32, both paths
+    double2 *XY;       // fp64 position
+    double2 *AUX;      // (J2 of fluid | J2 of outlet previous step, outlet advection velocity)
+    int *snnb;         // neighbour count N_k
+    // fp64 path
+    double2 *UV, *DUV; // (u, v), (u~ - u, v~ - v)
+    double2 *PV;       // (p, V)
+    double2 *RM;       // (rho, m / rho)
+    double *Ms;        // m
+    // mixed path
+    float4 *Bf;        // (u, v, u~ - u, v~ - v)
+    float4 *Qf;        // (p, V, rho, m / rho)
+    int *bnd;          // boundary particles (sorted index), n_bnd of them
+    // recycling
+    int *free_stack;   // [cap]
+    unsigned long long *ev_spawn_key; int *ev_spawn_slot;   // [LIST_MAX]
+    unsigned long long *ev_del_key;   int *ev_del_slot;     // [LIST_MAX]
+    unsigned long long *ev_out_key;   double *ev_out_m;     // [LIST_MAX]
+    int *drag_slots;   // [n_drag], ascending slot
+    double *scratch_m; // [LIST_MAX]
+    double *hist;      // [max_history][8]
+};
+
+// -------------------------------------------------------------------------------------------
+// Quintic spline (Eq. quintic-spline) in the branch-free form: with t_k = max(0, k - q),
+//   w(q) = t3^5 - 6 t2^5 + 15 t1^5,   dw/dq = -5 (t3^4 - 6 t2^4 + 15 t1^4),
+// which equals the paper's piecewise definition on every branch (t_k vanishes where the
+// corresponding term is absent).  W = alpha_2 w(q), dW/dr = (alpha_2 / h) dw/dq.
+// -------------------------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T quintic_w(T q)
+{
+    T t3 = q < T(3) ? T(3) - q : T(0);
+    T t2 = q < T(2) ? T(2) - q : T(0);
+    T t1 = q < T(1) ? T(1) - q : T(0);
+    T a = t3 * t3, b = t2 * t2, c = t1 * t1;
+    return t3 * a * a - T(6) * (t2 * b * b) + T(15) * (t1 * c * c);
+}
+
+template <class T>
+__device__ __forceinline__ T quintic_dw(T q)
+{
+    T t3 = q < T(3) ? T(3) - q : T(0);
+    T t2 = q < T(2) ? T(2) - q : T(0);
+    T t1 = q < T(1) ? T(1) - q : T(0);
+    T a = t3 * t3, b = t2 * t2, c = t1 * t1;
+    return T(-5) * (a * a - T(6) * (b * b) + T(15) * (c * c));
+}
+
+// Canonical fp64 separation r_i - r_j with the minimum image on periodic axes and
+// r^2 = dx*dx + dy*dy evaluated without fused multiply-add: the membership test
+// r^2 < (3h)^2 is decided by exactly this operation sequence.
+__device__ __forceinline__ double exact_r2(const Geo &g, double xi, double yi, double xj,
+                                          double yj, double &dx, double &dy)
+{
+    dx = xi - xj;
+    if (g.px) {
+        if (dx > g.hLx) dx = dx - g.Lx;
+        else if (dx < -g.hLx) dx = dx + g.Lx;
+    }
+    dy = yi - yj;
+    if (g.py) {
+        if (dy > g.hLy) dy = dy - g.Ly;
+        else if (dy < -g.hLy) dy = dy + g.Ly;
+    }
+    return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+}
+
+__device__ __forceinline__ int cell_coord(double v, double lo, double inv_s, int n)
+{
+    int c = (int)floor((v - lo) * inv_s);
+    return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+
+// Walk the exact neighbours j of a query point (fp64 position qx, qy; cell (cx, cy);
+// fp32 position relative to that cell's origin rx, ry).  An fp32 pre-test on
+// cell-relative coordinates rejects or accepts pairs far from the support
+// boundary; pairs inside the band |r^2 - rc^2| <~ 4e-5 rc^2 are decided by exact_r2.
+// f(j, dx32, dy32, r2_32, exact_dx, exact_dy, exact_r2, have_exact) is called for every
+// neighbour; have_exact says whether the fp64 values were computed.
+// NEED_EXACT = true computes the fp64 separation for every accepted pair (fp64 path).
+template <bool NEED_EXACT, class F>
+__device__ __forceinline__ void for_neighbors(const Dev &d, double qx, double qy, int cx, int cy,
+                                              float rx, float ry, F &&f)
+{
+    const Geo &g = d.g;
+#pragma unroll 1
+    for (int oy = -1; oy <= 1; ++oy) {
+        int by = cy + oy;
+        if (g.py) by = by < 0 ? by + g.ny : (by >= g.ny ? by - g.ny : by);
+        else if (by < 0 || by >= g.ny) continue;
+        const float offy = (float)oy * g.syf;
+#pragma unroll 1
+        for (int ox = -1; ox <= 1; ++ox) {
+            int bx = cx + ox;
+            if (g.px) bx = bx < 0 ? bx + g.nx : (bx >= g.nx ? bx - g.nx : bx);
+            else if (bx < 0 || bx >= g.nx) continue;
+            const float offx = (float)ox * g.sxf;
+            const int c = by * g.nx + bx;
+            const int j0 = __ldg(d.cell_start + c), j1 = __ldg(d.cell_start + c + 1);
+            f.begin_cell();
+#pragma unroll 1
+            for (int j = j0; j < j1; ++j) {
+                const float4 pj = __ldg(d.P + j);
+                const float dxf = rx - (pj.x + offx);
+                const float dyf = ry - (pj.y + offy);
+                const float r2f = dxf * dxf + dyf * dyf;
+                if (r2f >= g.rc2_hi) continue;
+                double edx = 0.0, edy = 0.0, er2 = 0.0;
+                bool have = false;
+                if (NEED_EXACT || r2f > g.rc2_lo) {
+                    const double2 xy = d.XY[j];
+                    er2 = exact_r2(g, qx, qy, xy.x, xy.y, edx, edy);
+                    if (!(er2 < g.rc2)) continue;
+                    have = true;
+                }
+                f(j, dxf, dyf, r2f, edx, edy, er2, have, pj);
+            }
+            f.end_cell();
+        }
+    }
+}
+
+// Error-free transformation a + b = s + e (Knuth two-sum), used to fold per-cell partial
+// sums into compensated accumulators in the fp32 pair passes.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b)
+{
+    float s = hi + b;
+    float z = s - hi;
+    float e = (hi - (s - z)) + (b - z);
+    hi = s;
+    lo += e;
+}
+
+__device__ __forceinline__ void set_err(const Dev &d, unsigned bits)
+{
+    atomicOr(&d.cnt->err, bits);
+}
+
+// Inlet profile u(y) = U + sum_k a_k sin(k pi (y - y0) / H).
+__device__ __forceinline__ double inlet_u(const Phys &ph, double y)
+{
+    double u = ph.U;
+    for (int k = 0; k < ph.n_modes; ++k)
+        u += ph.modes[k] * sin((double)(k + 1) * 3.141592653589793 * (y - ph.in_y0) / ph.in_H);
+    return u;
+}
+
+// ------------------------------------------------------------------- host-side launchers
+// Every launcher issues its kernels on `s` and returns the number of launches issued.
+int launch_rebuild(const Dev &d, cudaStream_t s, int mixed);
+int launch_pass_a(const Dev &d, cudaStream_t s, int mixed);
+int launch_boundary(const Dev &d, cudaStream_t s, int mixed, int end_of_step);
+int launch_pass_b(const Dev &d, cudaStream_t s, int mixed);
+int launch_stage(const Dev &d, cudaStream_t s, int corrector);
+int launch_recycle(const Dev &d, cudaStream_t s);
+int launch_init(const Dev &d, cudaStream_t s);
+int launch_neighbor_dump(const Dev &d, cudaStream_t s, int mixed, const long long *start,
+                         unsigned long long *ids);
+
+}  // namespace edac

@@ -1,0 +1,75 @@
+"""The C-ABI library: it loads, exports every symbol include/edac.h declares, and
+validates parameters on the host (no GPU call is made by these tests)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1907_04034_gb300 import binding, cases
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "edac.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(edac_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    binding.build()
+    return binding.load()
+
+
+def test_header_and_binding_agree():
+    assert _declared() == sorted(binding.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    out = os.popen(f"nm -D --defined-only {binding.LIB}").read()
+    for name in _declared():
+        assert re.search(rf"\bT {name}\b", out), name
+
+
+def _params(**kw):
+    c = cases.channel()
+    p = binding.make_params(c.params, binding.EDAC_FP64, c.capacity, 16, True, 0)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def test_workspace_size_for_valid_params(lib):
+    n = C.c_size_t(0)
+    assert lib.edac_workspace_bytes(C.byref(_params()), C.byref(n)) == 0
+    # at least the fp64 master state (~300 B per slot)
+    assert n.value > 300 * cases.channel().capacity
+    m = C.c_size_t(0)
+    assert lib.edac_workspace_bytes(C.byref(_params(precision=binding.EDAC_MIXED)), C.byref(m)) == 0
+    assert m.value < n.value
+
+
+@pytest.mark.parametrize("bad", [dict(dx=0.0), dict(dt=-1.0), dict(x_max=-1.0), dict(precision=7),
+                                 dict(capacity=0), dict(eta_reg=0.0), dict(nu=float("nan")),
+                                 dict(y_max=0.1)])
+def test_invalid_params_are_rejected(lib, bad):
+    n = C.c_size_t(0)
+    assert lib.edac_workspace_bytes(C.byref(_params(**bad)), C.byref(n)) == 1
+
+
+def test_create_rejects_missing_or_small_workspace(lib):
+    ctx = C.c_void_p()
+    p = _params()
+    assert lib.edac_create(C.byref(p), None, 0, C.byref(ctx)) == 1
+    assert lib.edac_create(C.byref(p), C.c_void_p(4096), 16, C.byref(ctx)) == 1
+    assert lib.edac_create(C.byref(p), C.c_void_p(4096 + 8), 1 << 40, C.byref(ctx)) == 1
+    assert not ctx.value
+
+
+def test_null_context_is_an_error(lib):
+    assert lib.edac_step(None, 1) == 1
+    assert lib.edac_last_error(None) == b"NULL context"

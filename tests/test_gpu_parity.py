@@ -1,0 +1,296 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Tolerances (the bar of the path): the fp64 path agrees with the oracle to 1e-10 and
+the mixed path (fp32 pair sums on cell-relative coordinates, fp64 integration) to
+1e-4, both as max|gpu - oracle| / max(max|oracle|, scale) per field, where scale is
+the field's natural size (domain length for positions, U for velocities, rho0 U^2/2
+for pressure, rho0 for density).  Neighbour sets, particle ids, tags and the
+recycling events are compared bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_04034_gb300 import binding, cases
+from paper_1907_04034_gb300.cases import FLUID, INLET, OUTLET, WALL, SLIPWALL
+
+TOL = {"fp64": 1e-10, "mixed": 1e-4}
+PRECS = ("fp64", "mixed")
+
+# (gpu field, oracle field, scale floor)
+EVAL_FIELDS = [("x", "x", 1.0), ("y", "y", 1.0), ("u", "u", 1.0), ("v", "v", 1.0),
+               ("p", "p", 0.5), ("rho", "rho", 1.0), ("vol", "V", 0.0), ("au", "au", 0.0),
+               ("av", "av", 0.0), ("ap", "ap", 0.0), ("abu", "abu", 0.0), ("abv", "abv", 0.0),
+               ("fx", "fx", 0.0), ("fy", "fy", 0.0)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    binding.build()
+    yield
+
+
+def _rel_err(g, r, floor):
+    den = max(float(np.abs(r).max()) if r.size else 0.0, floor, 1e-300)
+    return float(np.abs(g - r).max()) / den if r.size else 0.0
+
+
+def compare_eval(solver, ref, prec, extra_tol=1.0):
+    names = [f for f, _, _ in EVAL_FIELDS] + ["nnb"]
+    g = solver.state(names)
+    r = ref.fields()
+    np.testing.assert_array_equal(g["id"], r["id"])
+    np.testing.assert_array_equal(g["tag"], r["tag"])
+    np.testing.assert_array_equal(g["nnb"].astype(np.int64), r["nnb"].astype(np.int64))
+    errs = {}
+    for gf, rf, floor in EVAL_FIELDS:
+        errs[gf] = _rel_err(g[gf], r[rf], floor)
+    bad = {k: v for k, v in errs.items() if not v < TOL[prec] * extra_tol}
+    assert not bad, f"{prec}: fields beyond tolerance {bad}"
+    return errs
+
+
+def _small_cases():
+    return {
+        "channel": lambda: cases.channel(),
+        "random_periodic": lambda: cases.random_box(n=500, seed=11),
+        "random_open": lambda: cases.random_box(n=400, seed=12, periodic_y=0),
+        "taylor_green": lambda: cases.taylor_green(n=24, jitter=0.2, seed=4),
+        "poiseuille": lambda: cases.poiseuille(n=12),
+        "cylinder_coarse": lambda: cases.cylinder(dx=1.0 / 8.0, Lx=6.0, H=4.0, xc=2.0),
+    }
+
+
+# --------------------------------------------------------------------- one evaluation
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", list(_small_cases()))
+def test_one_evaluation_matches_oracle(prec, name):
+    c = _small_cases()[name]()
+    ref = oracle.OracleSim(c)
+    s = binding.Solver(c, precision=prec)
+    compare_eval(s, ref, prec)
+    s.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", ["channel", "random_periodic", "random_open", "cylinder_coarse"])
+def test_neighbor_sets_bit_exact(prec, name):
+    c = _small_cases()[name]()
+    ref = oracle.OracleSim(c)
+    rs, ri = ref.neighbors()
+    rid = ref.field("id")
+    s = binding.Solver(c, precision=prec)
+    gs, gi = s.neighbors()
+    s.close()
+    assert len(gs) == len(rs)
+    for i in range(len(rs) - 1):
+        want = np.sort(rid[ri[rs[i]:rs[i + 1]]])
+        np.testing.assert_array_equal(gi[gs[i]:gs[i + 1]], want)
+
+
+# ------------------------------------------------------------------------ step windows
+def _compare_window(s, ref, prec, tol_mult=1.0):
+    g = s.state(("x", "y", "u", "v", "p", "rho", "au", "ap"))
+    r = ref.fields()
+    np.testing.assert_array_equal(g["id"], r["id"])
+    np.testing.assert_array_equal(g["tag"], r["tag"])
+    errs = {k: _rel_err(g[k], r[k], f) for k, f in
+            (("x", 1.0), ("y", 1.0), ("u", 1.0), ("v", 1.0), ("p", 0.5), ("rho", 1.0))}
+    bad = {k: v for k, v in errs.items() if not v < TOL[prec] * tol_mult}
+    assert not bad, f"{prec}: {bad}"
+    return errs
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+def test_channel_200_steps(prec):
+    """The pulse channel (1450 particles, 200 steps) through inlet, fluid and hybrid outlet."""
+    c = cases.channel()
+    ref = oracle.OracleSim(c)
+    s = binding.Solver(c, precision=prec)
+    for _ in range(4):
+        ref.step(50)
+        s.step(50)
+        _compare_window(s, ref, prec)
+    h = s.history()
+    rh = ref.history
+    assert len(h["n_active"]) == 200
+    for k in ("n_active", "n_spawn", "n_delete", "n_to_outlet"):
+        np.testing.assert_array_equal(h[k], [x[k] for x in rh])
+    assert sum(h["n_spawn"]) > 0 and sum(h["n_to_outlet"]) > 0
+    mf = np.array([x["mass_flux"] for x in rh])
+    assert np.abs(h["mass_flux"] - mf).max() <= 1e-12 * max(1.0, np.abs(mf).max())
+    s.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+def test_gated_pulse_channel(prec):
+    """Pulse amplitude 1 trips the acoustic-intensity gate; 150 steps."""
+    c = cases.channel(pulse_amp=1.0, pulse_xy=(0.8, 0.25))
+    ref = oracle.OracleSim(c)
+    s = binding.Solver(c, precision=prec)
+    ref.step(150)
+    s.step(150)
+    _compare_window(s, ref, prec)
+    g = s.state(("ubar", "pbar", "J2", "rpos"))
+    r = ref.fields(("ubar", "pbar", "J2", "rpos", "tag"))
+    fl = r["tag"] == FLUID
+    np.testing.assert_array_equal(g["rpos"][fl].astype(int), r["rpos"][fl])
+    assert _rel_err(g["pbar"][fl], r["pbar"][fl], 0.5) < TOL[prec]
+    assert _rel_err(g["J2"][fl], r["J2"][fl], 1.0) < TOL[prec] * 10
+    s.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+def test_cylinder_coarse_window(prec):
+    """Cylinder with solid rings, slip walls, inlet and outlet: 60 steps and the drag."""
+    c = cases.cylinder(dx=1.0 / 8.0, Lx=6.0, H=4.0, xc=2.0)
+    ref = oracle.OracleSim(c, neighbor_mode=1)
+    s = binding.Solver(c, precision=prec)
+    ref.step(60)
+    s.step(60)
+    _compare_window(s, ref, prec)
+    h = s.history()
+    fx = np.array([x["fx"] for x in ref.history])
+    fy = np.array([x["fy"] for x in ref.history])
+    scale = max(np.abs(fx).max(), 1e-3)
+    assert np.abs(h["fx"] - fx).max() / scale < TOL[prec] * 10
+    assert np.abs(h["fy"] - fy).max() / scale < TOL[prec] * 10
+    s.close()
+
+
+@pytest.mark.gpu
+def test_graph_replay_equals_eager_launches():
+    c = cases.channel()
+    a = binding.Solver(c, precision="fp64", use_graphs=True)
+    b = binding.Solver(c, precision="fp64", use_graphs=False)
+    a.step(30)
+    b.step(30)
+    ga = a.state(("x", "y", "u", "p"))
+    gb = b.state(("x", "y", "u", "p"))
+    for k in ga:
+        np.testing.assert_array_equal(ga[k], gb[k])
+    a.close()
+    b.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+def test_runs_are_bitwise_reproducible(prec):
+    c = cases.random_box(n=600, seed=21)
+    out = []
+    for _ in range(2):
+        s = binding.Solver(c, precision=prec)
+        s.step(20)
+        out.append(s.state(("x", "y", "u", "v", "p")))
+        s.close()
+    for k in out[0]:
+        np.testing.assert_array_equal(out[0][k], out[1][k])
+
+
+# ------------------------------------------------------------------- full-size cases
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+def test_cylinder_dx40_window(prec):
+    """~245k-particle cylinder (dx = D/40): 20-step window against the binned oracle."""
+    c = cases.cylinder(dx=1.0 / 40.0)
+    ref = oracle.OracleSim(c, neighbor_mode=1)
+    s = binding.Solver(c, precision=prec)
+    compare_eval(s, ref, prec)
+    ref.step(20)
+    s.step(20)
+    _compare_window(s, ref, prec)
+    s.close()
+
+
+@pytest.mark.gpu
+def test_cylinder_dx100_one_step_full_size():
+    """The 1.5M-particle cylinder in the benchmark's configuration (mixed, graphs): the
+    initial evaluation and one step against the binned oracle, every particle."""
+    c = cases.cylinder(dx=1.0 / 100.0)
+    ref = oracle.OracleSim(c, neighbor_mode=1)
+    s = binding.Solver(c, precision="mixed", use_graphs=True)
+    compare_eval(s, ref, "mixed")
+    ref.step(1)
+    s.step(1)
+    _compare_window(s, ref, "mixed")
+    s.close()
+
+
+# ----------------------------------------------------------------- edge cases / errors
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+def test_empty_system(prec):
+    c = cases.random_box(n=50, seed=1)
+    s = binding.Solver(c, precision=prec)
+    empty = cases.Case("empty", c.params, *(np.zeros(0) for _ in range(6)),
+                       np.zeros(0, dtype=np.uint8), np.zeros(0, dtype=np.uint64), capacity=c.capacity)
+    s.upload(empty)
+    s.step(3)
+    assert s.count() == 0
+    st = s.state(("x",))
+    assert st["x"].size == 0
+    s.close()
+
+
+@pytest.mark.gpu
+def test_capacity_overflow_is_reported():
+    c = cases.channel()
+    s = binding.Solver(c, precision="fp64", capacity=c.n)  # no headroom for spawned inlet particles
+    s.step(60)
+    with pytest.raises(binding.EdacError) as e:
+        s.count()
+    assert e.value.code == 2
+    with pytest.raises(binding.EdacError) as e:
+        s.step(1)
+    assert e.value.code == 6
+    s.upload(c)  # re-initialisation clears the error
+    s.close()
+
+
+@pytest.mark.gpu
+def test_nonfinite_is_reported():
+    c = cases.taylor_green(n=16)
+    c.params.gx = 1e308
+    s = binding.Solver(c, precision="fp64")
+    s.step(2)
+    with pytest.raises(binding.EdacError) as e:
+        s.state(("x",))
+    assert e.value.code == 4
+    s.close()
+
+
+@pytest.mark.gpu
+def test_particle_leaving_the_box_is_reported():
+    c = cases.random_box(n=200, seed=5, periodic_y=0, tags=(FLUID,))
+    c.v[:] = 0.0
+    c.v[0] = 1e4  # leaves the box within a step
+    s = binding.Solver(c, precision="fp64")
+    s.step(1)
+    with pytest.raises(binding.EdacError) as e:
+        s.count()
+    assert e.value.code == 7
+    s.close()
+
+
+@pytest.mark.gpu
+def test_bad_uploads_are_rejected_on_the_host():
+    c = cases.random_box(n=100, seed=2)
+    s = binding.Solver(c, precision="fp64")
+    bad = cases.random_box(n=100, seed=2)
+    bad.id[3] = bad.id[4]
+    with pytest.raises(binding.EdacError) as e:
+        s.upload(bad)
+    assert e.value.code == 1
+    bad = cases.random_box(n=100, seed=2)
+    bad.x[0] = 99.0
+    with pytest.raises(binding.EdacError) as e:
+        s.upload(bad)
+    assert e.value.code == 7
+    s.close()
