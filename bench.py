@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark: EDAC particle-steps/s on the 1.5M-particle cylinder (Re = 200, dx = D/100).
+
+One step = the whole per-step particle pass (two cell builds, two evaluations of pass A,
+the boundary kernel and pass B, two integrator stages, the hybrid-outlet update,
+recycling, the drag reduction) on device-resident state.  The headline value is the
+mixed-precision path (fp32 pair sums on cell-relative coordinates, fp64 integration and
+reductions); the fp64 path and the drag difference between the two are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun, one rank per GPU) runs N independent replicas of the workload: the path
+does not shard (one GPU per system), so value = particle-steps of all ranks / max time.
+--impl reference times the CPU oracle (the plain fp64 statement of the method) on the
+host cores on the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EDAC particle-steps/s (1.5M cyl), mixed vs FP64 at stated err; adjoint/fwd time"
+UNIT = "particle-steps/s"
+WORKLOAD = "cylinder Re=200, 15D x 10D channel, dx=D/100 (~1.5M particles), hybrid outlet"
+
+# Algorithmic flops per neighbour pair of the two pair passes (counted from the formulas:
+# each add, multiply, divide, square root or comparison-select is one flop).
+FLOPS_PER_PAIR_A = 21
+FLOPS_PER_PAIR_B = 88
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--dx", type=float, default=0.01)
+    ap.add_argument("--fp64-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------ ranks
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = os.environ.get("BENCH_BACKEND", "nccl")
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local, dist
+
+
+def reduce_max_sum(dist, t, n, device=None):
+    """(max over ranks of t, sum over ranks of n); identity without a process group."""
+    if dist is None:
+        return float(t), float(n)
+    import torch
+    a = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    b = torch.tensor([float(n)], dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(a.item()), float(b.item())
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ peaks
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_count, max_mhz):
+    """FP32 FMA pipe: 128 lanes per SM, 2 flops per FMA, at the maximum SM clock."""
+    return sm_count * 128 * 2 * max_mhz * 1e6 / 1e12
+
+
+# -------------------------------------------------------------------------- reference
+def cpu_oracle_rate(case, steps):
+    """The oracle as it stands (binned neighbour mode, OpenMP on all host cores)."""
+    import oracle
+    t0 = time.perf_counter()
+    sim = oracle.OracleSim(case, neighbor_mode=1)
+    t_init = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = sim.step(steps)
+    dt = time.perf_counter() - t0
+    ps = float(sum(h["n_active"] for h in hist))
+    return ps / dt, dt, t_init
+
+
+def run_reference(args, rank, world, dist):
+    from paper_1907_04034_gb300 import cases
+    if rank != 0:
+        return
+    case = cases.cylinder(dx=args.dx)
+    k = max(1, min(args.steps, args.cpu_steps))
+    w = min(args.warmup, 1)
+    import oracle
+    sim = oracle.OracleSim(case, neighbor_mode=1)
+    if w:
+        sim.step(w)
+    t0 = time.perf_counter()
+    hist = sim.step(k)
+    el = time.perf_counter() - t0
+    ps = float(sum(h["n_active"] for h in hist))
+    val = ps / el
+    cores = os.cpu_count()
+    sample = (f"{k} full oracle steps of the workload ({case.n} particles) after {w} warm-up "
+              f"step(s); oracle in its binned-neighbour mode, fp64, OpenMP")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": k, "warmup": w, "ms_per_step": el / k * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "particles": case.n, "dx": args.dx},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------------------- ours
+def main():
+    args = parse()
+    rank, world, local, dist = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world, dist)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    import torch
+    from paper_1907_04034_gb300 import binding, cases
+
+    binding.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    case = cases.cylinder(dx=args.dx)
+    K, W = args.steps, args.warmup
+    hist_cap = max(4096, K + W + 64)
+
+    # ---------------------------------------------------------------- mixed (headline)
+    sm = binding.Solver(case, precision="mixed", use_graphs=True, device=str(dev),
+                        max_history=hist_cap)
+    stream = sm.stream
+    sm.step(W)
+    torch.cuda.synchronize(dev)
+    l0 = sm.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier(dist, dev if dist else None)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        sm.step(K)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(dist, dev if dist else None)
+    ms = ev0.elapsed_time(ev1)
+    launches = sm.launch_count() - l0
+    h = sm.history(K)
+    ps_local = float(np.sum(h["n_active"]))
+    t_max, ps_all = reduce_max_sum(dist, ms / 1e3, ps_local, dev if dist else None)
+    value = ps_all / t_max
+    fx_mixed = sm.history(W + K)["fx"]
+
+    # --------------------------------------------- roofline of the dominant kernel (pass B)
+    nb = sm.state(("nnb",))
+    pair_b = int(np.sum(nb["nnb"][(nb["tag"] == cases.FLUID) | (nb["tag"] == cases.INLET)]))
+    pair_a = int(np.sum(nb["nnb"]))
+    kp = min(K, 100)
+    for kname in ("pass_b", "pass_a", "rebuild", "boundary", "stage", "recycle"):
+        sm.profile(kname, True)
+    sm.step(kp)
+    prof = {}
+    for kname in ("pass_b", "pass_a", "rebuild", "boundary", "stage", "recycle"):
+        t, n = sm.read_profile(kname)
+        prof[kname] = {"ms_total": t, "launches": n, "ms_per_launch": t / max(n, 1)}
+        sm.profile(kname, False)
+    props = torch.cuda.get_device_properties(dev)
+    peaks, peak_src = load_peaks()
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(props.multi_processor_count, max_mhz)
+    b_ms = prof["pass_b"]["ms_per_launch"]
+    achieved = pair_b * FLOPS_PER_PAIR_B / (b_ms * 1e-3) / 1e12 if b_ms > 0 else None
+    a_ms = prof["pass_a"]["ms_per_launch"]
+    achieved_a = pair_a * FLOPS_PER_PAIR_A / (a_ms * 1e-3) / 1e12 if a_ms > 0 else None
+    step_ms_eager = sum(p["ms_total"] for p in prof.values()) / kp
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "pass B (mixed)",
+                "peak_note": f"fp32 FMA pipe: {props.multi_processor_count} SMs x 128 lanes x 2 "
+                             f"x {max_mhz:.0f} MHz ({peak_src} max clock)",
+                "pairs_per_launch": pair_b, "flops_per_pair": FLOPS_PER_PAIR_B,
+                "ms_per_launch": b_ms}
+    kernels = {k: round(v["ms_per_launch"], 5) for k, v in prof.items()}
+    kernels["pass_a_tflops"] = achieved_a
+    sm.close()
+    del sm
+    torch.cuda.empty_cache()
+
+    # ----------------------------------------------------------------- fp64 path + drag
+    K64 = max(1, min(args.fp64_steps, K))
+    s64 = binding.Solver(case, precision="fp64", use_graphs=True, device=str(dev),
+                         max_history=hist_cap)
+    s64.step(W)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s64.stream)
+    s64.step(K64)
+    e1.record(s64.stream)
+    torch.cuda.synchronize(dev)
+    ms64 = e0.elapsed_time(e1)
+    h64 = s64.history(K64)
+    v64 = float(np.sum(h64["n_active"])) / (ms64 / 1e3) * world
+    fx64 = s64.history(W + K64)["fx"]
+    nc = min(len(fx64), len(fx_mixed))
+    scale = max(float(np.abs(fx64[:nc]).max()), 1e-12)
+    drag_err = float(np.abs(fx_mixed[:nc] - fx64[:nc]).max()) / scale
+    s64.close()
+    del s64
+    torch.cuda.empty_cache()
+
+    # -------------------------------------------------------------- end to end (C ABI)
+    e2e = None
+    K2 = min(K, 200)
+    se = binding.Solver(case, precision="mixed", use_graphs=True, device=str(dev),
+                        max_history=hist_cap)
+    se.step(2)  # graph capture outside the timed region
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    se.upload(case)
+    se.step(K2)
+    he = se.history(K2)
+    st = se.state(("x", "y", "u", "v", "p"))
+    t1 = time.perf_counter()
+    ps_e = float(np.sum(he["n_active"]))
+    h2d = case.n * (6 * 8 + 1 + 8)
+    d2h = int(st["x"].size) * (5 * 8 + 1 + 8) + K2 * (3 * 8 + 4 * 4)
+    e2e = {"value": ps_e / (t1 - t0) * world, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / K2, "d2h_bytes_per_step": d2h / K2,
+           "steps": K2, "note": "upload from host arrays + K steps + history and field read-back"}
+    se.close()
+    del se
+
+    # ---------------------------------------------------------------------- CPU baseline
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, el, t_init = cpu_oracle_rate(case, args.cpu_steps)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{args.cpu_steps} full oracle steps of the workload ({case.n} particles), "
+                         f"binned-neighbour mode, fp64, OpenMP, {el:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": W, "ms_per_step": t_max * 1e3 / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "particles": case.n, "dx": args.dx,
+                           "precision": "mixed (fp32 pair sums, fp64 integration/reductions)",
+                           "parallelism": f"replicas x{world}",
+                           "l2": "no flush: the per-step state (~0.7 GB) is larger than L2"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary(),
+                "fp64_path": {"value": v64, "unit": UNIT, "steps": K64,
+                              "ms_per_step": ms64 / K64},
+                "mixed_over_fp64": value / v64 if v64 else None,
+                "drag_rel_err_mixed_vs_fp64": drag_err, "drag_steps_compared": nc,
+                "kernel_ms_per_launch": kernels, "eager_step_ms": step_ms_eager}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

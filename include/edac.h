@@ -192,7 +192,9 @@ edac_status edac_read_profile(edac_ctx *ctx, int kernel, double *ms, int64_t *la
  * graph replays included. */
 edac_status edac_launch_count(edac_ctx *ctx, int64_t *count);
 
-/* Text of the last error of this context (valid until the next call). */
+/* Text of the last error of this context (valid until the next call); with
+ * ctx = NULL, the last error of a context-less call (edac_workspace_bytes,
+ * edac_create) made on this host thread. */
 const char *edac_last_error(edac_ctx *ctx);
 
 /* Release the context (host memory, events, graphs).  The workspace stays the

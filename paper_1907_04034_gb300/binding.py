@@ -213,7 +213,7 @@ class Solver:
     # -------------------------------------------------------------------------- plumbing
     def _check(self, rc, ctx):
         if rc != 0:
-            msg = self.lib.edac_last_error(ctx).decode() if ctx else ""
+            msg = self.lib.edac_last_error(ctx).decode()
             raise EdacError(rc, msg)
 
     def _call(self, name, *args):

@@ -42,9 +42,13 @@ struct edac_ctx {
 
 namespace {
 
+// Last error of calls made without a context (parameter checks), per host thread.
+thread_local std::string g_err = "NULL context";
+
 edac_status fail(edac_ctx *c, edac_status st, const std::string &msg)
 {
     if (c) c->err = msg;
+    else g_err = msg;
     return st;
 }
 
@@ -307,11 +311,11 @@ edac_status edac_workspace_bytes(const edac_params *params, size_t *bytes)
 {
     std::string why;
     edac_status st = check_params(params, why);
-    if (st) return st;
-    if (!bytes) return EDAC_E_INVALID;
+    if (st) return fail(nullptr, st, why);
+    if (!bytes) return fail(nullptr, EDAC_E_INVALID, "bytes is NULL");
     Geo g;
     st = make_geo(*params, g, why);
-    if (st) return st;
+    if (st) return fail(nullptr, st, why);
     Dev d;
     *bytes = layout(d, g, params->capacity, params->max_history, params->precision == EDAC_MIXED, nullptr);
     return EDAC_OK;
@@ -319,18 +323,19 @@ edac_status edac_workspace_bytes(const edac_params *params, size_t *bytes)
 
 edac_status edac_create(const edac_params *params, void *d_workspace, size_t bytes, edac_ctx **out)
 {
-    if (!out) return EDAC_E_INVALID;
+    if (!out) return fail(nullptr, EDAC_E_INVALID, "out is NULL");
     *out = nullptr;
     std::string why;
     edac_status st = check_params(params, why);
-    if (st) return st;
+    if (st) return fail(nullptr, st, why);
     Geo g;
     st = make_geo(*params, g, why);
-    if (st) return st;
+    if (st) return fail(nullptr, st, why);
     Dev probe;
     const size_t need = layout(probe, g, params->capacity, params->max_history,
                                params->precision == EDAC_MIXED, nullptr);
-    if (!d_workspace || bytes < need || ((uintptr_t)d_workspace & 255u)) return EDAC_E_INVALID;
+    if (!d_workspace || bytes < need || ((uintptr_t)d_workspace & 255u))
+        return fail(nullptr, EDAC_E_INVALID, "workspace missing, too small or not 256-byte aligned");
     edac_ctx *c = new edac_ctx();
     c->P = *params;
     c->mixed = params->precision == EDAC_MIXED;
@@ -751,7 +756,7 @@ edac_status edac_launch_count(edac_ctx *ctx, int64_t *count)
 
 const char *edac_last_error(edac_ctx *ctx)
 {
-    return ctx ? ctx->err.c_str() : "NULL context";
+    return ctx ? ctx->err.c_str() : g_err.c_str();
 }
 
 void edac_destroy(edac_ctx *ctx)

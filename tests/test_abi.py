@@ -72,4 +72,11 @@ def test_create_rejects_missing_or_small_workspace(lib):
 
 def test_null_context_is_an_error(lib):
     assert lib.edac_step(None, 1) == 1
-    assert lib.edac_last_error(None) == b"NULL context"
+
+
+def test_contextless_errors_carry_a_message(lib):
+    n = C.c_size_t(0)
+    assert lib.edac_workspace_bytes(C.byref(_params(dt=-1.0)), C.byref(n)) == 1
+    assert b"must be > 0" in lib.edac_last_error(None)
+    assert lib.edac_workspace_bytes(C.byref(_params(periodic_y=1, y_max=0.1)), C.byref(n)) == 1
+    assert b"periodic" in lib.edac_last_error(None) or b"empty" in lib.edac_last_error(None)
