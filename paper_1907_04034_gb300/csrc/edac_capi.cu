@@ -118,6 +118,8 @@ void make_phys(const edac_params &P, Phys &ph)
     ph.gy = P.gy;
     ph.dt = P.dt;
     ph.U = P.U;
+    ph.inv_2rc = 1.0 / (2.0 * P.rho0 * P.cs);
+    ph.inv_navg = 1.0 / 6.0;
     ph.inv_hf = (float)ph.inv_h;
     ph.a2f = (float)ph.a2;
     ph.a2hf = (float)ph.a2h;
@@ -125,6 +127,7 @@ void make_phys(const edac_params &P, Phys &ph)
     ph.nuf = (float)ph.nu;
     ph.nuef = (float)ph.nu_e;
     ph.eh2f = (float)ph.eh2;
+    ph.w0f = (float)(ph.a2 * 66.0);  // W(0) = alpha_2 w(0), w(0) = 3^5 - 6 2^5 + 15
     ph.use_pavg = P.use_pavg ? 1 : 0;
     ph.has_inlet = 0;
     ph.n_modes = 0;
@@ -157,7 +160,7 @@ edac_status check_params(const edac_params *P, std::string &why)
         why = "precision must be EDAC_FP64 or EDAC_MIXED";
         return EDAC_E_INVALID;
     }
-    if (P->capacity < 1 || P->capacity > (1 << 30)) { why = "capacity out of range"; return EDAC_E_INVALID; }
+    if (P->capacity < 1 || P->capacity >= (1 << 28)) { why = "capacity out of range [1, 2^28)"; return EDAC_E_INVALID; }
     if (P->max_history < 1 || P->max_history > (1 << 26)) { why = "max_history out of range"; return EDAC_E_INVALID; }
     return EDAC_OK;
 }
@@ -195,6 +198,8 @@ size_t layout(Dev &d, const Geo &g, int cap, int max_history, int mixed, char *b
     DARR(slot_cell, int, C);
     DARR(within, int, C);
     DARR(order, int, C);
+    DARR(order_raw, int, C);
+    DARR(scan_part, int, (size_t)(g.ncells + 4095) / 4096 + 1);
     DARR(cellk, int, C);
     DARR(stag, uint8_t, C);
     DARR(P, float4, C);
@@ -261,9 +266,9 @@ int issue_eval(edac_ctx *c, int end_of_step)
 int issue_step(edac_ctx *c)
 {
     int n = 0;
-    { Group g(c, EDAC_K_STAGE); n += launch_stage(c->d, c->stream, 0); }
+    { Group g(c, EDAC_K_STAGE); n += launch_stage(c->d, c->stream, c->mixed, 0); }
     n += issue_eval(c, 0);
-    { Group g(c, EDAC_K_STAGE); n += launch_stage(c->d, c->stream, 1); }
+    { Group g(c, EDAC_K_STAGE); n += launch_stage(c->d, c->stream, c->mixed, 1); }
     n += issue_eval(c, 1);
     { Group g(c, EDAC_K_RECYCLE); n += launch_recycle(c->d, c->stream); }
     return n;
@@ -345,6 +350,7 @@ edac_status edac_create(const edac_params *params, void *d_workspace, size_t byt
     c->d.g = g;
     make_phys(*params, c->d.ph);
     c->d.cap = params->capacity;
+    c->d.mixed = c->mixed;
     c->d.max_history = params->max_history;
     layout(c->d, g, params->capacity, params->max_history, c->mixed, c->ws);
     *out = c;
@@ -384,6 +390,7 @@ edac_status edac_set_outlet(edac_ctx *ctx, double x_out, int n_layers, int kind,
     ph.x_out = x_out;
     ph.L_out = (double)n_layers * ctx->P.dx;
     ph.n_avg = n_avg;
+    ph.inv_navg = 1.0 / (double)n_avg;
     if (i_thresh >= 0) ph.I_thr = i_thresh;
     drop_graph(ctx);
     return EDAC_OK;

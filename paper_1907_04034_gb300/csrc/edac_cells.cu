@@ -48,47 +48,84 @@ __global__ void k_cell_count(Dev d)
     }
 }
 
-// Exclusive scan of the per-cell counts into cell_start[0..ncells], one block of 1024
-// threads: each thread owns a contiguous chunk, block-scans the chunk totals, then writes
-// its chunk's prefix sums.  Also resets the boundary-list length for the gather.
-__global__ void __launch_bounds__(1024) k_cell_scan(Dev d)
+// Exclusive scan of the per-cell counts into cell_start[0..ncells] in three launches:
+// per-block totals of SCAN_TILE cells, a one-block scan of the totals (which also sets the
+// live count and resets the boundary-list length), and the per-block scan with its offset.
+constexpr int SCAN_TILE = 4096;  // cells per block, 4 per thread
+
+__device__ __forceinline__ int block_exclusive_scan_1024(int v, int *sh_warp, int &total)
 {
-    __shared__ int warp_tot[32];
-    const int n = d.g.ncells;
     const int t = threadIdx.x;
-    const int chunk = (n + 1023) / 1024;
-    const int b = t * chunk, e = min(n, b + chunk);
-    int local = 0;
-    for (int c = b; c < e; ++c) local += d.cell_count[c];
-    // inclusive warp scan
-    int v = local;
+    int x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, v, o);
-        if ((int)lane_id() >= o) v += y;
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)lane_id() >= o) x += y;
     }
-    if (lane_id() == 31) warp_tot[t >> 5] = v;
+    if (lane_id() == 31) sh_warp[t >> 5] = x;
     __syncthreads();
     if (t < 32) {
-        int w = warp_tot[t];
+        int w = sh_warp[t];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, w, o);
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
             if (t >= o) w += y;
         }
-        warp_tot[t] = w;  // inclusive over warps
+        sh_warp[t] = w;
     }
     __syncthreads();
-    int run = v - local + ((t >> 5) > 0 ? warp_tot[(t >> 5) - 1] : 0);
-    for (int c = b; c < e; ++c) {
-        d.cell_start[c] = run;
-        run += d.cell_count[c];
+    total = sh_warp[31];
+    const int r = x - v + ((t >> 5) > 0 ? sh_warp[(t >> 5) - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_reduce(Dev d)
+{
+    __shared__ int sh[32];
+    const int n = d.g.ncells;
+    const int c0 = blockIdx.x * SCAN_TILE + threadIdx.x * 4;
+    int v = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v += (c0 + q < n) ? d.cell_count[c0 + q] : 0;
+    int total;
+    block_exclusive_scan_1024(v, sh, total);
+    if (threadIdx.x == 0) d.scan_part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(Dev d, int nblk)
+{
+    __shared__ int sh[32];
+    int run = 0;
+    for (int b0 = 0; b0 < nblk; b0 += 1024) {
+        const int b = b0 + (int)threadIdx.x;
+        const int v = b < nblk ? d.scan_part[b] : 0;
+        int total;
+        const int ex = block_exclusive_scan_1024(v, sh, total);
+        if (b < nblk) d.scan_part[b] = run + ex;
+        run += total;
     }
-    if (t == 1023) {
-        const int total = warp_tot[31];
-        d.cell_start[n] = total;
-        d.cnt->n_alive = total;
+    if (threadIdx.x == 0) {
+        d.cell_start[d.g.ncells] = run;
+        d.cnt->n_alive = run;
         d.cnt->n_bnd = 0;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_down(Dev d)
+{
+    __shared__ int sh[32];
+    const int n = d.g.ncells;
+    const int c0 = blockIdx.x * SCAN_TILE + threadIdx.x * 4;
+    int v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = (c0 + q < n) ? d.cell_count[c0 + q] : 0;
+    int total;
+    int run = block_exclusive_scan_1024(v[0] + v[1] + v[2] + v[3], sh, total) + d.scan_part[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (c0 + q < n) d.cell_start[c0 + q] = run;
+        run += v[q];
     }
 }
 
@@ -97,69 +134,69 @@ __global__ void k_cell_scatter(Dev d)
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.cap; s += gridDim.x * blockDim.x) {
         const int c = d.slot_cell[s];
         if (c < 0) continue;
-        d.order[d.cell_start[c] + d.within[s]] = s;
+        d.order_raw[d.cell_start[c] + d.within[s]] = s;
     }
 }
 
-// Sort each cell's slots ascending (insertion sort; a cell holds ~13 particles), and
-// clear the cell's count for the next build.
-__global__ void k_cell_sort(Dev d)
+// One warp per cell: rank the cell's slots (ascending slot, so the cell order does not depend
+// on the order of the counting atomics), write the order, clear the cell's count for the next
+// build, and gather the cell-ordered copies the pair kernels read.
+template <int MIXED>
+__device__ __forceinline__ void gather_one(const Dev &d, int s, int k, int c)
 {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.g.ncells; c += gridDim.x * blockDim.x) {
-        d.cell_count[c] = 0;
-        const int j0 = d.cell_start[c], j1 = d.cell_start[c + 1];
-        for (int a = j0 + 1; a < j1; ++a) {
-            const int key = d.order[a];
-            int b = a - 1;
-            while (b >= j0 && d.order[b] > key) {
-                d.order[b + 1] = d.order[b];
-                --b;
-            }
-            d.order[b + 1] = key;
-        }
+    const Geo &g = d.g;
+    d.order[k] = s;
+    d.cellk[k] = c;
+    const int cx = c % g.nx, cy = c / g.nx;
+    const double xs = d.x[s], ys = d.y[s];
+    const float rx = (float)(xs - (g.x_min + (double)cx * g.sx));
+    const float ry = (float)(ys - (g.y_min + (double)cy * g.sy));
+    const double ms = d.m[s];
+    d.P[k] = make_float4(rx, ry, (float)ms, 0.0f);
+    d.XY[k] = make_double2(xs, ys);
+    const uint8_t t = d.tag[s];
+    d.stag[k] = (uint8_t)(t | ((t == OUTLET && d.redp[s]) ? TAG_REDP : 0));
+    d.AUX[k] = make_double2(t == FLUID ? d.J2[s] : d.J2p[s], d.advp[s]);
+    const double us = d.u[s], vs = d.v[s];
+    const double dus = d.ut[s] - us, dvs = d.vt[s] - vs;
+    if (MIXED) {
+        d.Bf[k] = make_float4((float)us, (float)vs, (float)dus, (float)dvs);
+        d.Qf[k] = make_float4((float)d.p[s], 0.0f, 0.0f, 0.0f);
+    } else {
+        d.UV[k] = make_double2(us, vs);
+        d.DUV[k] = make_double2(dus, dvs);
+        d.PV[k] = make_double2(d.p[s], 0.0);
+        d.Ms[k] = ms;
     }
 }
 
 template <int MIXED>
-__global__ void k_gather(Dev d)
+__global__ void k_cell_gather(Dev d)
 {
-    const Geo &g = d.g;
-    const int n = d.cnt->n_alive;
-    const int stride = gridDim.x * blockDim.x;
-    // uniform trip count per warp so that warp_append sees all 32 lanes
-    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int k = base + threadIdx.x;
-        const bool valid = k < n;
-        bool is_bnd = false;
-        if (valid) {
-            const int s = d.order[k];
-            const int c = d.slot_cell[s];
-            d.cellk[k] = c;
-            const int cx = c % g.nx, cy = c / g.nx;
-            const double xs = d.x[s], ys = d.y[s];
-            const float rx = (float)(xs - (g.x_min + (double)cx * g.sx));
-            const float ry = (float)(ys - (g.y_min + (double)cy * g.sy));
-            const double ms = d.m[s];
-            d.P[k] = make_float4(rx, ry, (float)ms, 0.0f);
-            d.XY[k] = make_double2(xs, ys);
-            const uint8_t t = d.tag[s];
-            d.stag[k] = (uint8_t)(t | ((t == OUTLET && d.redp[s]) ? TAG_REDP : 0));
-            d.AUX[k] = make_double2(t == FLUID ? d.J2[s] : d.J2p[s], d.advp[s]);
-            const double us = d.u[s], vs = d.v[s];
-            const double dus = d.ut[s] - us, dvs = d.vt[s] - vs;
-            if (MIXED) {
-                d.Bf[k] = make_float4((float)us, (float)vs, (float)dus, (float)dvs);
-                d.Qf[k] = make_float4((float)d.p[s], 0.0f, 0.0f, 0.0f);
-            } else {
-                d.UV[k] = make_double2(us, vs);
-                d.DUV[k] = make_double2(dus, dvs);
-                d.PV[k] = make_double2(d.p[s], 0.0);
-                d.Ms[k] = ms;
+    const int lane = (int)lane_id();
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < d.g.ncells; c += nw) {
+        const int j0 = d.cell_start[c], j1 = d.cell_start[c + 1];
+        const int n = j1 - j0;
+        if (lane == 0) d.cell_count[c] = 0;
+        for (int base = 0; base < n; base += 32) {
+            const int e = base + lane;
+            const bool valid = e < n;
+            const int s = valid ? d.order_raw[j0 + e] : 0x7fffffff;
+            int rank = 0;
+            if (n <= 32) {
+                for (int q = 0; q < n; ++q) rank += (__shfl_sync(0xffffffffu, s, q) < s);
+            } else if (valid) {
+                for (int q = 0; q < n; ++q) rank += (d.order_raw[j0 + q] < s);
             }
-            is_bnd = (t != FLUID);
+            bool is_bnd = false;
+            if (valid) {
+                gather_one<MIXED>(d, s, j0 + rank, c);
+                is_bnd = d.tag[s] != FLUID;
+            }
+            const int slot = warp_append(&d.cnt->n_bnd, is_bnd);
+            if (is_bnd) d.bnd[slot] = j0 + rank;
         }
-        const int slot = warp_append(&d.cnt->n_bnd, is_bnd);
-        if (is_bnd) d.bnd[slot] = k;
     }
 }
 
@@ -172,7 +209,31 @@ __global__ void k_gather(Dev d)
 //   outlet: x = x^n + tau u_adv (y fixed), fields frozen within the step.
 // The predictor (tau = dt/2) saves the base state; the corrector (tau = dt) also takes
 // the time-average sample of the hybrid outlet (Eqs. timeevg, acouinten) and forms J2.
-template <bool CORR>
+// Time-average ring of the hybrid outlet: fp64 samples on the fp64 path, fp32 samples on the
+// mixed path (the average only feeds J2 and the frozen outlet values).
+template <class R>
+__device__ __forceinline__ void ring_sample(const Dev &d, int s, double un, double vn, double pn,
+                                            double &ub, double &vb, double &pbv)
+{
+    const Phys &ph = d.ph;
+    R *rg = reinterpret_cast<R *>(d.ring) + (size_t)s * NAVG_MAX * 3;
+    // intensity p^2/(2 rho0 c) against I of Eq. (acouinten): the average only takes samples
+    // below it
+    if (pn * pn * ph.inv_2rc <= ph.I_thr) {
+        const int k = d.rpos[s];
+        rg[3 * k + 0] = (R)un; rg[3 * k + 1] = (R)vn; rg[3 * k + 2] = (R)pn;
+        d.rpos[s] = (uint8_t)(k + 1 == ph.n_avg ? 0 : k + 1);
+    }
+    R su = 0, sv = 0, sp = 0;
+    for (int k = 0; k < ph.n_avg; ++k) {
+        su += rg[3 * k + 0]; sv += rg[3 * k + 1]; sp += rg[3 * k + 2];
+    }
+    ub = (double)su * ph.inv_navg;
+    vb = (double)sv * ph.inv_navg;
+    pbv = (double)sp * ph.inv_navg;
+}
+
+template <bool CORR, int MIXED>
 __global__ void k_stage(Dev d, double tau)
 {
     const Geo &g = d.g;
@@ -202,19 +263,9 @@ __global__ void k_stage(Dev d, double tau)
                   isfinite(utn) && isfinite(vtn)))
                 set_err(d, ERR_NONFINITE);
             if (CORR && ph.has_outlet) {
-                double *rg = d.ring + (size_t)s * NAVG_MAX * 3;
-                const double inten = pn * pn / (2.0 * ph.rho0 * ph.cs);
-                if (inten <= ph.I_thr) {
-                    const int k = d.rpos[s];
-                    rg[3 * k + 0] = un; rg[3 * k + 1] = vn; rg[3 * k + 2] = pn;
-                    d.rpos[s] = (uint8_t)((k + 1) % ph.n_avg);
-                }
-                double su = 0.0, sv = 0.0, sp = 0.0;
-                for (int k = 0; k < ph.n_avg; ++k) {
-                    su += rg[3 * k + 0]; sv += rg[3 * k + 1]; sp += rg[3 * k + 2];
-                }
-                const double ub = su / (double)ph.n_avg, vb = sv / (double)ph.n_avg,
-                             pbv = sp / (double)ph.n_avg;
+                double ub, vb, pbv;
+                if (MIXED) ring_sample<float>(d, s, un, vn, pn, ub, vb, pbv);
+                else ring_sample<double>(d, s, un, vn, pn, ub, vb, pbv);
                 d.ubar[s] = ub; d.vbar[s] = vb; d.pbar[s] = pbv;
                 d.J2[s] = ph.rho0 * ph.cs * (un - ub) + (pn - pbv);
             }
@@ -236,9 +287,14 @@ __global__ void k_stage(Dev d, double tau)
 // Ring buffer of a particle that becomes fluid: all samples = current (u, v, p).
 __device__ __forceinline__ void ring_fill(const Dev &d, int s)
 {
-    double *rg = d.ring + (size_t)s * NAVG_MAX * 3;
     const double u = d.u[s], v = d.v[s], p = d.p[s];
-    for (int k = 0; k < d.ph.n_avg; ++k) { rg[3 * k] = u; rg[3 * k + 1] = v; rg[3 * k + 2] = p; }
+    if (d.mixed) {
+        float *rg = reinterpret_cast<float *>(d.ring) + (size_t)s * NAVG_MAX * 3;
+        for (int k = 0; k < d.ph.n_avg; ++k) { rg[3 * k] = (float)u; rg[3 * k + 1] = (float)v; rg[3 * k + 2] = (float)p; }
+    } else {
+        double *rg = d.ring + (size_t)s * NAVG_MAX * 3;
+        for (int k = 0; k < d.ph.n_avg; ++k) { rg[3 * k] = u; rg[3 * k + 1] = v; rg[3 * k + 2] = p; }
+    }
     d.rpos[s] = 0;
     d.ubar[s] = u; d.vbar[s] = v; d.pbar[s] = p; d.J2[s] = 0.0;
 }
@@ -419,22 +475,31 @@ int grid_for(int n)
 }  // namespace
 
 // cell_count is all zero on entry: cleared by the workspace reset at upload and by
-// k_cell_sort of the previous build.
+// k_cell_gather of the previous build.
 int launch_rebuild(const Dev &d, cudaStream_t s, int mixed)
 {
+    const int nblk = (d.g.ncells + SCAN_TILE - 1) / SCAN_TILE;
+    const int gw = min((d.g.ncells + 7) / 8, 152 * 32);  // 8 warps per block, grid-stride
     k_cell_count<<<grid_for(d.cap), TPB, 0, s>>>(d);
-    k_cell_scan<<<1, 1024, 0, s>>>(d);
+    k_scan_reduce<<<nblk, 1024, 0, s>>>(d);
+    k_scan_top<<<1, 1024, 0, s>>>(d, nblk);
+    k_scan_down<<<nblk, 1024, 0, s>>>(d);
     k_cell_scatter<<<grid_for(d.cap), TPB, 0, s>>>(d);
-    k_cell_sort<<<grid_for(d.g.ncells), TPB, 0, s>>>(d);
-    if (mixed) k_gather<1><<<grid_for(d.cap), TPB, 0, s>>>(d);
-    else k_gather<0><<<grid_for(d.cap), TPB, 0, s>>>(d);
-    return 5;
+    if (mixed) k_cell_gather<1><<<gw, 256, 0, s>>>(d);
+    else k_cell_gather<0><<<gw, 256, 0, s>>>(d);
+    return 6;
 }
 
-int launch_stage(const Dev &d, cudaStream_t s, int corrector)
+int launch_stage(const Dev &d, cudaStream_t s, int mixed, int corrector)
 {
-    if (corrector) k_stage<true><<<grid_for(d.cap), TPB, 0, s>>>(d, d.ph.dt);
-    else k_stage<false><<<grid_for(d.cap), TPB, 0, s>>>(d, 0.5 * d.ph.dt);
+    const int gb = grid_for(d.cap);
+    if (corrector) {
+        if (mixed) k_stage<true, 1><<<gb, TPB, 0, s>>>(d, d.ph.dt);
+        else k_stage<true, 0><<<gb, TPB, 0, s>>>(d, d.ph.dt);
+    } else {
+        if (mixed) k_stage<false, 1><<<gb, TPB, 0, s>>>(d, 0.5 * d.ph.dt);
+        else k_stage<false, 0><<<gb, TPB, 0, s>>>(d, 0.5 * d.ph.dt);
+    }
     return 1;
 }
 

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace edac {
 
 constexpr int NAVG_MAX = 8;       // longest time-average window of the hybrid outlet
@@ -36,7 +38,8 @@ struct Geo {
 struct Phys {
     double h, inv_h, a2, a2h;        // alpha_2 = 7/(478 pi h^2), alpha_2 / h
     double rho0, cs, c2, nu, nu_e, eh2, pb, gx, gy, dt, U;
-    float inv_hf, a2f, a2hf, c2f, nuf, nuef, eh2f;
+    double inv_2rc, inv_navg;        // 1/(2 rho0 c_s), 1/n_avg
+    float inv_hf, a2f, a2hf, c2f, nuf, nuef, eh2f, w0f;
     int use_pavg;
     int has_inlet, n_modes;
     double x_in, L_in, in_y0, in_H;
@@ -66,6 +69,7 @@ struct Dev {
     Phys ph;
     int cap;
     int max_history;
+    int mixed;         // 1: mixed-precision path (fp32 ring samples, fp32 pair terms)
     Counters *cnt;
     // master particle state, slot-indexed [cap]
     double *x, *y, *u, *v, *ut, *vt, *p, *m;
@@ -74,7 +78,7 @@ struct Dev {
     int *nnb;
     uint8_t *tag;
     unsigned long long *id;
-    double *ring;   // [cap][NAVG_MAX][3]
+    double *ring;   // [cap][NAVG_MAX][3] (fp64 path) or float [cap][NAVG_MAX][3] (mixed path)
     uint8_t *rpos;
     double *ubar, *vbar, *pbar, *J2, *J2p, *advp;
     uint8_t *redp;
@@ -85,6 +89,8 @@ struct Dev {
     int *within;       // [cap]
     // sorted (cell-ordered) copies, index k < n_alive
     int *order;        // slot of k
+    int *order_raw;    // slots scattered by cell in atomic order (input of the per-cell sort)
+    int *scan_part;    // per-block partial sums of the cell-count scan
     int *cellk;        // cell of k
     uint8_t *stag;     // tag of k (| TAG_REDP)
     float4 *P;         // (x - cell x0, y - cell y0, m, 0) fp32, both paths
@@ -161,16 +167,31 @@ __device__ __forceinline__ int cell_coord(double v, double lo, double inv_s, int
     return c < 0 ? 0 : (c >= n ? n - 1 : c);
 }
 
-// Walk the exact neighbours j of a query point (fp64 position qx, qy; cell (cx, cy);
-// fp32 position relative to that cell's origin rx, ry).  An fp32 pre-test on
-// cell-relative coordinates rejects or accepts pairs far from the support
-// boundary; pairs inside the band |r^2 - rc^2| <~ 4e-5 rc^2 are decided by exact_r2.
-// f(j, dx32, dy32, r2_32, exact_dx, exact_dy, exact_r2, have_exact) is called for every
-// neighbour; have_exact says whether the fp64 values were computed.
-// NEED_EXACT = true computes the fp64 separation for every accepted pair (fp64 path).
-template <bool NEED_EXACT, class F>
-__device__ __forceinline__ void for_neighbors(const Dev &d, double qx, double qy, int cx, int cy,
-                                              float rx, float ry, F &&f)
+// The membership test of every pair kernel.  rxo, ryo: the query's fp32 position relative to
+// the origin of j's cell; pj: j's fp32 cell-relative position.  The fp32 pre-test rejects
+// pairs with r^2 >= rc^2 (1 + 4e-5) and accepts pairs with r^2 <= rc^2 (1 - 4e-5); inside that
+// band the fp64 test exact_r2 < rc^2 decides.  The fp32 error of r^2 on cell-relative
+// coordinates is below 2e-6 rc^2, so the result always equals the fp64 test.
+__device__ __forceinline__ bool is_member(const Dev &d, float rxo, float ryo, const float4 &pj,
+                                          int j, double qx, double qy, float &dxf, float &dyf,
+                                          float &r2f)
+{
+    dxf = rxo - pj.x;
+    dyf = ryo - pj.y;
+    r2f = dxf * dxf + dyf * dyf;
+    if (r2f >= d.g.rc2_hi) return false;
+    if (r2f > d.g.rc2_lo) {
+        const double2 xy = d.XY[j];
+        double ex, ey;
+        return exact_r2(d.g, qx, qy, xy.x, xy.y, ex, ey) < d.g.rc2;
+    }
+    return true;
+}
+
+// Visit the 3x3 block of cells around (cx, cy): f(ox, oy, j0, j1) for each existing cell,
+// with [j0, j1) its range in the cell order (periodic axes wrap).
+template <class F>
+__device__ __forceinline__ void for_block(const Dev &d, int cx, int cy, F &&f)
 {
     const Geo &g = d.g;
 #pragma unroll 1
@@ -178,34 +199,13 @@ __device__ __forceinline__ void for_neighbors(const Dev &d, double qx, double qy
         int by = cy + oy;
         if (g.py) by = by < 0 ? by + g.ny : (by >= g.ny ? by - g.ny : by);
         else if (by < 0 || by >= g.ny) continue;
-        const float offy = (float)oy * g.syf;
 #pragma unroll 1
         for (int ox = -1; ox <= 1; ++ox) {
             int bx = cx + ox;
             if (g.px) bx = bx < 0 ? bx + g.nx : (bx >= g.nx ? bx - g.nx : bx);
             else if (bx < 0 || bx >= g.nx) continue;
-            const float offx = (float)ox * g.sxf;
             const int c = by * g.nx + bx;
-            const int j0 = __ldg(d.cell_start + c), j1 = __ldg(d.cell_start + c + 1);
-            f.begin_cell();
-#pragma unroll 1
-            for (int j = j0; j < j1; ++j) {
-                const float4 pj = __ldg(d.P + j);
-                const float dxf = rx - (pj.x + offx);
-                const float dyf = ry - (pj.y + offy);
-                const float r2f = dxf * dxf + dyf * dyf;
-                if (r2f >= g.rc2_hi) continue;
-                double edx = 0.0, edy = 0.0, er2 = 0.0;
-                bool have = false;
-                if (NEED_EXACT || r2f > g.rc2_lo) {
-                    const double2 xy = d.XY[j];
-                    er2 = exact_r2(g, qx, qy, xy.x, xy.y, edx, edy);
-                    if (!(er2 < g.rc2)) continue;
-                    have = true;
-                }
-                f(j, dxf, dyf, r2f, edx, edy, er2, have, pj);
-            }
-            f.end_cell();
+            f(ox, oy, __ldg(d.cell_start + c), __ldg(d.cell_start + c + 1));
         }
     }
 }
@@ -241,7 +241,7 @@ int launch_rebuild(const Dev &d, cudaStream_t s, int mixed);
 int launch_pass_a(const Dev &d, cudaStream_t s, int mixed);
 int launch_boundary(const Dev &d, cudaStream_t s, int mixed, int end_of_step);
 int launch_pass_b(const Dev &d, cudaStream_t s, int mixed);
-int launch_stage(const Dev &d, cudaStream_t s, int corrector);
+int launch_stage(const Dev &d, cudaStream_t s, int mixed, int corrector);
 int launch_recycle(const Dev &d, cudaStream_t s);
 int launch_init(const Dev &d, cudaStream_t s);
 int launch_neighbor_dump(const Dev &d, cudaStream_t s, int mixed, const long long *start,
