@@ -209,12 +209,14 @@ size_t layout(Dev &d, const Geo &g, int cap, int max_history, int mixed, char *b
     if (mixed) {
         DARR(Bf, float4, C);
         DARR(Qf, float4, C);
+        DARR(nbm, uint4, C);
         d.UV = d.DUV = d.PV = d.RM = nullptr;
         d.Ms = nullptr;
     } else {
         DARR(UV, double2, C); DARR(DUV, double2, C); DARR(PV, double2, C); DARR(RM, double2, C);
         DARR(Ms, double, C);
         d.Bf = d.Qf = nullptr;
+        d.nbm = nullptr;
     }
     DARR(bnd, int, C);
     DARR(free_stack, int, C);

@@ -170,33 +170,33 @@ __device__ __forceinline__ void gather_one(const Dev &d, int s, int k, int c)
     }
 }
 
+// One thread per particle in the scattered (atomic) order: the particle's rank among the
+// slots of its cell (ascending slot) fixes its place in the cell order, which therefore does
+// not depend on the order of the counting atomics; the thread then gathers the cell-ordered
+// copies the pair kernels read.  Cells hold ~13 particles, so the rank costs ~13 cached loads.
 template <int MIXED>
 __global__ void k_cell_gather(Dev d)
 {
-    const int lane = (int)lane_id();
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < d.g.ncells; c += nw) {
-        const int j0 = d.cell_start[c], j1 = d.cell_start[c + 1];
-        const int n = j1 - j0;
-        if (lane == 0) d.cell_count[c] = 0;
-        for (int base = 0; base < n; base += 32) {
-            const int e = base + lane;
-            const bool valid = e < n;
-            const int s = valid ? d.order_raw[j0 + e] : 0x7fffffff;
+    const int n = d.cnt->n_alive;
+    const int stride = gridDim.x * blockDim.x;
+    // uniform trip count per warp so that warp_append sees all 32 lanes
+    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int e = base + threadIdx.x;
+        bool is_bnd = false;
+        int k = 0;
+        if (e < n) {
+            const int s = d.order_raw[e];
+            const int c = d.slot_cell[s];
+            const int j0 = d.cell_start[c], j1 = d.cell_start[c + 1];
             int rank = 0;
-            if (n <= 32) {
-                for (int q = 0; q < n; ++q) rank += (__shfl_sync(0xffffffffu, s, q) < s);
-            } else if (valid) {
-                for (int q = 0; q < n; ++q) rank += (d.order_raw[j0 + q] < s);
-            }
-            bool is_bnd = false;
-            if (valid) {
-                gather_one<MIXED>(d, s, j0 + rank, c);
-                is_bnd = d.tag[s] != FLUID;
-            }
-            const int slot = warp_append(&d.cnt->n_bnd, is_bnd);
-            if (is_bnd) d.bnd[slot] = j0 + rank;
+            for (int q = j0; q < j1; ++q) rank += (__ldg(d.order_raw + q) < s);
+            k = j0 + rank;
+            if (e == j0) d.cell_count[c] = 0;  // one thread per non-empty cell clears its count
+            gather_one<MIXED>(d, s, k, c);
+            is_bnd = d.tag[s] != FLUID;
         }
+        const int slot = warp_append(&d.cnt->n_bnd, is_bnd);
+        if (is_bnd) d.bnd[slot] = k;
     }
 }
 
@@ -479,14 +479,13 @@ int grid_for(int n)
 int launch_rebuild(const Dev &d, cudaStream_t s, int mixed)
 {
     const int nblk = (d.g.ncells + SCAN_TILE - 1) / SCAN_TILE;
-    const int gw = min((d.g.ncells + 7) / 8, 152 * 32);  // 8 warps per block, grid-stride
     k_cell_count<<<grid_for(d.cap), TPB, 0, s>>>(d);
     k_scan_reduce<<<nblk, 1024, 0, s>>>(d);
     k_scan_top<<<1, 1024, 0, s>>>(d, nblk);
     k_scan_down<<<nblk, 1024, 0, s>>>(d);
     k_cell_scatter<<<grid_for(d.cap), TPB, 0, s>>>(d);
-    if (mixed) k_cell_gather<1><<<gw, 256, 0, s>>>(d);
-    else k_cell_gather<0><<<gw, 256, 0, s>>>(d);
+    if (mixed) k_cell_gather<1><<<grid_for(d.cap), TPB, 0, s>>>(d);
+    else k_cell_gather<0><<<grid_for(d.cap), TPB, 0, s>>>(d);
     return 6;
 }
 

@@ -105,6 +105,7 @@ struct Dev {
     // mixed path
     float4 *Bf;        // (u, v, u~ - u, v~ - v)
     float4 *Qf;        // (p, V, rho, m / rho)
+    uint4 *nbm;        // neighbour mask over the tiled candidate order (pass A -> pass B)
     int *bnd;          // boundary particles (sorted index), n_bnd of them
     // recycling
     int *free_stack;   // [cap]
@@ -170,8 +171,9 @@ __device__ __forceinline__ int cell_coord(double v, double lo, double inv_s, int
 // The membership test of every pair kernel.  rxo, ryo: the query's fp32 position relative to
 // the origin of j's cell; pj: j's fp32 cell-relative position.  The fp32 pre-test rejects
 // pairs with r^2 >= rc^2 (1 + 4e-5) and accepts pairs with r^2 <= rc^2 (1 - 4e-5); inside that
-// band the fp64 test exact_r2 < rc^2 decides.  The fp32 error of r^2 on cell-relative
-// coordinates is below 2e-6 rc^2, so the result always equals the fp64 test.
+// band the fp64 test exact_r2 < rc^2 decides.  The fp32 error of r^2 on cell-relative (or
+// tile-relative, at most ~10 cells from the origin) coordinates stays below 1e-5 rc^2, so the
+// result always equals the fp64 test.
 __device__ __forceinline__ bool is_member(const Dev &d, float rxo, float ryo, const float4 &pj,
                                           int j, double qx, double qy, float &dxf, float &dyf,
                                           float &r2f)

@@ -20,7 +20,6 @@ namespace {
 
 constexpr int TPB = 128;   // threads per block of the pair passes
 constexpr int LMAX = 64;   // shared-memory list entries per thread (flushed when full)
-constexpr int FOLD = 8;    // pair terms summed in fp32 before a compensated fold
 
 __device__ __forceinline__ void cell_of(const Dev &d, int k, int &cx, int &cy)
 {
@@ -59,50 +58,12 @@ __device__ __forceinline__ void listed_neighbors(const Dev &d, int k, double qx,
     for (int c = 0; c < cnt; ++c) body(lst[c * TPB]);
 }
 
-// fp32 separation of a listed neighbour (same arithmetic as the membership pre-test)
-__device__ __forceinline__ int geom32(const Dev &d, unsigned e, float rx, float ry, float4 &pj,
-                                      float &dx, float &dy, float &r2)
-{
-    const int j = (int)(e >> 4);
-    const int ox = (int)((e >> 2) & 3u) - 1, oy = (int)(e & 3u) - 1;
-    pj = __ldg(d.P + j);
-    dx = (rx - (float)ox * d.g.sxf) - pj.x;
-    dy = (ry - (float)oy * d.g.syf) - pj.y;
-    r2 = dx * dx + dy * dy;
-    return j;
-}
-
 // r from r^2 without the IEEE square root: r^2 * rsqrt(r^2), 0 for coincident particles
 __device__ __forceinline__ float fast_r(float r2) { return r2 > 0.f ? r2 * rsqrtf(r2) : 0.f; }
 
-// ---------------------------------------------------------------------------- pass A
+// ------------------------------------------------------------------ fp64 path: pass A
 // S_i = sum_j W_ij, V_i = 1/S_i (number-density volume, Sec. 2), rho_i = sum_j m_j W_ij
 // (Eq. summation-density), N_i = number of neighbours (self included).
-struct BodyA32 {
-    const Dev &d;
-    float rx, ry, a2, inv_h;
-    float s = 0.f, r = 0.f, sh = 0.f, sl = 0.f, rh = 0.f, rl = 0.f;
-    int n = 0;
-    __device__ BodyA32(const Dev &dd, float x, float y)
-        : d(dd), rx(x), ry(y), a2(dd.ph.a2f), inv_h(dd.ph.inv_hf) {}
-    __device__ void operator()(unsigned e)
-    {
-        float4 pj;
-        float dx, dy, r2;
-        geom32(d, e, rx, ry, pj, dx, dy, r2);
-        const float w = a2 * quintic_w(fast_r(r2) * inv_h);
-        s += w;
-        r += pj.z * w;
-        if ((++n & (FOLD - 1)) == 0) fold();
-    }
-    __device__ void fold()
-    {
-        two_sum_acc(sh, sl, s);
-        two_sum_acc(rh, rl, r);
-        s = r = 0.f;
-    }
-};
-
 struct BodyA64 {
     const Dev &d;
     double qx, qy, a2, inv_h;
@@ -123,8 +84,7 @@ struct BodyA64 {
     }
 };
 
-template <int MIXED>
-__global__ void __launch_bounds__(TPB) k_pass_a(Dev d)
+__global__ void __launch_bounds__(TPB) k_pass_a64(Dev d)
 {
     __shared__ unsigned lst_all[LMAX * TPB];
     unsigned *lst = lst_all + threadIdx.x;
@@ -135,40 +95,22 @@ __global__ void __launch_bounds__(TPB) k_pass_a(Dev d)
         const float4 pi = d.P[k];
         const double2 xy = d.XY[k];
         const int s = d.order[k];
-        if (MIXED) {
-            BodyA32 f(d, pi.x, pi.y);
-            listed_neighbors(d, k, xy.x, xy.y, cx, cy, pi.x, pi.y, lst, f);
-            f.fold();
-            // self term: W(0) = alpha_2 w(0)
-            const float w0 = d.ph.w0f;
-            two_sum_acc(f.sh, f.sl, w0);
-            two_sum_acc(f.rh, f.rl, pi.z * w0);
-            const float S = f.sh + f.sl, R = f.rh + f.rl;
-            const float V = 1.0f / S;
-            const float4 q = d.Qf[k];
-            d.Qf[k] = make_float4(q.x, V, R, pi.z / R);
-            d.snnb[k] = f.n + 1;
-            d.rho[s] = (double)R;
-            d.vol[s] = (double)V;
-            d.nnb[s] = f.n + 1;
-        } else {
-            BodyA64 f(d, xy.x, xy.y);
-            const double mk = d.Ms[k];
-            const double w0 = d.ph.a2 * quintic_w(0.0);
-            listed_neighbors(d, k, xy.x, xy.y, cx, cy, pi.x, pi.y, lst, f);
-            const double S = f.s + w0, R = f.r + mk * w0;
-            const double V = 1.0 / S;
-            d.PV[k].y = V;
-            d.RM[k] = make_double2(R, mk / R);
-            d.snnb[k] = f.n + 1;
-            d.rho[s] = R;
-            d.vol[s] = V;
-            d.nnb[s] = f.n + 1;
-        }
+        BodyA64 f(d, xy.x, xy.y);
+        const double mk = d.Ms[k];
+        const double w0 = d.ph.a2 * quintic_w(0.0);
+        listed_neighbors(d, k, xy.x, xy.y, cx, cy, pi.x, pi.y, lst, f);
+        const double S = f.s + w0, R = f.r + mk * w0;
+        const double V = 1.0 / S;
+        d.PV[k].y = V;
+        d.RM[k] = make_double2(R, mk / R);
+        d.snnb[k] = f.n + 1;
+        d.rho[s] = R;
+        d.vol[s] = V;
+        d.nnb[s] = f.n + 1;
     }
 }
 
-// ---------------------------------------------------------------------------- pass B
+// ------------------------------------------------------------------ fp64 path: pass B
 // Fluid and inlet particles (rates used by the integrator):
 //   a_i   = (1/m_i) sum_j c_ij [ -p~_ij gW + (A_i + A_j).gW / 2
 //                                + eta~_ij u_ij (gW . r_ij) / (r_ij^2 + eta h^2) ] + g
@@ -180,71 +122,9 @@ __global__ void __launch_bounds__(TPB) k_pass_a(Dev d)
 // pbar_ij - p_i = rho_i (p_j - p_i)/(rho_i + rho_j) and p_i - p_avg,i = -sum_j (p_j - p_i)/N_i,
 // so that one pass over the neighbours suffices; the second part multiplies
 // G_i = sum_j c_ij gW, which is also the background-pressure sum.  The self pair contributes
-// nothing (gW = 0, p_j - p_i = 0) and is not listed.
+// exact zeros (gW = 0, p_j - p_i = 0).
 // Solid particles counted in the drag: F_i = sum_{j fluid} c_ij [ -p~_ij gW + eta~_ij
 // u_ij (gW . r_ij)/(r^2 + eta h^2) ] with u_ij = u_g,i - u_j (Eq. tvf-momentum_solid).
-struct BodyB32 {
-    const Dev &d;
-    float rx, ry;
-    float pi, Vi, rhoi, ui, vi, dui, dvi, mi_inv;
-    bool solid;
-    float a2h, inv_h, c2, nu2, nue2, eh2;
-    float ax = 0, ay = 0, ap = 0, gx = 0, gy = 0;
-    float axh = 0, axl = 0, ayh = 0, ayl = 0, aph = 0, apl = 0, gxh = 0, gxl = 0, gyh = 0, gyl = 0;
-    float sdp = 0;
-    int n = 0;
-    __device__ BodyB32(const Dev &dd, float x, float y) : d(dd), rx(x), ry(y)
-    {
-        a2h = dd.ph.a2hf; inv_h = dd.ph.inv_hf; c2 = dd.ph.c2f; nu2 = 2.0f * dd.ph.nuf;
-        nue2 = 2.0f * dd.ph.nuef; eh2 = dd.ph.eh2f;
-    }
-    __device__ void fold()
-    {
-        two_sum_acc(axh, axl, ax);
-        two_sum_acc(ayh, ayl, ay);
-        two_sum_acc(aph, apl, ap);
-        two_sum_acc(gxh, gxl, gx);
-        two_sum_acc(gyh, gyl, gy);
-        ax = ay = ap = gx = gy = 0.f;
-    }
-    __device__ void operator()(unsigned e)
-    {
-        float4 pj;
-        float dx, dy, r2;
-        const int j = geom32(d, e, rx, ry, pj, dx, dy, r2);
-        const float4 q = __ldg(d.Qf + j);  // (p, V, rho, m/rho)
-        const float dp = q.x - pi;
-        sdp += dp;
-        if (solid && (d.stag[j] & 0x7f) != FLUID) return;
-        const float4 bj = __ldg(d.Bf + j);  // (u, v, u~-u, v~-v)
-        const float inv_r = r2 > 0.f ? rsqrtf(r2) : 0.f;
-        const float dwq = quintic_dw(r2 * inv_r * inv_h);
-        const float F = a2h * dwq * inv_r;
-        const float gxv = F * dx, gyv = F * dy, gdotr = F * r2;
-        const float cij = Vi * Vi + q.y * q.y;
-        const float inv_rs = __fdividef(1.0f, rhoi + q.z);
-        const float e_ = rhoi * dp * inv_rs;
-        // eta~_ij (gW . r_ij)/(r^2 + eta h^2) = 2 nu hf,  hf = rho_i rho_j/(rho_i + rho_j) (...)
-        const float hf = rhoi * q.z * inv_rs * __fdividef(gdotr, r2 + eh2);
-        const float vis = nu2 * hf;
-        const float uij = ui - bj.x, vij = vi - bj.y;
-        const float cgx = cij * gxv, cgy = cij * gyv;
-        gx += cgx;
-        gy += cgy;
-        if (solid) {
-            ax += cij * (vis * uij) - e_ * cgx;
-            ay += cij * (vis * vij) - e_ * cgy;
-        } else {
-            const float Ai = rhoi * (dui * gxv + dvi * gyv);
-            const float Aj = q.z * (bj.z * gxv + bj.w * gyv);
-            ax += cij * (0.5f * (ui * Ai + bj.x * Aj) + vis * uij) - e_ * cgx;
-            ay += cij * (0.5f * (vi * Ai + bj.y * Aj) + vis * vij) - e_ * cgy;
-            ap += rhoi * c2 * q.w * (uij * gxv + vij * gyv) - cij * mi_inv * nue2 * hf * dp;
-        }
-        if ((++n & (FOLD - 1)) == 0) fold();
-    }
-};
-
 struct BodyB64 {
     const Dev &d;
     double qx, qy;
@@ -292,8 +172,7 @@ struct BodyB64 {
     }
 };
 
-template <int MIXED>
-__global__ void __launch_bounds__(TPB) k_pass_b(Dev d)
+__global__ void __launch_bounds__(TPB) k_pass_b64(Dev d)
 {
     __shared__ unsigned lst_all[LMAX * TPB];
     unsigned *lst = lst_all + threadIdx.x;
@@ -311,46 +190,527 @@ __global__ void __launch_bounds__(TPB) k_pass_b(Dev d)
         const int s = d.order[k];
         const int N = d.snnb[k];
         const double mi = d.m[s];
-        double sx, sy, spd, G0, G1, sdp, pi;
-        if (MIXED) {
-            BodyB32 f(d, pk.x, pk.y);
-            const float4 q = d.Qf[k];
-            const float4 b = d.Bf[k];
-            f.pi = q.x; f.Vi = q.y; f.rhoi = q.z; f.ui = b.x; f.vi = b.y; f.dui = b.z; f.dvi = b.w;
-            f.mi_inv = 1.0f / pk.z;
-            f.solid = solid;
-            listed_neighbors(d, k, xy.x, xy.y, cx, cy, pk.x, pk.y, lst, f);
-            f.fold();
-            sx = (double)f.axh + (double)f.axl;
-            sy = (double)f.ayh + (double)f.ayl;
-            spd = (double)f.aph + (double)f.apl;
-            G0 = (double)f.gxh + (double)f.gxl;
-            G1 = (double)f.gyh + (double)f.gyl;
-            sdp = f.sdp;
-            pi = q.x;
-        } else {
-            BodyB64 f(d, xy.x, xy.y);
-            const double2 pv = d.PV[k], rm = d.RM[k], uv = d.UV[k], duv = d.DUV[k];
-            f.pi = pv.x; f.Vi = pv.y; f.rhoi = rm.x; f.ui = uv.x; f.vi = uv.y;
-            f.dui = duv.x; f.dvi = duv.y;
-            f.mi_inv = 1.0 / d.Ms[k];
-            f.solid = solid;
-            listed_neighbors(d, k, xy.x, xy.y, cx, cy, pk.x, pk.y, lst, f);
-            sx = f.ax; sy = f.ay; spd = f.apd; G0 = f.gxs; G1 = f.gys; sdp = f.sdp;
-            pi = pv.x;
-        }
+        BodyB64 f(d, xy.x, xy.y);
+        const double2 pv = d.PV[k], rm = d.RM[k], uv = d.UV[k], duv = d.DUV[k];
+        f.pi = pv.x; f.Vi = pv.y; f.rhoi = rm.x; f.ui = uv.x; f.vi = uv.y;
+        f.dui = duv.x; f.dvi = duv.y;
+        f.mi_inv = 1.0 / d.Ms[k];
+        f.solid = solid;
+        listed_neighbors(d, k, xy.x, xy.y, cx, cy, pk.x, pk.y, lst, f);
         // -sum c p~ gW = -sum c (pbar - p_i) gW + (p_avg - p_i) G   (with p_avg) or - p_i G
-        const double corr = ph.use_pavg ? sdp / (double)N : -pi;
+        const double corr = ph.use_pavg ? f.sdp / (double)N : -pv.x;
         if (solid) {
-            d.fx[s] = sx + corr * G0;
-            d.fy[s] = sy + corr * G1;
+            d.fx[s] = f.ax + corr * f.gxs;
+            d.fy[s] = f.ay + corr * f.gys;
         } else {
-            d.au[s] = (sx + corr * G0) / mi + ph.gx;
-            d.av[s] = (sy + corr * G1) / mi + ph.gy;
-            d.ap[s] = spd;
-            d.abu[s] = -ph.pb / mi * G0;
-            d.abv[s] = -ph.pb / mi * G1;
+            d.au[s] = (f.ax + corr * f.gxs) / mi + ph.gx;
+            d.av[s] = (f.ay + corr * f.gys) / mi + ph.gy;
+            d.ap[s] = f.apd;
+            d.abu[s] = -ph.pb / mi * f.gxs;
+            d.abv[s] = -ph.pb / mi * f.gys;
         }
+    }
+}
+
+// ------------------------------------------------------------------ mixed-path pair bodies
+// fp32 arithmetic on the (x, y) pairs uses Blackwell's paired instructions (FADD2, FMUL2,
+// FFMA2); reciprocals and the inverse square root use the single-instruction approximations
+// (relative error ~2^-23).  Sums are accumulated per neighbour-cell row in fp32 and folded
+// into two-sum compensated (hi, lo) accumulators once per row.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ void two_sum_acc2(float2 &hi, float2 &lo, float2 b)
+{
+    const float2 s = __fadd2_rn(hi, b);
+    const float2 z = __fadd2_rn(s, f2(-hi.x, -hi.y));
+    const float2 e = __fadd2_rn(__fadd2_rn(hi, f2(-(s.x - z.x), -(s.y - z.y))),
+                                __fadd2_rn(b, f2(-z.x, -z.y)));
+    hi = s;
+    lo = __fadd2_rn(lo, e);
+}
+
+// r >= 0 from r^2, guarded so that coincident particles (r^2 = 0) give q ~ 0 where the kernel
+// derivative vanishes exactly: r^2 is raised to 1e-30 before the inverse square root.
+__device__ __forceinline__ float inv_r_of(float r2) { return rsqrt_approx(fmaxf(r2, 1e-30f)); }
+
+// w(q) and dw/dq of the quintic spline with t_k = max(k - q, 0) (see quintic_w/quintic_dw)
+__device__ __forceinline__ float w_fast(float q)
+{
+    const float t3 = fmaxf(3.f - q, 0.f), t2 = fmaxf(2.f - q, 0.f), t1 = fmaxf(1.f - q, 0.f);
+    const float2 s32 = __fmul2_rn(f2(t3, t2), f2(t3, t2));
+    const float2 q32 = __fmul2_rn(s32, s32);
+    const float2 p32 = __fmul2_rn(q32, f2(t3, t2));
+    const float s1 = t1 * t1;
+    return fmaf(15.f, s1 * s1 * t1, fmaf(-6.f, p32.y, p32.x));
+}
+
+__device__ __forceinline__ float dw_fast(float q)
+{
+    const float t3 = fmaxf(3.f - q, 0.f), t2 = fmaxf(2.f - q, 0.f), t1 = fmaxf(1.f - q, 0.f);
+    const float2 s32 = __fmul2_rn(f2(t3, t2), f2(t3, t2));
+    const float2 q32 = __fmul2_rn(s32, s32);
+    const float s1 = t1 * t1;
+    return -5.f * fmaf(15.f, s1 * s1, fmaf(-6.f, q32.y, q32.x));
+}
+
+// Pass A: sum of w(q_ij) and of m_j w(q_ij) over the neighbours (self included); alpha_2 is
+// applied once at the end.
+struct MixA {
+    float inv_h;
+    float s = 0.f, r = 0.f;
+    float2 hi = f2(0.f, 0.f), lo = f2(0.f, 0.f);  // (sum w, sum m w)
+    int n = 0;
+    __device__ __forceinline__ void add(float2 dd, float mj)
+    {
+        const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
+        const float q = r2 * inv_r_of(r2) * inv_h;
+        const float w = w_fast(q);
+        s += w;
+        r = fmaf(mj, w, r);
+        ++n;
+    }
+    __device__ __forceinline__ void fold()
+    {
+        two_sum_acc2(hi, lo, f2(s, r));
+        s = r = 0.f;
+    }
+};
+
+// Pass B body for a fluid / inlet particle i (SOLID = false) or a solid particle counted in
+// the drag (SOLID = true: fluid neighbours only, no A-term, no pressure rate).
+template <bool SOLID>
+struct MixB {
+    // i-side constants
+    float2 ui;       // (u_i, v_i)
+    float2 rdi;      // rho_i (u~_i - u_i, v~_i - v_i)
+    float pi, Vi2, rhoi, rhoic2, dif;  // dif = 2 nu_edac / m_i
+    float a2h, inv_h, nu2, eh2;
+    // per-row partial sums and compensated totals
+    float2 am = f2(0.f, 0.f), gg = f2(0.f, 0.f);
+    float ap = 0.f, sdp = 0.f;
+    float2 am_h = f2(0.f, 0.f), am_l = f2(0.f, 0.f), gg_h = f2(0.f, 0.f), gg_l = f2(0.f, 0.f);
+    float2 ap_hl = f2(0.f, 0.f);
+    // dd = r_i - r_j; q = (p, V, rho, m/rho); b = (u, v, u~-u, v~-v) of j
+    __device__ __forceinline__ void add(float2 dd, const float4 &q, const float4 &b, uint8_t tagj)
+    {
+        const float dp = q.x - pi;
+        sdp += dp;
+        if (SOLID && (tagj & 0x7f) != FLUID) return;
+        const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
+        const float ir = inv_r_of(r2);
+        const float F = a2h * dw_fast(r2 * ir * inv_h) * ir;   // gW = F r_ij
+        const float2 g = __fmul2_rn(f2s(F), dd);
+        const float gdotr = F * r2;
+        const float cij = fmaf(q.y, q.y, Vi2);
+        const float irs = rcp_approx(rhoi + q.z);
+        const float e = rhoi * dp * irs;                        // pbar_ij - p_i
+        const float hf = rhoi * q.z * irs * gdotr * rcp_approx(r2 + eh2);
+        const float2 uij = __fadd2_rn(ui, f2(-b.x, -b.y));
+        const float2 cg = __fmul2_rn(f2s(cij), g);
+        gg = __fadd2_rn(gg, cg);
+        float2 mom = __fmul2_rn(f2s(nu2 * hf), uij);            // viscous term
+        if (!SOLID) {
+            const float Ai = fmaf(rdi.x, g.x, rdi.y * g.y);      // A_i . gW / u_i
+            const float Aj = q.z * fmaf(b.z, g.x, b.w * g.y);    // A_j . gW / u_j
+            const float2 A = __ffma2_rn(f2(b.x, b.y), f2s(Aj), __fmul2_rn(ui, f2s(Ai)));
+            mom = __ffma2_rn(f2s(0.5f), A, mom);
+            const float div = fmaf(uij.x, g.x, uij.y * g.y);
+            ap = fmaf(rhoic2 * q.w, div, ap);
+            ap = fmaf(-cij * dif * hf, dp, ap);
+        }
+        am = __ffma2_rn(f2s(cij), mom, am);
+        am = __ffma2_rn(f2s(-e), cg, am);
+    }
+    __device__ __forceinline__ void fold()
+    {
+        two_sum_acc2(am_h, am_l, am);
+        two_sum_acc2(gg_h, gg_l, gg);
+        float s = ap_hl.x + ap, z = s - ap_hl.x;
+        ap_hl.y += (ap_hl.x - (s - z)) + (ap - z);
+        ap_hl.x = s;
+        am = gg = f2(0.f, 0.f);
+        ap = 0.f;
+    }
+};
+
+// ------------------------------------------------------------ cell-tiled mixed passes
+// A block owns a row segment of CT_TX cells.  It stages the particles of the 3 x (CT_TX + 2)
+// cells around the segment into shared memory once (positions relative to the tile origin,
+// fields of the pass), then each thread takes one particle of the segment.  Pass A lists
+// the particle's neighbours (itself included) as 16-bit shared-memory indices (phase 1),
+// evaluates its pair terms from shared memory (phase 2), and records the neighbours as a
+// 128-bit mask over the particle's candidate order; pass B iterates the set bits of that
+// mask instead of repeating the membership test.  Compensated sums are folded once per cell
+// row (pass A) or per 32 candidates (pass B).  A tile whose halo exceeds CT_HMAX particles
+// is processed from global memory instead (same membership test, same pair arithmetic), and
+// a particle with more than 128 candidates repeats the test in pass B.
+constexpr int CT_TX = 8;
+constexpr int CT_NV = CT_TX + 2;  // cells per staged row (halo included)
+constexpr int CT_TPB = 128;
+constexpr int CT_HMAX = 480;
+constexpr int CT_LMAX = 56;
+
+struct TileHdr {
+    int cstart[3][CT_NV + 1];  // shared index of each staged cell's first particle
+    int gstart[3][CT_NV];      // global index of that particle (-1: no such cell)
+    int H, i0, ni;
+};
+
+// Warp 0 builds the header: lane l < 3 CT_NV takes staged cell (r, v) = (l / CT_NV, l % CT_NV),
+// and a warp scan of the cell counts gives the shared-memory offsets.
+__device__ __forceinline__ void tile_setup(const Dev &d, int cx0, int cy, TileHdr &th)
+{
+    const Geo &g = d.g;
+    const int lane = threadIdx.x & 31;
+    const int txe = min(CT_TX, g.nx - cx0);  // cells of this segment
+    const int r = lane / CT_NV, v = lane - r * CT_NV;
+    bool ok = lane < 3 * CT_NV && v <= txe + 1;
+    int by = cy + r - 1, bx = cx0 + v - 1;
+    if (g.py) by = by < 0 ? by + g.ny : (by >= g.ny ? by - g.ny : by);
+    else ok = ok && by >= 0 && by < g.ny;
+    if (g.px) bx = bx < 0 ? bx + g.nx : (bx >= g.nx ? bx - g.nx : bx);
+    else ok = ok && bx >= 0 && bx < g.nx;
+    int a = -1, cnt = 0;
+    if (ok) {
+        const int c = by * g.nx + bx;
+        a = d.cell_start[c];
+        cnt = d.cell_start[c + 1] - a;
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane < 3 * CT_NV) {
+        th.cstart[r][v] = incl - cnt;
+        th.gstart[r][v] = a;
+        if (v == CT_NV - 1) th.cstart[r][CT_NV] = incl;
+    }
+    const int H = __shfl_sync(0xffffffffu, incl, 3 * CT_NV - 1);
+    const int own_lo = __shfl_sync(0xffffffffu, incl - cnt, CT_NV + 1);
+    const int own_hi = __shfl_sync(0xffffffffu, incl, CT_NV + txe);
+    const int i0 = __shfl_sync(0xffffffffu, a, CT_NV + 1);
+    if (lane == 0) {
+        th.H = H;
+        th.i0 = i0;
+        th.ni = own_hi - own_lo;
+    }
+}
+
+// Stage positions relative to the tile origin (lower-left corner of cell (cx0, cy)):
+// x = (x - cell x0) + (v - 1) sx, y likewise; fetch(t, j, P_j) stores the pass's fields.
+template <class Fetch>
+__device__ __forceinline__ void tile_stage(const Dev &d, const TileHdr &th, float2 *spos, int *sgj,
+                                           Fetch &&fetch)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int cv = w; cv < 3 * CT_NV; cv += CT_TPB / 32) {
+        const int r = cv / CT_NV, v = cv - r * CT_NV;
+        const int g0 = th.gstart[r][v];
+        if (g0 < 0) continue;
+        const int s0 = th.cstart[r][v], cnt = th.cstart[r][v + 1] - s0;
+        const float ox = (float)(v - 1) * d.g.sxf, oy = (float)(r - 1) * d.g.syf;
+        for (int m = lane; m < cnt; m += 32) {
+            const int j = g0 + m, t = s0 + m;
+            const float4 pj = d.P[j];
+            spos[t] = make_float2(pj.x + ox, pj.y + oy);
+            sgj[t] = j;
+            fetch(t, j, pj);
+        }
+    }
+}
+
+// Phase 1 in shared memory: the neighbours (itself included) of staged particle ti in
+// virtual cell vi of row 1; ends[r] receives the list length after row r.  When the list
+// fills, body(entry) is run on it and it restarts (fold points then fall at the flush).
+template <class Body>
+__device__ __forceinline__ void tile_neighbors(const Dev &d, const TileHdr &th, const float2 *spos,
+                                               const int *sgj, int ti, int vi, double qx, double qy,
+                                               unsigned short *lst, Body &&body, int (&ends)[3])
+{
+    const float2 pi = spos[ti];
+    const float hi2 = d.g.rc2_hi, lo2 = d.g.rc2_lo;
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int lo = th.cstart[r][vi - 1], hi = th.cstart[r][vi + 2];
+#pragma unroll 2
+        for (int t = lo; t < hi; ++t) {
+            const float2 pj = spos[t];
+            const float2 dd = __fadd2_rn(pi, f2(-pj.x, -pj.y));
+            const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
+            if (r2 >= hi2) continue;
+            if (r2 > lo2) {
+                const double2 xy = d.XY[sgj[t]];
+                double ex, ey;
+                if (!(exact_r2(d.g, qx, qy, xy.x, xy.y, ex, ey) < d.g.rc2)) continue;
+            }
+            lst[cnt * CT_TPB] = (unsigned short)t;
+            if (++cnt == CT_LMAX) {
+#pragma unroll 1
+                for (int c = 0; c < CT_LMAX; ++c) body(lst[c * CT_TPB], false);
+                body(0, true);
+                cnt = 0;
+#pragma unroll
+                for (int q = 0; q < r; ++q) ends[q] = 0;  // those entries are done
+            }
+        }
+        ends[r] = cnt;
+    }
+}
+
+// The candidate order of a staged particle in virtual cell vi: row 0, row 1, row 2, each the
+// shared-memory range of the three cells vi-1..vi+1.  Pass A and pass B stage the same tile
+// from the same cell table, so a candidate index means the same neighbour in both.
+struct CandRows {
+    int lo0, lo1, lo2, l0, l01, tot;
+    __device__ __forceinline__ CandRows(const TileHdr &th, int vi)
+    {
+        lo0 = th.cstart[0][vi - 1];
+        lo1 = th.cstart[1][vi - 1];
+        lo2 = th.cstart[2][vi - 1];
+        l0 = th.cstart[0][vi + 2] - lo0;
+        l01 = l0 + th.cstart[1][vi + 2] - lo1;
+        tot = l01 + th.cstart[2][vi + 2] - lo2;
+    }
+    __device__ __forceinline__ int cand_of(int t) const
+    {
+        return t < lo0 + l0 ? t - lo0 : (t < lo1 + (l01 - l0) ? t - lo1 + l0 : t - lo2 + l01);
+    }
+    __device__ __forceinline__ int smem_of(int c) const
+    {
+        return c < l0 ? lo0 + c : (c < l01 ? lo1 + c - l0 : lo2 + c - l01);
+    }
+};
+
+__device__ __forceinline__ int tile_of_block(const Dev &d, int &cx0, int &cy)
+{
+    const int tpr = (d.g.nx + CT_TX - 1) / CT_TX;
+    cy = blockIdx.x / tpr;
+    cx0 = (blockIdx.x - cy * tpr) * CT_TX;
+    return cy < d.g.ny;
+}
+
+// Global-memory walk for tiles whose halo does not fit: f(dd, j) over the neighbours of k
+// (itself included), folding after each row of cells.
+template <class F, class Fold>
+__device__ __forceinline__ void global_neighbors(const Dev &d, int k, const float4 &pk, double qx,
+                                                 double qy, F &&f, Fold &&fold)
+{
+    const int c = d.cellk[k];
+    const int cx = c % d.g.nx, cy = c / d.g.nx;
+    for_block(d, cx, cy, [&](int ox, int oy, int j0, int j1) {
+        const float rxo = pk.x - (float)ox * d.g.sxf, ryo = pk.y - (float)oy * d.g.syf;
+        for (int j = j0; j < j1; ++j) {
+            float dxf, dyf, r2f;
+            const float4 pj = __ldg(d.P + j);
+            if (!is_member(d, rxo, ryo, pj, j, qx, qy, dxf, dyf, r2f)) continue;
+            f(make_float2(dxf, dyf), j, pj);
+        }
+        if (ox == 1) fold();
+    });
+    fold();
+}
+
+__global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled(Dev d)
+{
+    __shared__ TileHdr th;
+    __shared__ float2 spos[CT_HMAX];
+    __shared__ float smass[CT_HMAX];
+    __shared__ int sgj[CT_HMAX];
+    __shared__ unsigned short lst_all[CT_LMAX * CT_TPB];
+    int cx0, cy;
+    if (!tile_of_block(d, cx0, cy)) return;
+    if (threadIdx.x < 32) tile_setup(d, cx0, cy, th);
+    __syncthreads();
+    const bool fits = th.H <= CT_HMAX;
+    if (fits) tile_stage(d, th, spos, sgj, [&](int t, int, const float4 &pj) { smass[t] = pj.z; });
+    __syncthreads();
+    unsigned short *lst = lst_all + threadIdx.x;
+    const float a2 = d.ph.a2f;
+    for (int ii = threadIdx.x; ii < th.ni; ii += CT_TPB) {
+        const int k = th.i0 + ii;
+        const float4 pk = d.P[k];
+        const double2 xy = d.XY[k];
+        MixA f;
+        f.inv_h = d.ph.inv_hf;
+        if (fits) {
+            const int ti = th.cstart[1][1] + ii;
+            const int vi = d.cellk[k] - cy * d.g.nx - cx0 + 1;
+            const float2 pi = spos[ti];
+            const CandRows cr(th, vi);
+            unsigned m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+            int ends[3];
+            auto body = [&](unsigned short t, bool flush) {
+                if (flush) { f.fold(); return; }
+                const float2 pj = spos[t];
+                f.add(__fadd2_rn(pi, f2(-pj.x, -pj.y)), smass[t]);
+                // neighbour mask over the candidate order, reused by pass B
+                const int c = cr.cand_of(t);
+                const unsigned bit = 1u << (c & 31);
+                const int w = c >> 5;
+                m0 |= w == 0 ? bit : 0u;
+                m1 |= w == 1 ? bit : 0u;
+                m2 |= w == 2 ? bit : 0u;
+                m3 |= w == 3 ? bit : 0u;
+            };
+            tile_neighbors(d, th, spos, sgj, ti, vi, xy.x, xy.y, lst, body, ends);
+            int c = 0;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+#pragma unroll 1
+                for (; c < ends[r]; ++c) body(lst[c * CT_TPB], false);
+                f.fold();
+            }
+            d.nbm[k] = make_uint4(m0, m1, m2, m3);
+        } else {
+            global_neighbors(d, k, pk, xy.x, xy.y,
+                             [&](float2 dd, int, const float4 &pj) { f.add(dd, pj.z); },
+                             [&]() { f.fold(); });
+        }
+        const float S = a2 * (f.hi.x + f.lo.x), R = a2 * (f.hi.y + f.lo.y);
+        const float V = 1.0f / S;
+        const float4 q = d.Qf[k];
+        d.Qf[k] = make_float4(q.x, V, R, pk.z / R);
+        d.snnb[k] = f.n;
+        const int s = d.order[k];
+        d.rho[s] = (double)R;
+        d.vol[s] = (double)V;
+        d.nnb[s] = f.n;
+    }
+}
+
+template <bool SOLID>
+__device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th, bool fits, int cy,
+                                                int cx0, int ii, const float2 *spos, const float4 *sq,
+                                                const float4 *sb, const uint8_t *stg, const int *sgj)
+{
+    const Phys &ph = d.ph;
+    const int k = th.i0 + ii;
+    const float4 pk = d.P[k];
+    const double2 xy = d.XY[k];
+    const float4 q = d.Qf[k];
+    const float4 b = d.Bf[k];
+    MixB<SOLID> f;
+    f.ui = f2(b.x, b.y);
+    f.rdi = f2(q.z * b.z, q.z * b.w);
+    f.pi = q.x; f.Vi2 = q.y * q.y; f.rhoi = q.z; f.rhoic2 = q.z * ph.c2f;
+    f.dif = 2.0f * ph.nuef / pk.z;
+    f.a2h = ph.a2hf; f.inv_h = ph.inv_hf; f.nu2 = 2.0f * ph.nuf; f.eh2 = ph.eh2f;
+    if (fits) {
+        const int ti = th.cstart[1][1] + ii;
+        const int vi = d.cellk[k] - cy * d.g.nx - cx0 + 1;
+        const float2 pi = spos[ti];
+        const CandRows cr(th, vi);
+        auto body = [&](int tj) {
+            const float2 pj = spos[tj];
+            f.add(__fadd2_rn(pi, f2(-pj.x, -pj.y)), sq[tj], sb[tj], stg[tj]);
+        };
+        if (cr.tot <= 128) {
+            // the neighbours pass A found, as set bits of the candidate order
+            const uint4 m = d.nbm[k];
+            unsigned w0 = m.x, w1 = m.y, w2 = m.z, w3 = m.w;
+            const int np = __popc(w0) + __popc(w1) + __popc(w2) + __popc(w3);
+            int base = 0;
+#pragma unroll 1
+            for (int it = 0; it < np; ++it) {
+                while (w0 == 0u) {
+                    w0 = w1; w1 = w2; w2 = w3; w3 = 0u;
+                    base += 32;
+                    f.fold();
+                }
+                const int b = __ffs(w0) - 1;
+                w0 &= w0 - 1u;
+                body(cr.smem_of(base + b));
+            }
+        } else {
+#pragma unroll 1
+            for (int c = 0; c < cr.tot; ++c) {
+                const int tj = cr.smem_of(c);
+                const float2 pj = spos[tj];
+                const float2 dd = __fadd2_rn(pi, f2(-pj.x, -pj.y));
+                const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
+                if (r2 >= d.g.rc2_hi) continue;
+                if (r2 > d.g.rc2_lo) {
+                    const double2 xj = d.XY[sgj[tj]];
+                    double ex, ey;
+                    if (!(exact_r2(d.g, xy.x, xy.y, xj.x, xj.y, ex, ey) < d.g.rc2)) continue;
+                }
+                body(tj);
+            }
+        }
+        f.fold();
+    } else {
+        global_neighbors(d, k, pk, xy.x, xy.y,
+                         [&](float2 dd, int j, const float4 &) {
+                             f.add(dd, __ldg(d.Qf + j), __ldg(d.Bf + j), d.stag[j]);
+                         },
+                         [&]() { f.fold(); });
+    }
+    const double sx = (double)f.am_h.x + (double)f.am_l.x;
+    const double sy = (double)f.am_h.y + (double)f.am_l.y;
+    const double G0 = (double)f.gg_h.x + (double)f.gg_l.x;
+    const double G1 = (double)f.gg_h.y + (double)f.gg_l.y;
+    const int N = d.snnb[k];
+    // -sum c p~ gW = -sum c (pbar - p_i) gW + (p_avg - p_i) G   (with p_avg) or - p_i G
+    const double corr = ph.use_pavg ? (double)f.sdp / (double)N : -(double)q.x;
+    const int s = d.order[k];
+    if (SOLID) {
+        d.fx[s] = sx + corr * G0;
+        d.fy[s] = sy + corr * G1;
+    } else {
+        const double mi = d.m[s];
+        d.au[s] = (sx + corr * G0) / mi + ph.gx;
+        d.av[s] = (sy + corr * G1) / mi + ph.gy;
+        d.ap[s] = (double)f.ap_hl.x + (double)f.ap_hl.y;
+        d.abu[s] = -ph.pb / mi * G0;
+        d.abv[s] = -ph.pb / mi * G1;
+    }
+}
+
+__global__ void __launch_bounds__(CT_TPB) k_pass_b_tiled(Dev d)
+{
+    __shared__ TileHdr th;
+    __shared__ float2 spos[CT_HMAX];
+    __shared__ float4 sq[CT_HMAX];
+    __shared__ float4 sb[CT_HMAX];
+    __shared__ uint8_t stg[CT_HMAX];
+    __shared__ int sgj[CT_HMAX];
+    const Phys &ph = d.ph;
+    int cx0, cy;
+    if (!tile_of_block(d, cx0, cy)) return;
+    if (threadIdx.x < 32) tile_setup(d, cx0, cy, th);
+    __syncthreads();
+    const bool fits = th.H <= CT_HMAX;
+    if (fits)
+        tile_stage(d, th, spos, sgj, [&](int t, int j, const float4 &) {
+            sq[t] = d.Qf[j];
+            sb[t] = d.Bf[j];
+            stg[t] = d.stag[j];
+        });
+    __syncthreads();
+    for (int ii = threadIdx.x; ii < th.ni; ii += CT_TPB) {
+        const int t = d.stag[th.i0 + ii] & 0x7f;
+        if (t == FLUID || t == INLET)
+            pass_b_particle<false>(d, th, fits, cy, cx0, ii, spos, sq, sb, stg, sgj);
+        else if ((t == WALL && ph.wall_drag[0]) || (t == SLIPWALL && ph.wall_drag[1]))
+            pass_b_particle<true>(d, th, fits, cy, cx0, ii, spos, sq, sb, stg, sgj);
     }
 }
 
@@ -373,22 +733,57 @@ template <int MIXED, class F>
 __device__ __forceinline__ void lane_neighbors(const Dev &d, int lane, double qx, double qy, int cx,
                                                int cy, float rx, float ry, F &&f)
 {
-    for_block(d, cx, cy, [&](int ox, int oy, int j0, int j1) {
-        const float rxo = rx - (float)ox * d.g.sxf, ryo = ry - (float)oy * d.g.syf;
-#pragma unroll 1
-        for (int j = j0 + lane; j < j1; j += 32) {
-            float dxf, dyf, r2f;
-            if (!is_member(d, rxo, ryo, __ldg(d.P + j), j, qx, qy, dxf, dyf, r2f)) continue;
-            if (MIXED) {
-                f(j, dxf, dyf, r2f);
-            } else {
-                const double2 xy = d.XY[j];
-                double dx, dy;
-                const double r2 = exact_r2(d.g, qx, qy, xy.x, xy.y, dx, dy);
-                f(j, dx, dy, r2);
-            }
+    // lanes 0..8 look up the 9 cells of the block; a warp scan concatenates their ranges so
+    // that the 32 lanes share the candidates evenly instead of walking cell after cell
+    const Geo &g = d.g;
+    int a = 0, cnt = 0;
+    if (lane < 9) {
+        const int oy = lane / 3 - 1, ox = lane % 3 - 1;
+        int by = cy + oy, bx = cx + ox;
+        bool ok = true;
+        if (g.py) by = by < 0 ? by + g.ny : (by >= g.ny ? by - g.ny : by);
+        else ok = by >= 0 && by < g.ny;
+        if (g.px) bx = bx < 0 ? bx + g.nx : (bx >= g.nx ? bx - g.nx : bx);
+        else ok = ok && bx >= 0 && bx < g.nx;
+        if (ok) {
+            const int c = by * g.nx + bx;
+            a = __ldg(d.cell_start + c);
+            cnt = __ldg(d.cell_start + c + 1) - a;
         }
-    });
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    int ex[9], st[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        ex[q] = __shfl_sync(0xffffffffu, incl, q);  // inclusive end of cell q
+        st[q] = __shfl_sync(0xffffffffu, a, q);
+    }
+    const int total = ex[8];
+#pragma unroll 1
+    for (int t = lane; t < total; t += 32) {
+        int q = 0, lo = 0;
+#pragma unroll
+        for (int z = 0; z < 8; ++z)
+            if (t >= ex[z]) { q = z + 1; lo = ex[z]; }
+        const int j = st[q] + (t - lo);
+        const int oy = q / 3 - 1, ox = q % 3 - 1;
+        const float rxo = rx - (float)ox * g.sxf, ryo = ry - (float)oy * g.syf;
+        float dxf, dyf, r2f;
+        if (!is_member(d, rxo, ryo, __ldg(d.P + j), j, qx, qy, dxf, dyf, r2f)) continue;
+        if (MIXED) {
+            f(j, dxf, dyf, r2f);
+        } else {
+            const double2 xy = d.XY[j];
+            double dx, dy;
+            const double r2 = exact_r2(g, qx, qy, xy.x, xy.y, dx, dy);
+            f(j, dx, dy, r2);
+        }
+    }
 }
 
 template <int MIXED>
@@ -502,29 +897,32 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
             const int cy = cell_coord(yk, g.y_min, g.inv_sy, g.ny);
             const float rx = (float)(xk - (g.x_min + (double)cx * g.sx));
             const float ry = (float)(yk - (g.y_min + (double)cy * g.sy));
-            T a[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-            lane_neighbors<MIXED>(d, lane, xk, yk, cx, cy, rx, ry, [&](int l, T dx, T dy, T r2) {
+            // fp64 on both paths: with disordered particles the system can be ill-conditioned
+            // and fp32 moment sums would lose the solution
+            double a[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            lane_neighbors<0>(d, lane, xk, yk, cx, cy, rx, ry, [&](int l, double dx, double dy,
+                                                                   double r2) {
                 if ((d.stag[l] & 0x7f) != FLUID) return;
-                const T xlk = -dx, ylk = -dy;  // the walk gives r_k - r_l
-                const T r = sqrt_t<T>(r2);
+                const double xlk = -dx, ylk = -dy;  // the walk gives r_k - r_l
+                const double r = sqrt(r2);
                 double p, u, v, Vl;
                 fluid_fields<MIXED>(d, l, p, u, v, Vl);
-                const T w = a2 * quintic_w(r * inv_h);
-                T wx = 0, wy = 0;
-                if (r > (T)0) {
-                    const T dw = a2h * quintic_dw(r * inv_h);
+                const double w = ph.a2 * quintic_w(r * ph.inv_h);
+                double wx = 0, wy = 0;
+                if (r > 0.0) {
+                    const double dw = ph.a2h * quintic_dw(r * ph.inv_h);
                     wx = dw * xlk / r;
                     wy = dw * ylk / r;
                 }
-                const T row[3] = {w * (T)Vl, wx * (T)Vl, wy * (T)Vl};
+                const double row[3] = {w * Vl, wx * Vl, wy * Vl};
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     a[3 * q + 0] += row[q];
                     a[3 * q + 1] += xlk * row[q];
                     a[3 * q + 2] += ylk * row[q];
-                    a[9 + q] += (T)p * row[q];
+                    a[9 + q] += p * row[q];
                 }
-                a[12] += (T)1;
+                a[12] += 1.0;
             });
             warp_sum(a);
             if (lane == 0) {
@@ -534,7 +932,7 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                     bb[q] = (double)a[9 + q];
                 }
                 double pk = 0.0, gxp = 0.0, gyp = 0.0;
-                if (a[12] > (T)0) {
+                if (a[12] > 0.0) {
                     const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
                                        M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
                                        M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
@@ -629,10 +1027,12 @@ int grid_for(int n, int tpb)
 
 }  // namespace
 
+int tiles(const Dev &d) { return d.g.ny * ((d.g.nx + CT_TX - 1) / CT_TX); }
+
 int launch_pass_a(const Dev &d, cudaStream_t s, int mixed)
 {
-    if (mixed) k_pass_a<1><<<grid_for(d.cap, TPB), TPB, 0, s>>>(d);
-    else k_pass_a<0><<<grid_for(d.cap, TPB), TPB, 0, s>>>(d);
+    if (mixed) k_pass_a_tiled<<<tiles(d), CT_TPB, 0, s>>>(d);
+    else k_pass_a64<<<grid_for(d.cap, TPB), TPB, 0, s>>>(d);
     return 1;
 }
 
@@ -647,8 +1047,8 @@ int launch_boundary(const Dev &d, cudaStream_t s, int mixed, int end_of_step)
 
 int launch_pass_b(const Dev &d, cudaStream_t s, int mixed)
 {
-    if (mixed) k_pass_b<1><<<grid_for(d.cap, TPB), TPB, 0, s>>>(d);
-    else k_pass_b<0><<<grid_for(d.cap, TPB), TPB, 0, s>>>(d);
+    if (mixed) k_pass_b_tiled<<<tiles(d), CT_TPB, 0, s>>>(d);
+    else k_pass_b64<<<grid_for(d.cap, TPB), TPB, 0, s>>>(d);
     return 1;
 }
 
