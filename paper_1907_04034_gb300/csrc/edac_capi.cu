@@ -128,6 +128,10 @@ void make_phys(const edac_params &P, Phys &ph)
     ph.nuef = (float)ph.nu_e;
     ph.eh2f = (float)ph.eh2;
     ph.w0f = (float)(ph.a2 * 66.0);  // W(0) = alpha_2 w(0), w(0) = 3^5 - 6 2^5 + 15
+    ph.gxf = (float)P.gx;
+    ph.gyf = (float)P.gy;
+    ph.pbf = (float)P.pb;
+    ph.inv_2rcf = (float)ph.inv_2rc;
     ph.use_pavg = P.use_pavg ? 1 : 0;
     ph.has_inlet = 0;
     ph.n_modes = 0;

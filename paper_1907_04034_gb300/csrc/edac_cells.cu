@@ -233,6 +233,12 @@ __device__ __forceinline__ void ring_sample(const Dev &d, int s, double un, doub
     pbv = (double)sp * ph.inv_navg;
 }
 
+// Finite test on the exponent bits (integer pipe; the fp64 pipe is the scarce one here).
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+
 template <bool CORR, int MIXED>
 __global__ void k_stage(Dev d, double tau)
 {
@@ -259,8 +265,8 @@ __global__ void k_stage(Dev d, double tau)
             const double pn = p0 + tau * d.ap[s];
             d.u[s] = un; d.v[s] = vn; d.ut[s] = utn; d.vt[s] = vtn;
             d.x[s] = xn; d.y[s] = yn; d.p[s] = pn;
-            if (!(isfinite(xn) && isfinite(yn) && isfinite(un) && isfinite(vn) && isfinite(pn) &&
-                  isfinite(utn) && isfinite(vtn)))
+            if (!(finite_bits(xn) & finite_bits(yn) & finite_bits(un) & finite_bits(vn) &
+                  finite_bits(pn) & finite_bits(utn) & finite_bits(vtn)))
                 set_err(d, ERR_NONFINITE);
             if (CORR && ph.has_outlet) {
                 double ub, vb, pbv;

@@ -39,7 +39,7 @@ struct Phys {
     double h, inv_h, a2, a2h;        // alpha_2 = 7/(478 pi h^2), alpha_2 / h
     double rho0, cs, c2, nu, nu_e, eh2, pb, gx, gy, dt, U;
     double inv_2rc, inv_navg;        // 1/(2 rho0 c_s), 1/n_avg
-    float inv_hf, a2f, a2hf, c2f, nuf, nuef, eh2f, w0f;
+    float inv_hf, a2f, a2hf, c2f, nuf, nuef, eh2f, w0f, gxf, gyf, pbf, inv_2rcf;
     int use_pavg;
     int has_inlet, n_modes;
     double x_in, L_in, in_y0, in_H;
@@ -141,6 +141,19 @@ __device__ __forceinline__ T quintic_dw(T q)
     T t1 = q < T(1) ? T(1) - q : T(0);
     T a = t3 * t3, b = t2 * t2, c = t1 * t1;
     return T(-5) * (a * a - T(6) * (b * b) + T(15) * (c * c));
+}
+
+// w(q) and dw/dq together (the branch terms t_k and their squares are shared).
+template <class T>
+__device__ __forceinline__ void quintic_w_dw(T q, T &w, T &dw)
+{
+    const T t3 = q < T(3) ? T(3) - q : T(0);
+    const T t2 = q < T(2) ? T(2) - q : T(0);
+    const T t1 = q < T(1) ? T(1) - q : T(0);
+    const T a = t3 * t3, b = t2 * t2, c = t1 * t1;
+    const T a4 = a * a, b4 = b * b, c4 = c * c;
+    w = t3 * a4 - T(6) * (t2 * b4) + T(15) * (t1 * c4);
+    dw = T(-5) * (a4 - T(6) * b4 + T(15) * c4);
 }
 
 // Canonical fp64 separation r_i - r_j with the minimum image on periodic axes and

@@ -437,8 +437,9 @@ __device__ __forceinline__ void tile_stage(const Dev &d, const TileHdr &th, floa
 }
 
 // Phase 1 in shared memory: the neighbours (itself included) of staged particle ti in
-// virtual cell vi of row 1; ends[r] receives the list length after row r.  When the list
-// fills, body(entry) is run on it and it restarts (fold points then fall at the flush).
+// virtual cell vi of row 1, listed by candidate index (the order of CandRows); ends[r]
+// receives the list length after row r.  When the list fills, body(entry) is run on it and
+// it restarts (the fold points then fall at the flush).
 template <class Body>
 __device__ __forceinline__ void tile_neighbors(const Dev &d, const TileHdr &th, const float2 *spos,
                                                const int *sgj, int ti, int vi, double qx, double qy,
@@ -446,12 +447,12 @@ __device__ __forceinline__ void tile_neighbors(const Dev &d, const TileHdr &th, 
 {
     const float2 pi = spos[ti];
     const float hi2 = d.g.rc2_hi, lo2 = d.g.rc2_lo;
-    int cnt = 0;
+    int cnt = 0, c = 0;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         const int lo = th.cstart[r][vi - 1], hi = th.cstart[r][vi + 2];
 #pragma unroll 2
-        for (int t = lo; t < hi; ++t) {
+        for (int t = lo; t < hi; ++t, ++c) {
             const float2 pj = spos[t];
             const float2 dd = __fadd2_rn(pi, f2(-pj.x, -pj.y));
             const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
@@ -461,10 +462,10 @@ __device__ __forceinline__ void tile_neighbors(const Dev &d, const TileHdr &th, 
                 double ex, ey;
                 if (!(exact_r2(d.g, qx, qy, xy.x, xy.y, ex, ey) < d.g.rc2)) continue;
             }
-            lst[cnt * CT_TPB] = (unsigned short)t;
+            lst[cnt * CT_TPB] = (unsigned short)c;
             if (++cnt == CT_LMAX) {
 #pragma unroll 1
-                for (int c = 0; c < CT_LMAX; ++c) body(lst[c * CT_TPB], false);
+                for (int e = 0; e < CT_LMAX; ++e) body(lst[e * CT_TPB], false);
                 body(0, true);
                 cnt = 0;
 #pragma unroll
@@ -488,10 +489,6 @@ struct CandRows {
         l0 = th.cstart[0][vi + 2] - lo0;
         l01 = l0 + th.cstart[1][vi + 2] - lo1;
         tot = l01 + th.cstart[2][vi + 2] - lo2;
-    }
-    __device__ __forceinline__ int cand_of(int t) const
-    {
-        return t < lo0 + l0 ? t - lo0 : (t < lo1 + (l01 - l0) ? t - lo1 + l0 : t - lo2 + l01);
     }
     __device__ __forceinline__ int smem_of(int c) const
     {
@@ -555,20 +552,28 @@ __global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled(Dev d)
             const int vi = d.cellk[k] - cy * d.g.nx - cx0 + 1;
             const float2 pi = spos[ti];
             const CandRows cr(th, vi);
-            unsigned m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+            // neighbour mask over the candidate order, reused by pass B: entries arrive in
+            // increasing candidate index, so one word is built at a time
+            unsigned m0 = 0, m1 = 0, m2 = 0, m3 = 0, cur = 0;
+            int wcur = 0;
+            auto put_word = [&]() {
+                m0 = wcur == 0 ? cur : m0;
+                m1 = wcur == 1 ? cur : m1;
+                m2 = wcur == 2 ? cur : m2;
+                m3 = wcur == 3 ? cur : m3;
+            };
             int ends[3];
-            auto body = [&](unsigned short t, bool flush) {
+            auto body = [&](unsigned short c, bool flush) {
                 if (flush) { f.fold(); return; }
+                const int t = cr.smem_of(c);
                 const float2 pj = spos[t];
                 f.add(__fadd2_rn(pi, f2(-pj.x, -pj.y)), smass[t]);
-                // neighbour mask over the candidate order, reused by pass B
-                const int c = cr.cand_of(t);
-                const unsigned bit = 1u << (c & 31);
-                const int w = c >> 5;
-                m0 |= w == 0 ? bit : 0u;
-                m1 |= w == 1 ? bit : 0u;
-                m2 |= w == 2 ? bit : 0u;
-                m3 |= w == 3 ? bit : 0u;
+                if ((c >> 5) != wcur) {
+                    put_word();
+                    wcur = c >> 5;
+                    cur = 0;
+                }
+                cur |= 1u << (c & 31);
             };
             tile_neighbors(d, th, spos, sgj, ti, vi, xy.x, xy.y, lst, body, ends);
             int c = 0;
@@ -578,6 +583,7 @@ __global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled(Dev d)
                 for (; c < ends[r]; ++c) body(lst[c * CT_TPB], false);
                 f.fold();
             }
+            put_word();
             d.nbm[k] = make_uint4(m0, m1, m2, m3);
         } else {
             global_neighbors(d, k, pk, xy.x, xy.y,
@@ -663,24 +669,25 @@ __device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th,
                          },
                          [&]() { f.fold(); });
     }
-    const double sx = (double)f.am_h.x + (double)f.am_l.x;
-    const double sy = (double)f.am_h.y + (double)f.am_l.y;
-    const double G0 = (double)f.gg_h.x + (double)f.gg_l.x;
-    const double G1 = (double)f.gg_h.y + (double)f.gg_l.y;
+    // fp32 epilogue (the fp64 pipe of this part is a small fraction of the fp32 one): only the
+    // stores of the fp64 rate arrays convert
+    const float sx = f.am_h.x + f.am_l.x, sy = f.am_h.y + f.am_l.y;
+    const float G0 = f.gg_h.x + f.gg_l.x, G1 = f.gg_h.y + f.gg_l.y;
     const int N = d.snnb[k];
     // -sum c p~ gW = -sum c (pbar - p_i) gW + (p_avg - p_i) G   (with p_avg) or - p_i G
-    const double corr = ph.use_pavg ? (double)f.sdp / (double)N : -(double)q.x;
+    const float corr = ph.use_pavg ? f.sdp / (float)N : -q.x;
     const int s = d.order[k];
     if (SOLID) {
-        d.fx[s] = sx + corr * G0;
-        d.fy[s] = sy + corr * G1;
+        d.fx[s] = (double)fmaf(corr, G0, sx);
+        d.fy[s] = (double)fmaf(corr, G1, sy);
     } else {
-        const double mi = d.m[s];
-        d.au[s] = (sx + corr * G0) / mi + ph.gx;
-        d.av[s] = (sy + corr * G1) / mi + ph.gy;
-        d.ap[s] = (double)f.ap_hl.x + (double)f.ap_hl.y;
-        d.abu[s] = -ph.pb / mi * G0;
-        d.abv[s] = -ph.pb / mi * G1;
+        const float mi_inv = 1.0f / pk.z;
+        d.au[s] = (double)fmaf(fmaf(corr, G0, sx), mi_inv, ph.gxf);
+        d.av[s] = (double)fmaf(fmaf(corr, G1, sy), mi_inv, ph.gyf);
+        d.ap[s] = (double)(f.ap_hl.x + f.ap_hl.y);
+        const float pbm = -ph.pbf * mi_inv;
+        d.abu[s] = (double)(pbm * G0);
+        d.abv[s] = (double)(pbm * G1);
     }
 }
 
@@ -757,20 +764,20 @@ __device__ __forceinline__ void lane_neighbors(const Dev &d, int lane, double qx
         const int y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
     }
-    int ex[9], st[9];
+    int ex[8];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        ex[q] = __shfl_sync(0xffffffffu, incl, q);  // inclusive end of cell q
-        st[q] = __shfl_sync(0xffffffffu, a, q);
-    }
-    const int total = ex[8];
+    for (int q = 0; q < 8; ++q) ex[q] = __shfl_sync(0xffffffffu, incl, q);  // end of cell q
+    const int total = __shfl_sync(0xffffffffu, incl, 8);
+    const int excl = incl - cnt;
+    const int trips = (total + 31) >> 5;  // uniform, so that the shuffles see the whole warp
 #pragma unroll 1
-    for (int t = lane; t < total; t += 32) {
-        int q = 0, lo = 0;
+    for (int it = 0; it < trips; ++it) {
+        const int t = it * 32 + lane;
+        int q = 0;
 #pragma unroll
-        for (int z = 0; z < 8; ++z)
-            if (t >= ex[z]) { q = z + 1; lo = ex[z]; }
-        const int j = st[q] + (t - lo);
+        for (int z = 0; z < 8; ++z) q += (t >= ex[z]);
+        const int j = __shfl_sync(0xffffffffu, a, q) + (t - __shfl_sync(0xffffffffu, excl, q));
+        if (t >= total) continue;
         const int oy = q / 3 - 1, ox = q % 3 - 1;
         const float rxo = rx - (float)ox * g.sxf, ryo = ry - (float)oy * g.syf;
         float dxf, dyf, r2f;
@@ -786,49 +793,72 @@ __device__ __forceinline__ void lane_neighbors(const Dev &d, int lane, double qx
     }
 }
 
-template <int MIXED>
-__device__ __forceinline__ void fluid_fields(const Dev &d, int j, double &p, double &u, double &v,
-                                             double &mrho)
+// (p, u, v, m/rho) of particle j in the path's own precision
+template <int MIXED, class T>
+__device__ __forceinline__ void fluid_fields(const Dev &d, int j, T &p, T &u, T &v, T &mrho)
 {
     if (MIXED) {
         const float4 q = d.Qf[j];
         const float4 b = d.Bf[j];
-        p = q.x; u = b.x; v = b.y; mrho = q.w;
+        p = (T)q.x; u = (T)b.x; v = (T)b.y; mrho = (T)q.w;
     } else {
         const double2 pv = d.PV[j], uv = d.UV[j];
-        p = pv.x; u = uv.x; v = uv.y; mrho = d.RM[j].y;
+        p = (T)pv.x; u = (T)uv.x; v = (T)uv.y; mrho = (T)d.RM[j].y;
     }
+}
+
+// 1/sqrt(x) in fp64 for x > 0: the fp32 hardware estimate refined by two Newton-Raphson
+// steps on f(y) = 1/y^2 - x, y <- y (3 - x y^2)/2; each step squares the relative error
+// (2^-23 -> 2^-46 -> below the fp64 rounding), with no fp64 division or square root.
+__device__ __forceinline__ double rsqrt_newton(double x)
+{
+    double y = (double)rsqrt_approx((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y;
 }
 
 template <class T>
 __device__ __forceinline__ T sqrt_t(T x);
 template <>
-__device__ __forceinline__ float sqrt_t<float>(float x) { return fast_r(x); }
+__device__ __forceinline__ float sqrt_t<float>(float x) { return x * rsqrt_approx(fmaxf(x, 1e-30f)); }
 template <>
 __device__ __forceinline__ double sqrt_t<double>(double x) { return sqrt(x); }
 
-// Gaussian elimination with partial pivoting on a 3x3 system.
-__device__ bool solve3(double A[3][3], double b[3], double x[3])
+// Gaussian elimination with partial pivoting on a 3x3 system, kept in registers (row
+// exchanges by selects).  Returns false on a zero pivot.
+__device__ __forceinline__ void swap_rows(bool c, double &a0, double &a1, double &a2, double &ab,
+                                          double &b0, double &b1, double &b2, double &bb)
 {
-    int piv[3] = {0, 1, 2};
-    for (int c = 0; c < 3; ++c) {
-        int best = c;
-        for (int r = c + 1; r < 3; ++r)
-            if (fabs(A[piv[r]][c]) > fabs(A[piv[best]][c])) best = r;
-        const int tmp = piv[c]; piv[c] = piv[best]; piv[best] = tmp;
-        const double dg = A[piv[c]][c];
-        if (dg == 0.0) return false;
-        for (int r = c + 1; r < 3; ++r) {
-            const double f = A[piv[r]][c] / dg;
-            for (int k = c; k < 3; ++k) A[piv[r]][k] -= f * A[piv[c]][k];
-            b[piv[r]] -= f * b[piv[c]];
-        }
-    }
-    for (int c = 2; c >= 0; --c) {
-        double s = b[piv[c]];
-        for (int k = c + 1; k < 3; ++k) s -= A[piv[c]][k] * x[k];
-        x[c] = s / A[piv[c]][c];
-    }
+    double t;
+    t = c ? b0 : a0; b0 = c ? a0 : b0; a0 = t;
+    t = c ? b1 : a1; b1 = c ? a1 : b1; a1 = t;
+    t = c ? b2 : a2; b2 = c ? a2 : b2; a2 = t;
+    t = c ? bb : ab; bb = c ? ab : bb; ab = t;
+}
+
+__device__ bool solve3(const double (&M)[3][3], const double (&b)[3], double (&x)[3])
+{
+    double a00 = M[0][0], a01 = M[0][1], a02 = M[0][2], b0 = b[0];
+    double a10 = M[1][0], a11 = M[1][1], a12 = M[1][2], b1 = b[1];
+    double a20 = M[2][0], a21 = M[2][1], a22 = M[2][2], b2 = b[2];
+    // column 0: the largest |a_r0| to the top (first maximum wins, as in a row scan)
+    swap_rows(fabs(a10) > fabs(a00) && fabs(a10) >= fabs(a20), a00, a01, a02, b0, a10, a11, a12, b1);
+    swap_rows(fabs(a20) > fabs(a00), a00, a01, a02, b0, a20, a21, a22, b2);
+    if (a00 == 0.0) return false;
+    double f = a10 / a00;
+    a11 -= f * a01; a12 -= f * a02; b1 -= f * b0;
+    f = a20 / a00;
+    a21 -= f * a01; a22 -= f * a02; b2 -= f * b0;
+    // column 1
+    swap_rows(fabs(a21) > fabs(a11), a10, a11, a12, b1, a20, a21, a22, b2);
+    if (a11 == 0.0) return false;
+    f = a21 / a11;
+    a22 -= f * a12; b2 -= f * b1;
+    if (a22 == 0.0) return false;
+    x[2] = b2 / a22;
+    x[1] = (b1 - a12 * x[2]) / a11;
+    x[0] = (b0 - a01 * x[1] - a02 * x[2]) / a00;
     return true;
 }
 
@@ -857,22 +887,23 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
             lane_neighbors<MIXED>(d, lane, xy.x, xy.y, cx, cy, pk.x, pk.y, [&](int j, T, T, T r2) {
                 if ((d.stag[j] & 0x7f) != FLUID) return;
                 const T w = a2 * quintic_w(sqrt_t<T>(r2) * inv_h);
-                double p, u, v, mr;
+                T p, u, v, mr;
                 fluid_fields<MIXED>(d, j, p, u, v, mr);
-                a[0] += w; a[1] += w * (T)p; a[2] += w * (T)u; a[3] += w * (T)v;
+                a[0] += w; a[1] += w * p; a[2] += w * u; a[3] += w * v;
             });
             warp_sum(a);
             if (lane == 0) {
                 const int wi = (t == WALL) ? 0 : 1;
-                double pw, ug, vg;
-                const double sw = a[0];
-                if (sw > 0.0) {
-                    pw = (double)a[1] / sw;
-                    const double uf = (double)a[2] / sw, vf = (double)a[3] / sw;
+                T pw, ug, vg;
+                const T sw = a[0];
+                if (sw > (T)0) {
+                    const T isw = (T)1 / sw;
+                    pw = a[1] * isw;
+                    const T uf = a[2] * isw, vf = a[3] * isw;
                     if (ph.wall_slip[wi]) { ug = uf; vg = -vf; }
-                    else { ug = 2.0 * ph.wall_u[wi] - uf; vg = 2.0 * ph.wall_v[wi] - vf; }
+                    else { ug = (T)(2.0 * ph.wall_u[wi]) - uf; vg = (T)(2.0 * ph.wall_v[wi]) - vf; }
                 } else {
-                    pw = 0.0; ug = ph.wall_u[wi]; vg = ph.wall_v[wi];
+                    pw = (T)0; ug = (T)ph.wall_u[wi]; vg = (T)ph.wall_v[wi];
                 }
                 if (MIXED) {
                     float4 q = d.Qf[k];
@@ -904,15 +935,23 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                                                                    double r2) {
                 if ((d.stag[l] & 0x7f) != FLUID) return;
                 const double xlk = -dx, ylk = -dy;  // the walk gives r_k - r_l
-                const double r = sqrt(r2);
                 double p, u, v, Vl;
                 fluid_fields<MIXED>(d, l, p, u, v, Vl);
-                const double w = ph.a2 * quintic_w(r * ph.inv_h);
-                double wx = 0, wy = 0;
-                if (r > 0.0) {
-                    const double dw = ph.a2h * quintic_dw(r * ph.inv_h);
-                    wx = dw * xlk / r;
-                    wy = dw * ylk / r;
+                double w, wx = 0, wy = 0;
+                if (r2 > 1e-30) {
+                    // fp64 path: IEEE square root and division (the oracle's arithmetic);
+                    // mixed path: Newton-refined inverse square root, no fp64 division
+                    double ir, r;
+                    if (MIXED) { ir = rsqrt_newton(r2); r = r2 * ir; }
+                    else { r = sqrt(r2); ir = 1.0 / r; }
+                    double wq, dwq;
+                    quintic_w_dw(r * ph.inv_h, wq, dwq);
+                    w = ph.a2 * wq;
+                    const double dwr = ph.a2h * dwq * ir;
+                    wx = dwr * xlk;
+                    wy = dwr * ylk;
+                } else {
+                    w = ph.a2 * quintic_w(0.0);
                 }
                 const double row[3] = {w * Vl, wx * Vl, wy * Vl};
 #pragma unroll
@@ -938,7 +977,7 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                                        M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
                     pk = bb[0] / M[0][0];
                     if (!(fabs(det) <= 1e-9 * fabs(M[0][0] * M[1][1] * M[2][2]))) {
-                        double sol[3];
+                        double sol[3] = {0.0, 0.0, 0.0};
                         if (solve3(M, bb, sol)) { pk = sol[0]; gxp = sol[1]; gyp = sol[2]; }
                     }
                 }
@@ -967,7 +1006,7 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                 if ((tj & 0x7f) == FLUID) {
                     const T w = a2 * quintic_w(sqrt_t<T>(r2) * inv_h);
                     a[0] += w;
-                    a[1] += w * (T)d.AUX[j].x;
+                    a[1] += w * (T)d.AUX[j].x;  // J2 of the fluid particle
                     a[2] += (T)1;
                 } else if (tj == (OUTLET | TAG_REDP)) {
                     const double2 x2 = d.AUX[j];
@@ -979,16 +1018,17 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
             warp_sum(a);
             if (lane == 0) {
                 const bool red = a[2] > (T)0;
-                const double mr = (double)a[5];
-                const double J2 = red ? (double)a[1] / (double)a[0] : (mr > 0 ? (double)a[3] / mr : 0.0);
-                const double un = d.ubar[s] + J2 / (2.0 * ph.rho0 * ph.cs);
-                const double adv = red ? un : (mr > 0 ? (double)a[4] / mr : d.ubar[s]);
+                const T mr = a[5];
+                const T J2 = red ? a[1] / a[0] : (mr > (T)0 ? a[3] / mr : (T)0);
+                const double ub = d.ubar[s];
+                const double un = ub + (double)(J2 * (MIXED ? (T)ph.inv_2rcf : (T)ph.inv_2rc));
+                const double adv = red ? un : (mr > (T)0 ? (double)(a[4] / mr) : ub);
                 d.u[s] = un;
                 d.v[s] = d.vbar[s];
-                d.p[s] = d.pbar[s] + 0.5 * J2;
+                d.p[s] = d.pbar[s] + (double)((T)0.5 * J2);
                 d.ut[s] = un;
                 d.vt[s] = d.vbar[s];
-                d.J2p[s] = J2;
+                d.J2p[s] = (double)J2;
                 d.advp[s] = adv;
                 d.redp[s] = red ? 1 : 0;
             }
