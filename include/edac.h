@@ -192,6 +192,33 @@ edac_status edac_read_profile(edac_ctx *ctx, int kernel, double *ms, int64_t *la
  * graph replays included. */
 edac_status edac_launch_count(edac_ctx *ctx, int64_t *count);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free summation density.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory at the time they need
+ * the result -- code running inside CUDA stream capture (an allocation there is
+ * not allowed), code whose framework has handed all device memory to its own
+ * pool allocator, and real-time code that forbids allocation on its hot path.
+ * Neither this call nor the library allocates anything for it: the cell-list
+ * scratch is a fixed static device array of the library (about 3.7 MB, held on
+ * every GPU that loads the library until the process exits).
+ *
+ * For n particles at d_x, d_y with masses d_m (caller-owned device arrays, fp64,
+ * any order) it writes, in the same order, rho_i = sum_j m_j W_ij, the volume
+ * 1 / sum_j W_ij and the neighbour count N_i (self included), fp64, with the
+ * membership test and quintic spline of edac_step's fp64 path.  Only the domain
+ * box, periodic flags, dx, hdx and cuda_stream of params are used.
+ * Limits: n <= EDAC_STATIC_MAX_PARTICLES and at most EDAC_STATIC_MAX_CELLS cells
+ * (EDAC_E_INVALID / EDAC_E_CAPACITY beyond them); a particle outside the box
+ * gives EDAC_E_DOMAIN.  The first call on a device (with that device current)
+ * looks up the scratch address; make it before any stream capture.  All calls
+ * share the scratch, so calls whose GPU work overlaps (other streams, other
+ * host threads on the same device) race.  Synchronises params->cuda_stream. */
+#define EDAC_STATIC_MAX_PARTICLES 262144
+#define EDAC_STATIC_MAX_CELLS 65536
+edac_status edac_density_static(const edac_params *params, int n, const double *d_x,
+                                const double *d_y, const double *d_m, double *d_rho,
+                                double *d_vol, int *d_nnb);
+
 /* Text of the last error of this context (valid until the next call); with
  * ctx = NULL, the last error of a context-less call (edac_workspace_bytes,
  * edac_create) made on this host thread. */

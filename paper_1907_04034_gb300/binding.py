@@ -24,7 +24,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libedac.so")
-SOURCES = ("edac_capi.cu", "edac_cells.cu", "edac_pairs.cu")
+SOURCES = ("edac_capi.cu", "edac_cells.cu", "edac_pairs.cu", "edac_static.cu")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 EDAC_FP64, EDAC_MIXED = 0, 1
@@ -40,7 +40,7 @@ EXPORTS = ("edac_workspace_bytes", "edac_create", "edac_set_inlet", "edac_set_ou
            "edac_set_wall", "edac_set_particles", "edac_step", "edac_evaluate", "edac_get_count",
            "edac_read_state", "edac_read_history", "edac_neighbor_scratch_bytes",
            "edac_read_neighbors", "edac_profile", "edac_read_profile", "edac_launch_count",
-           "edac_last_error", "edac_destroy")
+           "edac_density_static", "edac_last_error", "edac_destroy")
 
 
 class EdacError(RuntimeError):
@@ -140,6 +140,7 @@ def load(path: Optional[str] = None):
         L.edac_profile.argtypes = [_P, i32, i32]
         L.edac_read_profile.argtypes = [_P, i32, _DP, C.POINTER(i64), i32]
         L.edac_launch_count.argtypes = [_P, C.POINTER(i64)]
+        L.edac_density_static.argtypes = [C.POINTER(Params), i32] + [_P] * 6
         L.edac_last_error.argtypes = [_P]
         L.edac_last_error.restype = C.c_char_p
         L.edac_destroy.argtypes = [_P]
@@ -170,6 +171,36 @@ def make_params(p: "_cases.Params", precision: int, capacity: int, max_history: 
 
 def _ptr(a: np.ndarray, ct):
     return a.ctypes.data_as(C.POINTER(ct))
+
+
+def density_static(case, device: str = "cuda:0", stream=None):
+    """Summation density, volume and neighbour count through edac_density_static.
+
+    The call itself allocates nothing on the device: its scratch is the library's static
+    array.  This helper (the caller) owns the input and output tensors.  Returns numpy
+    arrays (rho, vol, nnb) in the order of the case's particles.
+    """
+    import torch
+
+    lib = load()
+    dev = torch.device(device)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    p = make_params(case.params, EDAC_FP64, max(1, case.n), 1, False, st.cuda_stream)
+    x = torch.as_tensor(np.ascontiguousarray(case.x, dtype=np.float64), device=dev)
+    y = torch.as_tensor(np.ascontiguousarray(case.y, dtype=np.float64), device=dev)
+    m = torch.as_tensor(np.ascontiguousarray(case.m, dtype=np.float64), device=dev)
+    rho = torch.empty_like(x)
+    vol = torch.empty_like(x)
+    nnb = torch.empty(case.n, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.device(dev):
+        rc = lib.edac_density_static(C.byref(p), int(case.n), C.c_void_p(x.data_ptr()),
+                                     C.c_void_p(y.data_ptr()), C.c_void_p(m.data_ptr()),
+                                     C.c_void_p(rho.data_ptr()), C.c_void_p(vol.data_ptr()),
+                                     C.c_void_p(nnb.data_ptr()))
+    if rc != 0:
+        raise EdacError(rc, "edac_density_static")
+    return rho.cpu().numpy(), vol.cpu().numpy(), nnb.cpu().numpy()
 
 
 class Solver:
