@@ -359,10 +359,10 @@ struct MixB {
 // row (pass A) or per 32 candidates (pass B).  A tile whose halo exceeds CT_HMAX particles
 // is processed from global memory instead (same membership test, same pair arithmetic), and
 // a particle with more than 128 candidates repeats the test in pass B.
-constexpr int CT_TX = 8;
+constexpr int CT_TX = 8;          // ~104 particles per tile at 13 per cell, for 128 threads
 constexpr int CT_NV = CT_TX + 2;  // cells per staged row (halo included)
 constexpr int CT_TPB = 128;
-constexpr int CT_HMAX = 480;
+constexpr int CT_HMAX = 512;
 constexpr int CT_LMAX = 56;
 
 struct TileHdr {
@@ -371,41 +371,70 @@ struct TileHdr {
     int H, i0, ni;
 };
 
-// Warp 0 builds the header: lane l < 3 CT_NV takes staged cell (r, v) = (l / CT_NV, l % CT_NV),
+// Warp 0 builds the header: lane l takes staged cells l and l + 32 (cell index r CT_NV + v),
 // and a warp scan of the cell counts gives the shared-memory offsets.
-__device__ __forceinline__ void tile_setup(const Dev &d, int cx0, int cy, TileHdr &th)
+__device__ __forceinline__ void tile_cell(const Dev &d, int cx0, int cy, int txe, int cell, int &a,
+                                          int &cnt)
 {
     const Geo &g = d.g;
-    const int lane = threadIdx.x & 31;
-    const int txe = min(CT_TX, g.nx - cx0);  // cells of this segment
-    const int r = lane / CT_NV, v = lane - r * CT_NV;
-    bool ok = lane < 3 * CT_NV && v <= txe + 1;
+    const int r = cell / CT_NV, v = cell - r * CT_NV;
+    bool ok = cell < 3 * CT_NV && v <= txe + 1;
     int by = cy + r - 1, bx = cx0 + v - 1;
     if (g.py) by = by < 0 ? by + g.ny : (by >= g.ny ? by - g.ny : by);
     else ok = ok && by >= 0 && by < g.ny;
     if (g.px) bx = bx < 0 ? bx + g.nx : (bx >= g.nx ? bx - g.nx : bx);
     else ok = ok && bx >= 0 && bx < g.nx;
-    int a = -1, cnt = 0;
+    a = -1;
+    cnt = 0;
     if (ok) {
         const int c = by * g.nx + bx;
         a = d.cell_start[c];
         cnt = d.cell_start[c + 1] - a;
     }
-    int incl = cnt;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane)
+{
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
     }
-    if (lane < 3 * CT_NV) {
-        th.cstart[r][v] = incl - cnt;
-        th.gstart[r][v] = a;
-        if (v == CT_NV - 1) th.cstart[r][CT_NV] = incl;
+    return v;
+}
+
+__device__ __forceinline__ void tile_setup(const Dev &d, int cx0, int cy, TileHdr &th)
+{
+    static_assert(3 * CT_NV <= 64, "tile header: at most two cells per lane");
+    const int lane = threadIdx.x & 31;
+    const int txe = min(CT_TX, d.g.nx - cx0);  // cells of this segment
+    int a0, n0, a1, n1;
+    tile_cell(d, cx0, cy, txe, lane, a0, n0);
+    tile_cell(d, cx0, cy, txe, lane + 32, a1, n1);
+    const int i0s = warp_incl_scan(n0, lane);
+    const int tot0 = __shfl_sync(0xffffffffu, i0s, 31);
+    const int i1s = warp_incl_scan(n1, lane) + tot0;
+    const int cells[2] = {lane, lane + 32};
+    const int incl[2] = {i0s, i1s}, cnt[2] = {n0, n1}, aa[2] = {a0, a1};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int cell = cells[h];
+        if (cell < 3 * CT_NV) {
+            const int r = cell / CT_NV, v = cell - r * CT_NV;
+            th.cstart[r][v] = incl[h] - cnt[h];
+            th.gstart[r][v] = aa[h];
+            if (v == CT_NV - 1) th.cstart[r][CT_NV] = incl[h];
+        }
     }
-    const int H = __shfl_sync(0xffffffffu, incl, 3 * CT_NV - 1);
-    const int own_lo = __shfl_sync(0xffffffffu, incl - cnt, CT_NV + 1);
-    const int own_hi = __shfl_sync(0xffffffffu, incl, CT_NV + txe);
-    const int i0 = __shfl_sync(0xffffffffu, a, CT_NV + 1);
+    // the segment's own cells are row 1, v = 1..txe
+    const int lo_cell = CT_NV + 1, hi_cell = CT_NV + txe;
+    const int own_lo = lo_cell < 32 ? __shfl_sync(0xffffffffu, i0s - n0, lo_cell)
+                                    : __shfl_sync(0xffffffffu, i1s - n1, lo_cell - 32);
+    const int own_hi = __shfl_sync(0xffffffffu, hi_cell < 32 ? i0s : i1s, hi_cell & 31);
+    const int i0 = lo_cell < 32 ? __shfl_sync(0xffffffffu, a0, lo_cell)
+                                : __shfl_sync(0xffffffffu, a1, lo_cell - 32);
+    const int last = 3 * CT_NV - 1;
+    const int H = __shfl_sync(0xffffffffu, last < 32 ? i0s : i1s, last & 31);
     if (lane == 0) {
         th.H = H;
         th.i0 = i0;
@@ -793,6 +822,76 @@ __device__ __forceinline__ void lane_neighbors(const Dev &d, int lane, double qx
     }
 }
 
+// Lane-strided walk that lists the *fluid* neighbours of a query point in a per-warp shared
+// buffer (ballot compaction, CMP_CAP entries) and then runs body(j) over the list with all
+// lanes busy, so that fp64 pair work does not idle the lanes of rejected candidates.
+constexpr int CMP_CAP = 128;
+
+template <class F>
+__device__ __forceinline__ void lane_fluid_compact(const Dev &d, int lane, int *buf, double qx,
+                                                   double qy, int cx, int cy, float rx, float ry,
+                                                   F &&body)
+{
+    const Geo &g = d.g;
+    int a = 0, cnt = 0;
+    if (lane < 9) {
+        const int oy = lane / 3 - 1, ox = lane % 3 - 1;
+        int by = cy + oy, bx = cx + ox;
+        bool ok = true;
+        if (g.py) by = by < 0 ? by + g.ny : (by >= g.ny ? by - g.ny : by);
+        else ok = by >= 0 && by < g.ny;
+        if (g.px) bx = bx < 0 ? bx + g.nx : (bx >= g.nx ? bx - g.nx : bx);
+        else ok = ok && bx >= 0 && bx < g.nx;
+        if (ok) {
+            const int c = by * g.nx + bx;
+            a = __ldg(d.cell_start + c);
+            cnt = __ldg(d.cell_start + c + 1) - a;
+        }
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    int ex[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ex[q] = __shfl_sync(0xffffffffu, incl, q);
+    const int total = __shfl_sync(0xffffffffu, incl, 8);
+    const int excl = incl - cnt;
+    const int trips = (total + 31) >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    int nacc = 0;
+#pragma unroll 1
+    for (int it = 0; it < trips; ++it) {
+        const int t = it * 32 + lane;
+        int q = 0;
+#pragma unroll
+        for (int z = 0; z < 8; ++z) q += (t >= ex[z]);
+        const int j = __shfl_sync(0xffffffffu, a, q) + (t - __shfl_sync(0xffffffffu, excl, q));
+        bool want = false;
+        if (t < total) {
+            const int oy = q / 3 - 1, ox = q % 3 - 1;
+            const float rxo = rx - (float)ox * g.sxf, ryo = ry - (float)oy * g.syf;
+            float dxf, dyf, r2f;
+            want = is_member(d, rxo, ryo, __ldg(d.P + j), j, qx, qy, dxf, dyf, r2f) &&
+                   (d.stag[j] & 0x7f) == FLUID;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, want);
+        if (want) buf[nacc + __popc(m & below)] = j;
+        nacc += __popc(m);
+        if (nacc > CMP_CAP - 32) {
+            __syncwarp();
+            for (int e = lane; e < nacc; e += 32) body(buf[e]);
+            __syncwarp();
+            nacc = 0;
+        }
+    }
+    __syncwarp();
+    for (int e = lane; e < nacc; e += 32) body(buf[e]);
+    __syncwarp();
+}
+
 // (p, u, v, m/rho) of particle j in the path's own precision
 template <int MIXED, class T>
 __device__ __forceinline__ void fluid_fields(const Dev &d, int j, T &p, T &u, T &v, T &mrho)
@@ -866,6 +965,7 @@ template <int MIXED>
 __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
 {
     typedef typename std::conditional<MIXED, float, double>::type T;
+    __shared__ int wbuf[8][CMP_CAP];  // per-warp list of the mirror's fluid neighbours
     const Geo &g = d.g;
     const Phys &ph = d.ph;
     const int lane = threadIdx.x & 31;
@@ -931,10 +1031,10 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
             // fp64 on both paths: with disordered particles the system can be ill-conditioned
             // and fp32 moment sums would lose the solution
             double a[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-            lane_neighbors<0>(d, lane, xk, yk, cx, cy, rx, ry, [&](int l, double dx, double dy,
-                                                                   double r2) {
-                if ((d.stag[l] & 0x7f) != FLUID) return;
-                const double xlk = -dx, ylk = -dy;  // the walk gives r_k - r_l
+            lane_fluid_compact(d, lane, wbuf[threadIdx.x >> 5], xk, yk, cx, cy, rx, ry, [&](int l) {
+                const double2 xyl = d.XY[l];
+                double xlk, ylk;  // r_lk = r_l - r_k, the canonical fp64 separation
+                const double r2 = exact_r2(g, xyl.x, xyl.y, xk, yk, xlk, ylk);
                 double p, u, v, Vl;
                 fluid_fields<MIXED>(d, l, p, u, v, Vl);
                 double w, wx = 0, wy = 0;
