@@ -362,7 +362,7 @@ struct MixB {
 constexpr int CT_TX = 8;          // ~104 particles per tile at 13 per cell, for 128 threads
 constexpr int CT_NV = CT_TX + 2;  // cells per staged row (halo included)
 constexpr int CT_TPB = 128;
-constexpr int CT_HMAX = 512;
+constexpr int CT_HMAX = 480;
 constexpr int CT_LMAX = 56;
 
 struct TileHdr {
