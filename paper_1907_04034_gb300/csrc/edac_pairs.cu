@@ -363,7 +363,6 @@ constexpr int CT_TX = 8;          // ~104 particles per tile at 13 per cell, for
 constexpr int CT_NV = CT_TX + 2;  // cells per staged row (halo included)
 constexpr int CT_TPB = 128;
 constexpr int CT_HMAX = 480;
-constexpr int CT_LMAX = 56;
 
 struct TileHdr {
     int cstart[3][CT_NV + 1];  // shared index of each staged cell's first particle
@@ -465,46 +464,6 @@ __device__ __forceinline__ void tile_stage(const Dev &d, const TileHdr &th, floa
     }
 }
 
-// Phase 1 in shared memory: the neighbours (itself included) of staged particle ti in
-// virtual cell vi of row 1, listed by candidate index (the order of CandRows); ends[r]
-// receives the list length after row r.  When the list fills, body(entry) is run on it and
-// it restarts (the fold points then fall at the flush).
-template <class Body>
-__device__ __forceinline__ void tile_neighbors(const Dev &d, const TileHdr &th, const float2 *spos,
-                                               const int *sgj, int ti, int vi, double qx, double qy,
-                                               unsigned short *lst, Body &&body, int (&ends)[3])
-{
-    const float2 pi = spos[ti];
-    const float hi2 = d.g.rc2_hi, lo2 = d.g.rc2_lo;
-    int cnt = 0, c = 0;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        const int lo = th.cstart[r][vi - 1], hi = th.cstart[r][vi + 2];
-#pragma unroll 2
-        for (int t = lo; t < hi; ++t, ++c) {
-            const float2 pj = spos[t];
-            const float2 dd = __fadd2_rn(pi, f2(-pj.x, -pj.y));
-            const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
-            if (r2 >= hi2) continue;
-            if (r2 > lo2) {
-                const double2 xy = d.XY[sgj[t]];
-                double ex, ey;
-                if (!(exact_r2(d.g, qx, qy, xy.x, xy.y, ex, ey) < d.g.rc2)) continue;
-            }
-            lst[cnt * CT_TPB] = (unsigned short)c;
-            if (++cnt == CT_LMAX) {
-#pragma unroll 1
-                for (int e = 0; e < CT_LMAX; ++e) body(lst[e * CT_TPB], false);
-                body(0, true);
-                cnt = 0;
-#pragma unroll
-                for (int q = 0; q < r; ++q) ends[q] = 0;  // those entries are done
-            }
-        }
-        ends[r] = cnt;
-    }
-}
-
 // The candidate order of a staged particle in virtual cell vi: row 0, row 1, row 2, each the
 // shared-memory range of the three cells vi-1..vi+1.  Pass A and pass B stage the same tile
 // from the same cell table, so a candidate index means the same neighbour in both.
@@ -554,13 +513,71 @@ __device__ __forceinline__ void global_neighbors(const Dev &d, int k, const floa
     fold();
 }
 
+// Phase 1 of pass A: walk the candidate order of particle ti (CandRows) and return the
+// 128-bit mask of its neighbours (itself included); only for cr.tot <= 128.  The loop over the
+// candidates is fp32 only: it sets a tentative bit (r2 below the upper band edge) and a band bit
+// (r2 above the lower edge); the fp64 test then settles the few band candidates, so the fp64
+// work stays out of the candidate loop (a predicated fp64 test would issue for every candidate).
+__device__ __forceinline__ uint4 tile_mask(const Dev &d, const float2 *spos, const int *sgj,
+                                           const CandRows &cr, int ti, double qx, double qy)
+{
+    const float2 pi = spos[ti];
+    const float hi2 = d.g.rc2_hi, lo2 = d.g.rc2_lo;
+    unsigned w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        unsigned cur = 0u, band = 0u;
+        const int cend = min(32 * (q + 1), cr.tot);
+#pragma unroll 4
+        for (int c = 32 * q; c < cend; ++c) {
+            const float2 pj = spos[cr.smem_of(c)];
+            const float2 dd = __fadd2_rn(pi, f2(-pj.x, -pj.y));
+            const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
+            cur |= (unsigned)(r2 < hi2) << (c & 31);
+            band |= (unsigned)(r2 > lo2) << (c & 31);
+        }
+        band &= cur;
+#pragma unroll 1
+        while (band) {
+            const int b = __ffs(band) - 1;
+            band &= band - 1u;
+            const double2 xy = d.XY[sgj[cr.smem_of(32 * q + b)]];
+            double ex, ey;
+            if (!(exact_r2(d.g, qx, qy, xy.x, xy.y, ex, ey) < d.g.rc2)) cur &= ~(1u << b);
+        }
+        w[q] = cur;
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Run body(t) over the set bits of a candidate mask (shared indices t), calling fold() each
+// time a 32-candidate word is exhausted.
+template <class Body, class Fold>
+__device__ __forceinline__ void for_mask(const CandRows &cr, uint4 m, Body &&body, Fold &&fold)
+{
+    unsigned w0 = m.x, w1 = m.y, w2 = m.z, w3 = m.w;
+    const int np = __popc(w0) + __popc(w1) + __popc(w2) + __popc(w3);
+    int base = 0;
+#pragma unroll 1
+    for (int it = 0; it < np; ++it) {
+        while (w0 == 0u) {
+            w0 = w1; w1 = w2; w2 = w3; w3 = 0u;
+            base += 32;
+            fold();
+        }
+        const int b = __ffs(w0) - 1;
+        w0 &= w0 - 1u;
+        body(cr.smem_of(base + b));
+    }
+    fold();
+}
+
 __global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled(Dev d)
 {
     __shared__ TileHdr th;
     __shared__ float2 spos[CT_HMAX];
     __shared__ float smass[CT_HMAX];
     __shared__ int sgj[CT_HMAX];
-    __shared__ unsigned short lst_all[CT_LMAX * CT_TPB];
     int cx0, cy;
     if (!tile_of_block(d, cx0, cy)) return;
     if (threadIdx.x < 32) tile_setup(d, cx0, cy, th);
@@ -568,7 +585,6 @@ __global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled(Dev d)
     const bool fits = th.H <= CT_HMAX;
     if (fits) tile_stage(d, th, spos, sgj, [&](int t, int, const float4 &pj) { smass[t] = pj.z; });
     __syncthreads();
-    unsigned short *lst = lst_all + threadIdx.x;
     const float a2 = d.ph.a2f;
     for (int ii = threadIdx.x; ii < th.ni; ii += CT_TPB) {
         const int k = th.i0 + ii;
@@ -581,39 +597,33 @@ __global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled(Dev d)
             const int vi = d.cellk[k] - cy * d.g.nx - cx0 + 1;
             const float2 pi = spos[ti];
             const CandRows cr(th, vi);
-            // neighbour mask over the candidate order, reused by pass B: entries arrive in
-            // increasing candidate index, so one word is built at a time
-            unsigned m0 = 0, m1 = 0, m2 = 0, m3 = 0, cur = 0;
-            int wcur = 0;
-            auto put_word = [&]() {
-                m0 = wcur == 0 ? cur : m0;
-                m1 = wcur == 1 ? cur : m1;
-                m2 = wcur == 2 ? cur : m2;
-                m3 = wcur == 3 ? cur : m3;
-            };
-            int ends[3];
-            auto body = [&](unsigned short c, bool flush) {
-                if (flush) { f.fold(); return; }
-                const int t = cr.smem_of(c);
+            auto body = [&](int t) {
                 const float2 pj = spos[t];
                 f.add(__fadd2_rn(pi, f2(-pj.x, -pj.y)), smass[t]);
-                if ((c >> 5) != wcur) {
-                    put_word();
-                    wcur = c >> 5;
-                    cur = 0;
-                }
-                cur |= 1u << (c & 31);
             };
-            tile_neighbors(d, th, spos, sgj, ti, vi, xy.x, xy.y, lst, body, ends);
-            int c = 0;
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
+            if (cr.tot <= 128) {
+                // phase 1: the neighbour mask over the candidate order (also pass B's input);
+                // phase 2: the pair terms over its set bits
+                const uint4 m = tile_mask(d, spos, sgj, cr, ti, xy.x, xy.y);
+                d.nbm[k] = m;
+                for_mask(cr, m, body, [&]() { f.fold(); });
+            } else {
 #pragma unroll 1
-                for (; c < ends[r]; ++c) body(lst[c * CT_TPB], false);
+                for (int c = 0; c < cr.tot; ++c) {
+                    const int tj = cr.smem_of(c);
+                    const float2 pj = spos[tj];
+                    const float2 dd = __fadd2_rn(pi, f2(-pj.x, -pj.y));
+                    const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
+                    if (r2 >= d.g.rc2_hi) continue;
+                    if (r2 > d.g.rc2_lo) {
+                        const double2 xj = d.XY[sgj[tj]];
+                        double ex, ey;
+                        if (!(exact_r2(d.g, xy.x, xy.y, xj.x, xj.y, ex, ey) < d.g.rc2)) continue;
+                    }
+                    body(tj);
+                }
                 f.fold();
             }
-            put_word();
-            d.nbm[k] = make_uint4(m0, m1, m2, m3);
         } else {
             global_neighbors(d, k, pk, xy.x, xy.y,
                              [&](float2 dd, int, const float4 &pj) { f.add(dd, pj.z); },
@@ -659,21 +669,7 @@ __device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th,
         };
         if (cr.tot <= 128) {
             // the neighbours pass A found, as set bits of the candidate order
-            const uint4 m = d.nbm[k];
-            unsigned w0 = m.x, w1 = m.y, w2 = m.z, w3 = m.w;
-            const int np = __popc(w0) + __popc(w1) + __popc(w2) + __popc(w3);
-            int base = 0;
-#pragma unroll 1
-            for (int it = 0; it < np; ++it) {
-                while (w0 == 0u) {
-                    w0 = w1; w1 = w2; w2 = w3; w3 = 0u;
-                    base += 32;
-                    f.fold();
-                }
-                const int b = __ffs(w0) - 1;
-                w0 &= w0 - 1u;
-                body(cr.smem_of(base + b));
-            }
+            for_mask(cr, d.nbm[k], body, [&]() { f.fold(); });
         } else {
 #pragma unroll 1
             for (int c = 0; c < cr.tot; ++c) {
@@ -689,8 +685,8 @@ __device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th,
                 }
                 body(tj);
             }
+            f.fold();
         }
-        f.fold();
     } else {
         global_neighbors(d, k, pk, xy.x, xy.y,
                          [&](float2 dd, int j, const float4 &) {
