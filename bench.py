@@ -41,7 +41,7 @@ FLOPS_PER_PAIR_B = 90
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the pair kernels from
 # one ncu capture of the current kernels on the 247k-particle cylinder, scaled by particle count
 # to the 1.51M workload (bytes grow with the particles: one read of the cell-ordered arrays).
-TRAFFIC = {"pass_a": 62.1e6, "pass_b": 139.9e6}  # profiles/pair_kernels_cylinder_dx25_full.md
+TRAFFIC = {"pass_a": 62.2e6, "pass_b": 139.9e6}  # profiles/pair_kernels_cylinder_dx25_full.md
 
 
 def parse():
@@ -270,7 +270,10 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     peaks, peak_src = load_peaks()
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = fp32_peak_tflops(props.multi_processor_count, max_mhz)
+    peak_nominal = fp32_peak_tflops(props.multi_processor_count, max_mhz)
+    # measured FMA-pipe peaks (FMA chains filling every SM), the roofline denominators
+    peak = binding.fma_peak(binding.EDAC_PEAK_FP32, str(dev))
+    peak64 = binding.fma_peak(binding.EDAC_PEAK_FP64, str(dev))
     step_ms_eager = sum(p["ms_total"] for p in prof.values()) / kp
     # the roofline of the dominant (largest total time) of the two arithmetic kernels
     cand = {"pass_b": (pair_b, FLOPS_PER_PAIR_B), "pass_a": (pair_a, FLOPS_PER_PAIR_A)}
@@ -281,8 +284,9 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": TRAFFIC.get(dom),
                 "kernel": dom + " (mixed)",
-                "peak_note": f"fp32 FMA pipe: {props.multi_processor_count} SMs x 128 lanes x 2 "
-                             f"x {max_mhz:.0f} MHz ({peak_src} max clock); 'of measured' clock",
+                "peak_note": "of measured: fp32 FMA pipe, FMA chains on every SM (edac_fma_peak); "
+                             f"nominal {props.multi_processor_count} SMs x 128 lanes x 2 x "
+                             f"{max_mhz:.0f} MHz = {peak_nominal:.1f}",
                 "pairs_per_launch": pairs, "flops_per_pair": fpp, "ms_per_launch": k_ms}
     kernels = {k: round(v["ms_per_launch"], 5) for k, v in prof.items()}
     for k, (pp, f) in cand.items():
@@ -307,6 +311,19 @@ def main():
     h64 = s64.history(K64)
     v64 = float(np.sum(h64["n_active"])) / (ms64 / 1e3) * world
     fx64 = s64.history(W + K64)["fx"]
+    # fp64 pair passes against the measured fp64 FMA peak
+    kp64 = 2
+    for kname in ("pass_b", "pass_a"):
+        s64.profile(kname, True)
+    s64.step(kp64)
+    roof64 = {}
+    for kname, (pp, f) in (("pass_b", (pair_b, FLOPS_PER_PAIR_B)), ("pass_a", (pair_a, FLOPS_PER_PAIR_A))):
+        t, n = s64.read_profile(kname)
+        s64.profile(kname, False)
+        kms = t / max(n, 1)
+        ach = pp * f / (kms * 1e-3) / 1e12 if kms > 0 else None
+        roof64[kname] = {"ms_per_launch": kms, "achieved_tflops": ach,
+                         "frac": ach / peak64 if ach and peak64 else None}
     nc = min(len(fx64), len(fx_mixed))
     scale = max(float(np.abs(fx64[:nc]).max()), 1e-12)
     drag_err = float(np.abs(fx_mixed[:nc] - fx64[:nc]).max()) / scale
@@ -355,7 +372,8 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary(),
                 "fp64_path": {"value": v64, "unit": UNIT, "steps": K64,
-                              "ms_per_step": ms64 / K64},
+                              "ms_per_step": ms64 / K64, "fp64_peak_tflops": peak64,
+                              "pair_kernels": roof64},
                 "mixed_over_fp64": value / v64 if v64 else None,
                 "drag_rel_err_mixed_vs_fp64": drag_err, "drag_steps_compared": nc,
                 "kernel_ms_per_launch": kernels, "eager_step_ms": step_ms_eager}

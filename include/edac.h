@@ -219,6 +219,21 @@ edac_status edac_density_static(const edac_params *params, int n, const double *
                                 const double *d_y, const double *d_m, double *d_rho,
                                 double *d_vol, int *d_nnb);
 
+/* ---------------------------------------------------------------------------
+ * FMA-pipe peak of the current device, measured.  The paper has no counterpart:
+ * this is the denominator of the pair passes' roofline (their binding resource
+ * is the FP32 pipe on the mixed path and the FP64 pipe on the fp64 path), taken
+ * on the device at the clocks it runs under load rather than from a data sheet.
+ * kind: EDAC_PEAK_FP32 (the larger of scalar and paired FP32 FMA) or
+ * EDAC_PEAK_FP64.  Runs FMA-chain kernels filling every SM for about 0.1 s on
+ * cuda_stream (NULL: default stream) and writes the best rate of three timed
+ * launches to *tflops, in TFLOP/s with 2 flops per FMA.  Allocates nothing;
+ * synchronises the stream.  EDAC_E_INVALID for a bad kind or NULL tflops,
+ * EDAC_E_CUDA if a launch or event call fails. */
+#define EDAC_PEAK_FP32 0
+#define EDAC_PEAK_FP64 1
+edac_status edac_fma_peak(int kind, void *cuda_stream, double *tflops);
+
 /* Text of the last error of this context (valid until the next call); with
  * ctx = NULL, the last error of a context-less call (edac_workspace_bytes,
  * edac_create) made on this host thread. */

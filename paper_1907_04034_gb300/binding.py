@@ -24,7 +24,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libedac.so")
-SOURCES = ("edac_capi.cu", "edac_cells.cu", "edac_pairs.cu", "edac_static.cu")
+SOURCES = ("edac_capi.cu", "edac_cells.cu", "edac_pairs.cu", "edac_static.cu", "edac_peaks.cu")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 EDAC_FP64, EDAC_MIXED = 0, 1
@@ -40,7 +40,7 @@ EXPORTS = ("edac_workspace_bytes", "edac_create", "edac_set_inlet", "edac_set_ou
            "edac_set_wall", "edac_set_particles", "edac_step", "edac_evaluate", "edac_get_count",
            "edac_read_state", "edac_read_history", "edac_neighbor_scratch_bytes",
            "edac_read_neighbors", "edac_profile", "edac_read_profile", "edac_launch_count",
-           "edac_density_static", "edac_last_error", "edac_destroy")
+           "edac_density_static", "edac_fma_peak", "edac_last_error", "edac_destroy")
 
 
 class EdacError(RuntimeError):
@@ -201,6 +201,25 @@ def density_static(case, device: str = "cuda:0", stream=None):
     if rc != 0:
         raise EdacError(rc, "edac_density_static")
     return rho.cpu().numpy(), vol.cpu().numpy(), nnb.cpu().numpy()
+
+
+EDAC_PEAK_FP32, EDAC_PEAK_FP64 = 0, 1
+
+
+def fma_peak(kind: int, device: str = "cuda:0", stream=None) -> float:
+    """Measured FMA-pipe peak of the device in TFLOP/s (edac_fma_peak): kind EDAC_PEAK_FP32
+    or EDAC_PEAK_FP64.  About 0.1 s of GPU time; synchronises the stream."""
+    import torch
+
+    lib = load()
+    dev = torch.device(device)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    out = C.c_double(0.0)
+    with torch.cuda.device(dev):
+        rc = lib.edac_fma_peak(int(kind), C.c_void_p(st.cuda_stream), C.byref(out))
+    if rc != 0:
+        raise EdacError(rc, "edac_fma_peak")
+    return float(out.value)
 
 
 class Solver:

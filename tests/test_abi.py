@@ -80,3 +80,9 @@ def test_contextless_errors_carry_a_message(lib):
     assert b"must be > 0" in lib.edac_last_error(None)
     assert lib.edac_workspace_bytes(C.byref(_params(periodic_y=1, y_max=0.1)), C.byref(n)) == 1
     assert b"periodic" in lib.edac_last_error(None) or b"empty" in lib.edac_last_error(None)
+
+
+def test_fma_peak_rejects_bad_arguments_before_any_gpu_call(lib):
+    out = C.c_double(-1.0)  # status 1 = EDAC_E_INVALID
+    assert lib.edac_fma_peak(7, None, C.byref(out)) == 1
+    assert lib.edac_fma_peak(binding.EDAC_PEAK_FP32, None, None) == 1

@@ -305,3 +305,17 @@ def test_bad_uploads_are_rejected_on_the_host():
         s.upload(bad)
     assert e.value.code == 7
     s.close()
+
+
+@pytest.mark.gpu
+def test_fma_peaks_are_measured_and_plausible():
+    """edac_fma_peak: the FP32 rate lies between a quarter and 2.2x of 128 lanes x 2 flops x
+    SMs x 2.1 GHz, and the FP64 rate is positive and below the FP32 rate."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal = sms * 128 * 2 * 2.1e9 / 1e12
+    p32 = binding.fma_peak(binding.EDAC_PEAK_FP32)
+    p64 = binding.fma_peak(binding.EDAC_PEAK_FP64)
+    assert 0.25 * nominal < p32 < 2.2 * nominal, (p32, nominal)
+    assert 0.0 < p64 < p32, (p64, p32)
