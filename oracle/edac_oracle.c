@@ -351,7 +351,11 @@ static void pass_a(const orc_params *P, orc_state *S, const nlist *L)
  * walls, no body-force term in the pressure projection; p_w is the Shepard
  * average of fluid pressure; the ghost velocity is 2 u_wall - <u_f> for a
  * no-slip wall and (<u_f>, -<v_f>) for a slip wall whose normal is y.  With no
- * fluid neighbour: p_w = 0, u_g = u_wall.
+ * fluid neighbour: p_w = 0, u_g = u_wall.  When every fluid neighbour sits at
+ * the edge of the support, where W vanishes in floating point (q rounds to 3),
+ * the weights are all zero and <.> is the plain mean over those neighbours:
+ * the limit of the weighted mean for one such neighbour, and a value that a
+ * lower-precision W (the mixed path's) reaches for the same neighbour set.
  * ------------------------------------------------------------------------- */
 static void walls(const orc_params *P, orc_state *S, const nlist *L)
 {
@@ -361,6 +365,8 @@ static void walls(const orc_params *P, orc_state *S, const nlist *L)
         if (!is_wall(S->tag[i])) continue;
         int wi = wall_index(S->tag[i]);
         double sw = 0.0, sp = 0.0, su = 0.0, sv = 0.0, dx, dy;
+        double mp = 0.0, mu = 0.0, mv = 0.0;
+        int nf = 0;
         for (int t = L->start[i]; t < L->start[i + 1]; t++) {
             int j = L->idx[t];
             if (S->tag[j] != ORC_FLUID) continue;
@@ -370,11 +376,23 @@ static void walls(const orc_params *P, orc_state *S, const nlist *L)
             sp += S->p[j] * w;
             su += S->u[j] * w;
             sv += S->v[j] * w;
+            mp += S->p[j];
+            mu += S->u[j];
+            mv += S->v[j];
+            nf++;
         }
         double ug, vg, pw;
-        if (sw > 0.0) {
-            pw = sp / sw;
-            double uf = su / sw, vf = sv / sw;
+        if (nf > 0) {
+            double uf, vf;
+            if (sw > 0.0) {
+                pw = sp / sw;
+                uf = su / sw;
+                vf = sv / sw;
+            } else {
+                pw = mp / (double)nf;
+                uf = mu / (double)nf;
+                vf = mv / (double)nf;
+            }
             if (P->wall_slip[wi]) { ug = uf; vg = -vf; }
             else { ug = 2.0 * P->wall_u[wi] - uf; vg = 2.0 * P->wall_v[wi] - vf; }
         } else {
@@ -469,6 +487,12 @@ static int mirror_value(const orc_params *P, const orc_state *S, double xk, doub
         *pk_out = 0.0;
         return 0;
     }
+    if (!(M[0][0] > 0.0)) { /* all weights zero: plain mean of the fluid pressures */
+        double sp = 0.0;
+        for (int t = 0; t < nl; t++) sp += S->p[ls[t]];
+        *pk_out = sp / (double)nl;
+        return nl;
+    }
     double d = det3(M);
     if (fabs(d) <= 1e-9 * fabs(M[0][0] * M[1][1] * M[2][2])) {
         *pk_out = b[0] / M[0][0];
@@ -537,7 +561,13 @@ static void inlet_mirror(const orc_params *P, orc_state *S)
  * Reading: accelerations are computed for fluid and inlet particles (an inlet
  * particle that becomes fluid keeps the rate computed for it); u_ij uses the
  * momentum velocities, wall ghost velocities for wall j.  The solid force sums
- * over fluid j only, with u_ij = u_g,i - u_j; its p_avg,i uses all neighbours.
+ * over fluid j only, with u_ij = u_g,i - u_j, and its p~_ij is the interpolated
+ * pressure (rho_j p_i + rho_i p_j)/(rho_i + rho_j) without the p_avg shift:
+ * summed over all neighbours, the solid-solid pairs of that antisymmetric form
+ * cancel in the total, so the fluid-only sum is the body force of Eq.
+ * (tvf-momentum_solid); a p_avg,i shift on the one-sided fluid sum would instead
+ * subtract about p_i times the surface element and remove the pressure drag
+ * that the c_d of Table clcd (Sec. 4.6) contains.
  * ------------------------------------------------------------------------- */
 static void pass_b(const orc_params *P, orc_state *S, const nlist *L)
 {
@@ -554,7 +584,7 @@ static void pass_b(const orc_params *P, orc_state *S, const nlist *L)
         S->fx[i] = S->fy[i] = 0.0;
         if (!do_fluid && !do_solid) continue;
         double pavg = 0.0;
-        if (P->use_pavg) {
+        if (P->use_pavg && !do_solid) {
             double sp = 0.0;
             for (int t = L->start[i]; t < L->start[i + 1]; t++) sp += S->p[L->idx[t]];
             pavg = sp / (double)S->nnb[i];
@@ -695,7 +725,8 @@ static void ring_update(const orc_params *P, orc_state *S)
 /* Outlet side, once per step.  An outlet particle with fluid neighbours ("red",
  * Fig. io_moc) takes J2 as the Shepard average of fluid J2, Eq. (shepard); one
  * without ("blue") takes the mean of the previous step's J2 of the red outlet
- * particles in its support, Eq. (average_old), or 0 if there are none.  With
+ * particles in its support, Eq. (average_old), or 0 if there are none (the
+ * Shepard average with all weights zero is the plain mean, as for walls).  With
  * J3 = 0: p' = J2/2, u' = J2/(2 rho0 c).  The particle's value is its frozen
  * time average plus this acoustic part, Eq. (acou); v stays at its average.
  * The advection velocity of a red particle is that u; a blue one takes the
@@ -717,7 +748,7 @@ static void outlet_update(const orc_params *P, orc_state *S, const nlist *L)
 #pragma omp parallel for schedule(static)
     for (int o = 0; o < n; o++) {
         if (S->tag[o] != ORC_OUTLET) continue;
-        double sw = 0.0, sj = 0.0, sjp = 0.0, sadv = 0.0, dx, dy;
+        double sw = 0.0, sj = 0.0, sjm = 0.0, sjp = 0.0, sadv = 0.0, dx, dy;
         int nf = 0, mr = 0;
         for (int t = L->start[o]; t < L->start[o + 1]; t++) {
             int j = L->idx[t];
@@ -726,6 +757,7 @@ static void outlet_update(const orc_params *P, orc_state *S, const nlist *L)
                 double w = orc_W(r, h);
                 sw += w;
                 sj += w * S->J2[j];
+                sjm += S->J2[j];
                 nf++;
             } else if (S->tag[j] == ORC_OUTLET && S->redp[j]) {
                 sjp += S->J2p[j];
@@ -734,7 +766,9 @@ static void outlet_update(const orc_params *P, orc_state *S, const nlist *L)
             }
         }
         int red = nf > 0;
-        double J2 = red ? sj / sw : (mr > 0 ? sjp / (double)mr : 0.0);
+        /* all weights zero (every fluid neighbour at the support edge): plain mean */
+        double J2 = red ? (sw > 0.0 ? sj / sw : sjm / (double)nf)
+                        : (mr > 0 ? sjp / (double)mr : 0.0);
         double pa = 0.5 * J2, ua = J2 / (2.0 * rc);
         double u = S->ubar[o] + ua;
         double adv = red ? u : (mr > 0 ? sadv / (double)mr : S->ubar[o]);

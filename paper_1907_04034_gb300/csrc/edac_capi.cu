@@ -305,7 +305,12 @@ edac_status check_device(edac_ctx *ctx)
     if (h.err) {
         ctx->failed = true;
         if (h.err & ERR_NONFINITE) return fail(ctx, EDAC_E_NONFINITE, "non-finite value in the particle fields");
-        if (h.err & ERR_DOMAIN) return fail(ctx, EDAC_E_DOMAIN, "a particle left the domain box");
+        if (h.err & ERR_DOMAIN) {
+            char buf[192];
+            snprintf(buf, sizeof buf, "a particle left the domain box (id %llu, tag %d, at x = %.9g, "
+                     "y = %.9g, in step %d)", h.err_id, h.err_tag, h.err_x, h.err_y, h.step + 1);
+            return fail(ctx, EDAC_E_DOMAIN, buf);
+        }
         if (h.err & (ERR_CAPACITY | ERR_LIST)) return fail(ctx, EDAC_E_CAPACITY, "particle capacity or event list exceeded");
         if (h.err & ERR_TIMEOUT) return fail(ctx, EDAC_E_TIMEOUT, "a device wait timed out");
         return fail(ctx, EDAC_E_STATE, "device error");

@@ -39,7 +39,15 @@ __global__ void k_cell_count(Dev d)
             continue;
         }
         const double xs = d.x[s], ys = d.y[s];
-        if (!(xs >= g.x_min && xs < g.x_max && ys >= g.y_min && ys < g.y_max)) set_err(d, ERR_DOMAIN);
+        if (!(xs >= g.x_min && xs < g.x_max && ys >= g.y_min && ys < g.y_max)) {
+            set_err(d, ERR_DOMAIN);
+            if (atomicCAS(&d.cnt->err_rec, 0, 1) == 0) {
+                d.cnt->err_tag = d.tag[s];
+                d.cnt->err_id = d.id[s];
+                d.cnt->err_x = xs;
+                d.cnt->err_y = ys;
+            }
+        }
         const int cx = cell_coord(xs, g.x_min, g.inv_sx, g.nx);
         const int cy = cell_coord(ys, g.y_min, g.inv_sy, g.ny);
         const int c = cy * g.nx + cx;

@@ -61,6 +61,10 @@ struct Counters {
     int n_drag;      // solid particles in the drag sum (static)
     int hist_len;    // history records written (saturates at max_history)
     unsigned long long next_id;
+    // the first particle found outside the domain box (error context for the host)
+    int err_rec, err_tag;
+    unsigned long long err_id;
+    double err_x, err_y;
 };
 
 // Everything a kernel may touch.

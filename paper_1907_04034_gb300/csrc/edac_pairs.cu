@@ -197,8 +197,9 @@ __global__ void __launch_bounds__(TPB) k_pass_b64(Dev d)
         f.mi_inv = 1.0 / d.Ms[k];
         f.solid = solid;
         listed_neighbors(d, k, xy.x, xy.y, cx, cy, pk.x, pk.y, lst, f);
-        // -sum c p~ gW = -sum c (pbar - p_i) gW + (p_avg - p_i) G   (with p_avg) or - p_i G
-        const double corr = ph.use_pavg ? f.sdp / (double)N : -pv.x;
+        // -sum c p~ gW = -sum c (pbar - p_i) gW + (p_avg - p_i) G   (with p_avg) or - p_i G;
+        // the solid force takes pbar_ij itself (no p_avg shift on its one-sided fluid sum)
+        const double corr = (ph.use_pavg && !solid) ? f.sdp / (double)N : -pv.x;
         if (solid) {
             d.fx[s] = f.ax + corr * f.gxs;
             d.fy[s] = f.ay + corr * f.gys;
@@ -699,8 +700,9 @@ __device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th,
     const float sx = f.am_h.x + f.am_l.x, sy = f.am_h.y + f.am_l.y;
     const float G0 = f.gg_h.x + f.gg_l.x, G1 = f.gg_h.y + f.gg_l.y;
     const int N = d.snnb[k];
-    // -sum c p~ gW = -sum c (pbar - p_i) gW + (p_avg - p_i) G   (with p_avg) or - p_i G
-    const float corr = ph.use_pavg ? f.sdp / (float)N : -q.x;
+    // -sum c p~ gW = -sum c (pbar - p_i) gW + (p_avg - p_i) G   (with p_avg) or - p_i G;
+    // the solid force takes pbar_ij itself (no p_avg shift on its one-sided fluid sum)
+    const float corr = (ph.use_pavg && !SOLID) ? f.sdp / (float)N : -q.x;
     const int s = d.order[k];
     if (SOLID) {
         d.fx[s] = (double)fmaf(corr, G0, sx);
@@ -979,23 +981,28 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
             int cx, cy;
             cell_of(d, k, cx, cy);
             const float4 pk = d.P[k];
-            T a[4] = {0, 0, 0, 0};
+            // [sum W, sum W p, sum W u, sum W v, count, sum p, sum u, sum v] over fluid j
+            T a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             lane_neighbors<MIXED>(d, lane, xy.x, xy.y, cx, cy, pk.x, pk.y, [&](int j, T, T, T r2) {
                 if ((d.stag[j] & 0x7f) != FLUID) return;
                 const T w = a2 * quintic_w(sqrt_t<T>(r2) * inv_h);
                 T p, u, v, mr;
                 fluid_fields<MIXED>(d, j, p, u, v, mr);
                 a[0] += w; a[1] += w * p; a[2] += w * u; a[3] += w * v;
+                a[4] += (T)1; a[5] += p; a[6] += u; a[7] += v;
             });
             warp_sum(a);
             if (lane == 0) {
                 const int wi = (t == WALL) ? 0 : 1;
                 T pw, ug, vg;
                 const T sw = a[0];
-                if (sw > (T)0) {
-                    const T isw = (T)1 / sw;
-                    pw = a[1] * isw;
-                    const T uf = a[2] * isw, vf = a[3] * isw;
+                if (a[4] > (T)0) {
+                    // Shepard average; all weights zero (every fluid neighbour at the support
+                    // edge, where W rounds to 0): the plain mean over those neighbours
+                    const bool wz = !(sw > (T)0);
+                    const T isw = wz ? (T)1 / a[4] : (T)1 / sw;
+                    pw = (wz ? a[5] : a[1]) * isw;
+                    const T uf = (wz ? a[6] : a[2]) * isw, vf = (wz ? a[7] : a[3]) * isw;
                     if (ph.wall_slip[wi]) { ug = uf; vg = -vf; }
                     else { ug = (T)(2.0 * ph.wall_u[wi]) - uf; vg = (T)(2.0 * ph.wall_v[wi]) - vf; }
                 } else {
@@ -1018,7 +1025,8 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
             // the mirror point k = (2 x_in - x_o, y_o) over fluid l with r_lk = r_l - r_k and
             // V_l = m_l/rho_l, solved with partial pivoting; p_o = p_k - (r_o - r_k).grad p_k
             // (Eq. taylor2).  No fluid in reach: p_o = 0; singular system
-            // (|det| <= 1e-9 |M00 M11 M22|): the Shepard value sum p W V / sum W V.
+            // (|det| <= 1e-9 |M00 M11 M22|): the Shepard value sum p W V / sum W V; all
+            // weights zero (every fluid neighbour at the support edge): the plain mean of p.
             const double xk = 2.0 * ph.x_in - xy.x, yk = xy.y;
             const int cx = cell_coord(xk, g.x_min, g.inv_sx, g.nx);
             const int cy = cell_coord(yk, g.y_min, g.inv_sy, g.ny);
@@ -1026,7 +1034,7 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
             const float ry = (float)(yk - (g.y_min + (double)cy * g.sy));
             // fp64 on both paths: with disordered particles the system can be ill-conditioned
             // and fp32 moment sums would lose the solution
-            double a[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            double a[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             lane_fluid_compact(d, lane, wbuf[threadIdx.x >> 5], xk, yk, cx, cy, rx, ry, [&](int l) {
                 const double2 xyl = d.XY[l];
                 double xlk, ylk;  // r_lk = r_l - r_k, the canonical fp64 separation
@@ -1058,6 +1066,7 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                     a[9 + q] += p * row[q];
                 }
                 a[12] += 1.0;
+                a[13] += p;
             });
             warp_sum(a);
             if (lane == 0) {
@@ -1067,7 +1076,9 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                     bb[q] = (double)a[9 + q];
                 }
                 double pk = 0.0, gxp = 0.0, gyp = 0.0;
-                if (a[12] > 0.0) {
+                if (a[12] > 0.0 && !(M[0][0] > 0.0)) {
+                    pk = a[13] / a[12];  // all weights zero (fluid at the support edge): mean
+                } else if (a[12] > 0.0) {
                     const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
                                        M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
                                        M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
@@ -1096,14 +1107,16 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
             int cx, cy;
             cell_of(d, k, cx, cy);
             const float4 pk = d.P[k];
-            T a[6] = {0, 0, 0, 0, 0, 0};
+            T a[7] = {0, 0, 0, 0, 0, 0, 0};
             lane_neighbors<MIXED>(d, lane, xy.x, xy.y, cx, cy, pk.x, pk.y, [&](int j, T, T, T r2) {
                 const uint8_t tj = d.stag[j];
                 if ((tj & 0x7f) == FLUID) {
                     const T w = a2 * quintic_w(sqrt_t<T>(r2) * inv_h);
+                    const T J2j = (T)d.AUX[j].x;  // J2 of the fluid particle
                     a[0] += w;
-                    a[1] += w * (T)d.AUX[j].x;  // J2 of the fluid particle
+                    a[1] += w * J2j;
                     a[2] += (T)1;
+                    a[6] += J2j;
                 } else if (tj == (OUTLET | TAG_REDP)) {
                     const double2 x2 = d.AUX[j];
                     a[3] += (T)x2.x;
@@ -1115,7 +1128,9 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
             if (lane == 0) {
                 const bool red = a[2] > (T)0;
                 const T mr = a[5];
-                const T J2 = red ? a[1] / a[0] : (mr > (T)0 ? a[3] / mr : (T)0);
+                // Shepard J2; all weights zero (fluid at the support edge): plain mean
+                const T J2 = red ? (a[0] > (T)0 ? a[1] / a[0] : a[6] / a[2])
+                                 : (mr > (T)0 ? a[3] / mr : (T)0);
                 const double ub = d.ubar[s];
                 const double un = ub + (double)(J2 * (MIXED ? (T)ph.inv_2rcf : (T)ph.inv_2rc));
                 const double adv = red ? un : (mr > (T)0 ? (double)(a[4] / mr) : ub);

@@ -1,0 +1,144 @@
+"""Long-run physics of the flow past a cylinder (Sec. 4.6): drag and lift coefficients and
+the Strouhal number from the library's force history, for comparison with Table clcd
+(Re = 200) and Table hybridconv (Re = 20).
+
+The paper's setup: cylinder of diameter D, channel 15D x 15D with the cylinder 5D behind the
+inlet interface, slip walls, uniform inlet velocity U, hybrid outlet, six layers of inlet,
+outlet and wall particles, h = 1.2 dx, Re = U D / nu, the cylinder filled with rings of solid
+particles spaced dx down to its centre, run to t = 150 s with D = 2 m and U = 1 m/s, i.e. 75
+convective times D / U.  Coefficients: c_d = F_x / (rho0 U^2 D / 2), c_l = F_y / (rho0 U^2 D
+/ 2) (per unit length, so that they match the literature values the paper compares with),
+filtered with a five-point moving average; St = f D / U with f the shedding frequency.
+
+    python -m paper_1907_04034_gb300.validate --dx-over-d 30 --t-end 75
+
+prints one JSON line.  Everything runs on the GPU through the C ABI (`binding.Solver`).
+"""
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import binding, cases
+
+
+def paper_cylinder(dx_over_d: float = 30.0, Re: float = 200.0, D: float = 1.0,
+                   layers: int = 6) -> cases.Case:
+    """The Sec. 4.6 geometry at spacing D / dx_over_d (D = 1 instead of 2 m: only D/dx, Re and
+    the convective time matter for the coefficients)."""
+    dx = D / dx_over_d
+    return cases.cylinder(dx=dx, D=D, Re=Re, Lx=15.0 * D, H=15.0 * D, xc=5.0 * D,
+                          n_solid=int(0.5 * D / dx) + 1, n_in=layers, n_out=layers,
+                          n_wall=layers)
+
+
+def moving_average(a: np.ndarray, k: int = 5) -> np.ndarray:
+    """k-point centred moving average (the ends average the available points)."""
+    if len(a) < k:
+        return a.copy()
+    c = np.convolve(a, np.ones(k), mode="same")
+    n = np.convolve(np.ones_like(a), np.ones(k), mode="same")
+    return c / n
+
+
+def coefficients(fx, fy, dt: float, D: float, U: float, rho0: float, t_from: float) -> dict:
+    """c_d mean and range, c_l amplitude and St over t >= t_from (forces per step)."""
+    q = 0.5 * rho0 * U * U * D
+    cd = moving_average(np.asarray(fx) / q)
+    cl = moving_average(np.asarray(fy) / q)
+    t = (np.arange(len(cd)) + 1) * dt
+    sel = t >= t_from
+    if sel.sum() < 16:
+        raise ValueError("averaging window too short")
+    cdw, clw, tw = cd[sel], cl[sel], t[sel]
+    # shedding frequency: peak of the lift spectrum (Hann window, zero-padded x8)
+    x = (clw - clw.mean()) * np.hanning(len(clw))
+    nfft = 8 * len(x)
+    spec = np.abs(np.fft.rfft(x, nfft))
+    freq = np.fft.rfftfreq(nfft, dt)
+    lo = np.searchsorted(freq, 0.02 * U / D)  # ignore the slow drift
+    f = float(freq[lo + int(np.argmax(spec[lo:]))])
+    # lift amplitude: least-squares sinusoid at f (robust to the SPH force noise)
+    A = np.stack([np.sin(2 * math.pi * f * tw), np.cos(2 * math.pi * f * tw), np.ones_like(tw)], 1)
+    coef, *_ = np.linalg.lstsq(A, clw, rcond=None)
+    # smoothed extremes over one-twentieth of a shedding period
+    w = max(5, int(round(1.0 / (20.0 * max(f, 1e-9) * dt))))
+    cls = moving_average(clw, w)
+    return {"cd_mean": float(cdw.mean()), "cd_std": float(cdw.std()),
+            "cl_amp_fit": float(math.hypot(coef[0], coef[1])),
+            "cl_amp_smoothed": float(0.5 * (cls.max() - cls.min())),
+            "cl_mean": float(clw.mean()), "St": f * D / U, "window": [float(tw[0]), float(tw[-1])]}
+
+
+def run(dx_over_d: float = 30.0, Re: float = 200.0, t_end: float = 75.0, t_from: float = None,
+        precision: str = "mixed", chunk: int = 5000, device: str = "cuda:0",
+        diagnose: bool = False) -> dict:
+    import torch
+
+    case = paper_cylinder(dx_over_d, Re)
+    p = case.params
+    D, U = p.drag_length, p.U
+    nsteps = int(math.ceil(t_end * U / D / p.dt)) if D > 0 else 0
+    solver = binding.Solver(case, precision=precision, use_graphs=True, device=device,
+                            max_history=nsteps + 16)
+    torch.cuda.synchronize(torch.device(device))
+    out = {"case": f"cylinder Re={Re:g}, 15D x 15D, dx=D/{dx_over_d:g}", "precision": precision,
+           "particles": case.n, "fluid": int(np.sum(case.tag == cases.FLUID)), "dt": p.dt}
+    t0 = time.perf_counter()
+    done = 0
+    last = None
+    trace = []  # [step, max |u - U e_x| of fluid, its x, y, min p, max p]
+    try:
+        while done < nsteps:
+            k = min(chunk, nsteps - done)
+            solver.step(k)
+            done += k
+            if diagnose:  # per chunk: the fastest fluid particle and the field ranges per tag
+                st = solver.state(("x", "y", "u", "v", "p"))
+                last = {int(t): {f: [float(st[f][st["tag"] == t].min()), float(st[f][st["tag"] == t].max())]
+                                 for f in ("x", "y", "u", "v", "p")}
+                        for t in np.unique(st["tag"])}
+                last["step"] = done
+                fl = st["tag"] == cases.FLUID
+                sp = np.hypot(st["u"][fl] - U, st["v"][fl])
+                k = int(np.argmax(sp))
+                trace.append([done, float(sp[k]), float(st["x"][fl][k]), float(st["y"][fl][k]),
+                              float(st["p"][fl].min()), float(st["p"][fl].max())])
+    except binding.EdacError as e:
+        out.update({"error": str(e), "failed_in_chunk_after_step": done, "last_good": last,
+                    "trace": trace})
+        solver.close()
+        return out
+    h = solver.history(nsteps)
+    t1 = time.perf_counter()
+    n_final = solver.count()
+    solver.close()
+    if t_from is None:
+        t_from = 0.6 * t_end
+    out.update({"particles_final": n_final, "steps": nsteps, "t_end": nsteps * p.dt,
+                "wall_s": t1 - t0})
+    if diagnose:
+        out["trace"] = trace
+    out.update(coefficients(h["fx"], h["fy"], p.dt, D, U, p.rho0, t_from))
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--dx-over-d", type=float, default=30.0)
+    ap.add_argument("--re", type=float, default=200.0)
+    ap.add_argument("--t-end", type=float, default=75.0, help="in convective times D/U")
+    ap.add_argument("--t-from", type=float, default=None, help="start of the averaging window")
+    ap.add_argument("--precision", default="mixed", choices=("mixed", "fp64"))
+    ap.add_argument("--chunk", type=int, default=5000, help="steps per edac_step call")
+    ap.add_argument("--diagnose", action="store_true",
+                    help="record the per-tag field ranges after every chunk")
+    a = ap.parse_args()
+    print(json.dumps(run(a.dx_over_d, a.re, a.t_end, a.t_from, a.precision, a.chunk,
+                         diagnose=a.diagnose)))
+
+
+if __name__ == "__main__":
+    main()

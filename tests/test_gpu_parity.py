@@ -319,3 +319,72 @@ def test_fma_peaks_are_measured_and_plausible():
     p64 = binding.fma_peak(binding.EDAC_PEAK_FP64)
     assert 0.25 * nominal < p32 < 2.2 * nominal, (p32, nominal)
     assert 0.0 < p64 < p32, (p64, p32)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("edge", ["tiny_weight", "zero_weight"])
+def test_wall_shepard_with_one_fluid_neighbour_at_the_support_edge(prec, edge):
+    """One fluid neighbour at the edge of a wall particle's support: the projected values are
+    that neighbour's, whether its weight is tiny (oracle, fp64) or rounds to zero (the mixed
+    path's fp32 W, and the oracle's fp64 W one ulp inside r_c at this spacing)."""
+    dx = 0.01303
+    h = 1.2 * dx
+    rc = 3.0 * h
+    r = math.nextafter(rc, 0.0) if edge == "zero_weight" else rc * (1.0 - 1e-9)
+    cs = 10.0
+    prm = cases.Params(x_min=-1.0, x_max=1.0, y_min=-1.0, y_max=1.0, dx=dx, hdx=1.2,
+                       nu=0.01, cs=cs, pb=cs * cs, dt=1e-4, wall_drag=(0, 0))
+    c = cases.Case("wall_pair", prm, np.array([0.0, r]), np.zeros(2), np.array([0.0, 0.3]),
+                   np.array([0.0, -0.2]), np.array([0.0, 0.7]), np.full(2, dx * dx),
+                   np.array([WALL, FLUID], dtype=np.uint8), np.arange(2, dtype=np.uint64),
+                   capacity=8)
+    ref = oracle.OracleSim(c)
+    s = binding.Solver(c, precision=prec)
+    g = s.state(("p", "u", "v", "nnb"))
+    s.close()
+    assert int(g["nnb"][0]) == 2 == int(ref.field("nnb")[0])
+    tol = 1e-15 if prec == "fp64" else 1e-6
+    for f, want in (("p", 0.7), ("u", -0.3), ("v", 0.2)):
+        assert ref.field(f)[0] == pytest.approx(want, rel=1e-15)
+        assert g[f][0] == pytest.approx(want, rel=tol), f
+
+
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    return rows
+
+
+@pytest.mark.gpu
+def test_cylinder_re200_forces_match_table_clcd():
+    """Long-run physics (Sec. 4.6): the paper's cylinder (15D x 15D, dx = D/30, Re = 200,
+    hybrid outlet) run for 75 convective times on the mixed path; over the last 30 the mean
+    drag coefficient, the lift amplitude and the Strouhal number are compared with the
+    paper's hybrid-outlet row of Table clcd: c_d within 0.1 (twice the paper's band), the
+    lift amplitude within 15%, St within 5%."""
+    from paper_1907_04034_gb300 import validate
+
+    ref = {k: float(v) for k, v in _golden("cylinder_re200_table_clcd.txt")}
+    out = validate.run(dx_over_d=30.0, Re=200.0, t_end=75.0, t_from=45.0, precision="mixed")
+    assert "error" not in out, out
+    assert abs(out["cd_mean"] - ref["cd_mean"]) < 2 * ref["cd_band"], out
+    assert abs(out["cl_amp_fit"] - ref["cl_amp"]) < 0.15 * ref["cl_amp"], out
+    assert abs(out["St"] - ref["St"]) < 0.05 * ref["St"], out
+
+
+@pytest.mark.gpu
+def test_cylinder_re20_drag_matches_table_hybridconv():
+    """Long-run physics (Sec. 4.6): at Re = 20 the wake is steady; the paper's hybrid-outlet
+    drag coefficient is 2.317-2.320 at all three spacings of Table hybridconv.  At its coarsest
+    spacing (dx = D/20), after 60 convective times, the mean c_d over the last 24 is within 5%
+    and the lift stays near zero."""
+    from paper_1907_04034_gb300 import validate
+
+    rows = _golden("cylinder_re20_table_hybridconv.txt")
+    cd_ref = float([r for r in rows if r[1] == "0.050"][0][3])
+    out = validate.run(dx_over_d=20.0, Re=20.0, t_end=60.0, t_from=36.0, precision="mixed")
+    assert "error" not in out, out
+    assert abs(out["cd_mean"] - cd_ref) < 0.05 * cd_ref, out
+    assert abs(out["cl_mean"]) < 0.02, out

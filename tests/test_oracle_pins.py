@@ -186,6 +186,76 @@ def test_pavg_breaks_pair_symmetry_by_the_closed_form():
     np.testing.assert_allclose(got, tot, rtol=1e-9, atol=1e-12 * np.abs(m * o.field("au")).sum())
 
 
+def test_solid_force_balances_the_fluid_pressure_force():
+    """Eq. tvf-momentum_solid read with the interpolated pressure pbar_ij (no p_avg shift on the
+    solid's one-sided fluid sum).  Fluid at rest, random pressure, a solid block counted in the
+    drag, p_avg on for the fluid: all pair terms are antisymmetric except the fluid's p_avg
+    shift, so  sum_fluid m (a - g) + sum_solid F = sum_fluid p_avg,i G_i  with
+    G_i = sum_j c_ij gW_ij = -m_i abg_i / p_b.  A p_avg shift on the solid side would add
+    sum_solid p_avg,i sum_(j fluid) c_ij gW_ij to the left."""
+    c = cases.taylor_green(n=16, jitter=0.3, seed=11)
+    rng = np.random.default_rng(12)
+    c.u[:] = 0.0
+    c.v[:] = 0.0
+    c.p[:] = rng.normal(0.0, 1.0, c.n)
+    blk = (np.abs(c.x - 0.5) < 0.2) & (np.abs(c.y - 0.5) < 0.15)
+    c.tag[blk] = cases.WALL
+    c.params.use_pavg = 1
+    c.params.wall_drag = (1, 0)
+    o = oracle.OracleSim(c)
+    start, idx = o.neighbors()
+    tag, p, m = o.field("tag"), o.field("p"), o.field("m")
+    fl = tag == cases.FLUID
+    sol = tag == cases.WALL
+    pa = np.array([p[idx[start[i]:start[i + 1]]].mean() for i in range(c.n)])
+    lhs = np.zeros(2)
+    rhs = np.zeros(2)
+    for k, (a, ab, f) in enumerate((("au", "abu", "fx"), ("av", "abv", "fy"))):
+        lhs[k] = np.sum(m[fl] * o.field(a)[fl]) + np.sum(o.field(f)[sol])
+        G = -m * o.field(ab) / c.params.pb
+        rhs[k] = np.sum(pa[fl] * G[fl])
+    scale = np.sum(np.abs(m[fl] * o.field("au")[fl]))
+    np.testing.assert_allclose(lhs, rhs, rtol=0, atol=1e-10 * scale)
+    # the solid force is not small: the identity is not met trivially
+    assert np.abs(o.field("fx")[sol]).sum() > 1e-2 * scale
+
+
+def _wall_and_one_fluid(r, dx=0.05):
+    """A no-slip wall particle at the origin and one fluid particle at (r, 0)."""
+    cs = 10.0
+    prm = cases.Params(x_min=-1.0, x_max=1.0, y_min=-1.0, y_max=1.0, dx=dx, hdx=1.2,
+                       nu=0.01, cs=cs, pb=cs * cs, dt=1e-4, wall_drag=(0, 0))
+    x = np.array([0.0, r])
+    y = np.zeros(2)
+    return cases.Case("wall_pair", prm, x, y, np.array([0.0, 0.3]), np.array([0.0, -0.2]),
+                      np.array([0.0, 0.7]), np.full(2, dx * dx),
+                      np.array([cases.WALL, cases.FLUID], dtype=np.uint8),
+                      np.arange(2, dtype=np.uint64), capacity=8)
+
+
+def test_wall_shepard_with_one_fluid_neighbour_at_the_support_edge():
+    """Shepard projection on a wall (Adami et al., cited in Sec. 2) over one fluid neighbour is
+    that neighbour's value: near the support edge (W tiny) and at the edge itself, where W
+    rounds to exactly 0 and the all-zero-weights rule (plain mean) takes over."""
+    # a spacing at which the largest separation inside the support (one ulp below r_c, so
+    # that r^2 < r_c^2) gives q = r/h = 3 exactly in fp64, hence W = 0
+    dx = 0.01303
+    h = 1.2 * dx
+    rc = 3.0 * h
+    r0 = math.nextafter(rc, 0.0)
+    assert r0 * r0 < rc * rc and oracle.W(r0, h) == 0.0
+    r1 = rc * (1.0 - 1e-9)  # W > 0 but tiny
+    assert 0.0 < oracle.W(r1, h) < 1e-30
+    for r in (r1, r0):
+        o = oracle.OracleSim(_wall_and_one_fluid(r, dx))
+        o.evaluate()
+        start, idx = o.neighbors()
+        assert list(idx[start[0]:start[1]]) == [0, 1]  # the fluid particle is a neighbour
+        assert o.field("p")[0] == pytest.approx(0.7, rel=1e-15)
+        assert o.field("u")[0] == pytest.approx(-0.3, rel=1e-15)  # 2 u_wall - u_f
+        assert o.field("v")[0] == pytest.approx(0.2, rel=1e-15)
+
+
 # ----------------------------------------------------------------- full scheme
 def test_taylor_green_decay_rate():
     # velocity amplitude of the Taylor-Green vortex decays as exp(-8 pi^2 nu t)
