@@ -55,7 +55,7 @@ class CParams(C.Structure):
         ("n_modes", C.c_int), ("modes", C.c_double * MAX_MODES),
         ("inlet_y0", C.c_double), ("inlet_h", C.c_double),
         ("has_outlet", C.c_int), ("x_out", C.c_double), ("n_out_layers", C.c_int),
-        ("n_avg", C.c_int), ("i_thresh", C.c_double),
+        ("n_avg", C.c_int), ("i_thresh", C.c_double), ("outlet_kind", C.c_int),
         ("wall_slip", C.c_int * 2), ("wall_u", C.c_double * 2), ("wall_v", C.c_double * 2),
         ("wall_drag", C.c_int * 2), ("drag_length", C.c_double),
         ("neighbor_mode", C.c_int), ("mirror_sign", C.c_int),
@@ -112,6 +112,8 @@ def lib():
             L.orc_mirror_points.argtypes = [C.POINTER(CParams), C.POINTER(CState), C.c_int, _DP, _DP,
                                             _DP, _DP, _DP]
             L.orc_mirror_points.restype = C.c_int
+            L.orc_outlet_mirror.argtypes = [C.POINTER(CParams), C.POINTER(CState)]
+            L.orc_outlet_mirror.restype = C.c_int
             assert L.orc_sizeof_params() == C.sizeof(CParams), "orc_params layout mismatch"
             assert L.orc_sizeof_state() == C.sizeof(CState), "orc_state layout mismatch"
             assert L.orc_sizeof_hist() == C.sizeof(CHist), "orc_hist layout mismatch"
@@ -142,7 +144,7 @@ def make_params(p, neighbor_mode: int = 0, mirror_sign: int = -1) -> CParams:
                  "pb", "eta_reg", "gx", "gy", "dt", "x_in", "x_out", "i_thresh", "drag_length"):
         setattr(cp, name, float(getattr(p, name)))
     for name in ("periodic_x", "periodic_y", "use_pavg", "has_inlet", "n_in_layers", "has_outlet",
-                 "n_out_layers", "n_avg"):
+                 "n_out_layers", "n_avg", "outlet_kind"):
         setattr(cp, name, int(getattr(p, name)))
     modes = tuple(p.inlet_modes)
     assert len(modes) <= MAX_MODES
@@ -251,3 +253,7 @@ class OracleSim:
                                 qy.ctypes.data_as(_DP), pk.ctypes.data_as(_DP),
                                 gx.ctypes.data_as(_DP), gy.ctypes.data_as(_DP))
         return pk, gx, gy
+
+    def outlet_mirror(self):
+        """Run the mirrored outlet update (Sec. 3.2 at the outlet) on the current fields."""
+        lib().orc_outlet_mirror(C.byref(self.cp), C.byref(self.st))

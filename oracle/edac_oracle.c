@@ -30,6 +30,13 @@
 #define ORC_WALL 3
 #define ORC_SLIPWALL 4
 #define ORC_NAVG_MAX 8
+/* outlet treatments: hybrid (Sec. 3.4), do-nothing (Sec. 3.1), modified do-nothing
+ * (Sec. 3.1.1), method of characteristics (Sec. 3.3), mirroring (Sec. 3.2) */
+#define ORC_OUT_HYBRID 0
+#define ORC_OUT_DONOTHING 1
+#define ORC_OUT_MOD_DONOTHING 2
+#define ORC_OUT_CHARACTERISTIC 3
+#define ORC_OUT_MIRROR 4
 #define ORC_MAX_MODES 16
 
 typedef struct {
@@ -48,6 +55,7 @@ typedef struct {
     int n_out_layers;
     int n_avg;
     double i_thresh;
+    int outlet_kind; /* ORC_OUT_*: the outlet treatment of Sec. 3 */
     int wall_slip[2];
     double wall_u[2], wall_v[2];
     int wall_drag[2];
@@ -456,12 +464,14 @@ static double det3(double M[3][3])
          + M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
 }
 
-/* the extrapolated value for one mirror point; returns the fluid count */
-static int mirror_value(const orc_params *P, const orc_state *S, double xk, double yk,
-                        const int *ls, int nl, double *pk_out, double grad_out[2])
+/* the values f_k and gradients of nf fields (fld[f][l]) at one mirror point k from its
+ * fluid neighbours ls[0..nl); returns the fluid count.  One matrix, nf right-hand sides. */
+static int mirror_values(const orc_params *P, const orc_state *S, double xk, double yk,
+                         const int *ls, int nl, int nf, double *const *fld, double *fk,
+                         double (*grad)[2])
 {
     const double h = h_of(P);
-    double M[3][3] = {{0}}, b[3] = {0};
+    double M[3][3] = {{0}}, b[3][3] = {{0}}, mean[3] = {0};
     for (int t = 0; t < nl; t++) {
         int l = ls[t];
         double xlk, ylk;
@@ -479,36 +489,46 @@ static int mirror_value(const orc_params *P, const orc_state *S, double xk, doub
             M[a][0] += row[a];
             M[a][1] += xlk * row[a];
             M[a][2] += ylk * row[a];
-            b[a] += S->p[l] * row[a];
+            for (int f = 0; f < nf; f++) b[f][a] += fld[f][l] * row[a];
         }
+        for (int f = 0; f < nf; f++) mean[f] += fld[f][l];
     }
-    grad_out[0] = grad_out[1] = 0.0;
+    for (int f = 0; f < nf; f++) grad[f][0] = grad[f][1] = 0.0;
     if (nl == 0) {
-        *pk_out = 0.0;
+        for (int f = 0; f < nf; f++) fk[f] = 0.0;
         return 0;
     }
-    if (!(M[0][0] > 0.0)) { /* all weights zero: plain mean of the fluid pressures */
-        double sp = 0.0;
-        for (int t = 0; t < nl; t++) sp += S->p[ls[t]];
-        *pk_out = sp / (double)nl;
+    if (!(M[0][0] > 0.0)) { /* all weights zero: plain mean of the fluid values */
+        for (int f = 0; f < nf; f++) fk[f] = mean[f] / (double)nl;
         return nl;
     }
     double d = det3(M);
-    if (fabs(d) <= 1e-9 * fabs(M[0][0] * M[1][1] * M[2][2])) {
-        *pk_out = b[0] / M[0][0];
-        return nl;
+    int singular = fabs(d) <= 1e-9 * fabs(M[0][0] * M[1][1] * M[2][2]);
+    for (int f = 0; f < nf; f++) {
+        double A[3][3], rhs[3], sol[3];
+        memcpy(A, M, sizeof(A));
+        memcpy(rhs, b[f], sizeof(rhs));
+        if (singular || !solve3(A, rhs, sol)) {
+            fk[f] = b[f][0] / M[0][0];
+            continue;
+        }
+        fk[f] = sol[0];
+        grad[f][0] = sol[1];
+        grad[f][1] = sol[2];
     }
-    double A[3][3], rhs[3], sol[3];
-    memcpy(A, M, sizeof(A));
-    memcpy(rhs, b, sizeof(rhs));
-    if (!solve3(A, rhs, sol)) {
-        *pk_out = b[0] / M[0][0];
-        return nl;
-    }
-    *pk_out = sol[0];
-    grad_out[0] = sol[1];
-    grad_out[1] = sol[2];
     return nl;
+}
+
+/* the pressure alone (the inlet's field) */
+static int mirror_value(const orc_params *P, const orc_state *S, double xk, double yk,
+                        const int *ls, int nl, double *pk_out, double grad_out[2])
+{
+    double *fld[1] = {S->p};
+    double g[1][2];
+    int n = mirror_values(P, S, xk, yk, ls, nl, 1, fld, pk_out, g);
+    grad_out[0] = g[0][0];
+    grad_out[1] = g[0][1];
+    return n;
 }
 
 static void inlet_mirror(const orc_params *P, orc_state *S)
@@ -700,6 +720,12 @@ static void ring_update(const orc_params *P, orc_state *S)
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < S->n; i++) {
         if (S->tag[i] != ORC_FLUID) continue;
+        if (P->outlet_kind == ORC_OUT_CHARACTERISTIC) {
+            /* Sec. 3.3 alone: the reference state is the free stream (U, 0) */
+            S->J2[i] = rc * (S->u[i] - P->U) + S->p[i];
+            continue;
+        }
+        if (P->outlet_kind != ORC_OUT_HYBRID) continue;
         double *rg = S->ring + (size_t)i * ORC_NAVG_MAX * 3;
         double inten = S->p[i] * S->p[i] / (2.0 * P->rho0 * P->cs);
         if (inten <= I) {
@@ -722,23 +748,97 @@ static void ring_update(const orc_params *P, orc_state *S)
     }
 }
 
-/* Outlet side, once per step.  An outlet particle with fluid neighbours ("red",
- * Fig. io_moc) takes J2 as the Shepard average of fluid J2, Eq. (shepard); one
- * without ("blue") takes the mean of the previous step's J2 of the red outlet
- * particles in its support, Eq. (average_old), or 0 if there are none (the
- * Shepard average with all weights zero is the plain mean, as for walls).  With
- * J3 = 0: p' = J2/2, u' = J2/(2 rho0 c).  The particle's value is its frozen
- * time average plus this acoustic part, Eq. (acou); v stays at its average.
- * The advection velocity of a red particle is that u; a blue one takes the
- * mean previous-step advection velocity of the red particles in its support,
- * else its frozen u average.  Reading: "previous step" values are the ones this
- * routine stored one step earlier, self included in the blue averages; the
- * advection velocity set here moves the particle in x during the next step's
- * stages (x = x^n + tau adv, y fixed), like the do-nothing update
- * x^n = x^(n-1) + u^(n-1) dt of Sec. 3.1, so outlet and fluid particles move
- * together. */
+/* Outlet side, once per step, after the corrector's evaluation.
+ *
+ * Hybrid (Sec. 3.4): an outlet particle with fluid neighbours ("red", Fig. io_moc)
+ * takes J2 as the Shepard average of fluid J2, Eq. (shepard); one without ("blue")
+ * takes the mean of the previous step's J2 of the red outlet particles in its
+ * support, Eq. (average_old), or 0 if there are none (the Shepard average with all
+ * weights zero is the plain mean, as for walls).  With J3 = 0: p' = J2/2,
+ * u' = J2/(2 rho0 c).  The particle's value is its frozen time average plus this
+ * acoustic part, Eq. (acou); v stays at its average.  The advection velocity of a
+ * red particle is that u; a blue one takes the mean previous-step advection
+ * velocity of the red particles in its support, else its frozen u average.
+ * Reading: "previous step" values are the ones this routine stored one step
+ * earlier, self included in the blue averages; the advection velocity set here
+ * moves the particle in x during the next step's stages (x = x^n + tau adv, y
+ * fixed), like the do-nothing update x^n = x^(n-1) + u^(n-1) dt of Sec. 3.1, so
+ * outlet and fluid particles move together.
+ *
+ * Method of characteristics (Sec. 3.3): the same red/blue extrapolation of J2, with
+ * the free stream (U, p = 0) as the fixed reference state instead of the time
+ * averages: p = J2/2, u = U + J2/(2 rho0 c); the transverse velocity keeps the
+ * value frozen at the crossing.  A blue particle without red neighbours advects
+ * with its own u.
+ *
+ * Do-nothing (Sec. 3.1): u, v, p stay frozen at their values at the crossing and
+ * the particle advects with that u: nothing to update.
+ *
+ * Modified do-nothing (Sec. 3.1.1): values frozen as in do-nothing; the advection
+ * velocity is the Shepard average of the fluid u, Eq. (shepard0), for red
+ * particles; blue ones take the mean previous-step advection velocity of their red
+ * neighbours (the rule Sec. 3.4 gives where the Shepard interpolation does not
+ * reach), else their frozen u.
+ *
+ * Mirroring (Sec. 3.2 applied at the outlet): p, u and v by the Taylor
+ * extrapolation of Eq. (matform) about k = (2 x_out - x_o, y_o) with the minus sign
+ * of Eq. (taylor2); the particle advects with that u. */
+static void outlet_mirror(const orc_params *P, orc_state *S)
+{
+    int nq = 0;
+    for (int i = 0; i < S->n; i++) nq += (S->tag[i] == ORC_OUTLET);
+    if (nq == 0) return;
+    int *who = (int *)malloc(sizeof(int) * (size_t)nq);
+    double *qx = (double *)malloc(sizeof(double) * (size_t)nq);
+    double *qy = (double *)malloc(sizeof(double) * (size_t)nq);
+    nq = 0;
+    for (int i = 0; i < S->n; i++)
+        if (S->tag[i] == ORC_OUTLET) {
+            who[nq] = i;
+            qx[nq] = 2.0 * P->x_out - S->x[i];
+            qy[nq] = S->y[i];
+            nq++;
+        }
+    nlist L;
+    build_lists(P, S, nq, qx, qy, 1u << ORC_FLUID, &L);
+    double *fo = (double *)malloc(sizeof(double) * 3 * (size_t)nq);
+#pragma omp parallel for schedule(static)
+    for (int t = 0; t < nq; t++) {
+        int o = who[t];
+        double *fld[3] = {S->p, S->u, S->v};
+        double fk[3], g[3][2];
+        mirror_values(P, S, qx[t], qy[t], L.idx + L.start[t], L.start[t + 1] - L.start[t], 3,
+                      fld, fk, g);
+        double rx = S->x[o] - qx[t], ry = S->y[o] - qy[t];
+        for (int f = 0; f < 3; f++)
+            fo[3 * t + f] = fk[f] + (double)P->mirror_sign * (rx * g[f][0] + ry * g[f][1]);
+    }
+    for (int t = 0; t < nq; t++) { /* written after all reads (the fields are inputs above) */
+        int o = who[t];
+        S->p[o] = fo[3 * t + 0];
+        S->u[o] = fo[3 * t + 1];
+        S->v[o] = fo[3 * t + 2];
+        S->ut[o] = S->u[o];
+        S->vt[o] = S->v[o];
+        S->advp[o] = S->u[o];
+        S->J2p[o] = 0.0;
+        S->redp[o] = 0;
+    }
+    nlist_free(&L);
+    free(fo);
+    free(who);
+    free(qx);
+    free(qy);
+}
+
 static void outlet_update(const orc_params *P, orc_state *S, const nlist *L)
 {
+    const int kind = P->outlet_kind;
+    if (kind == ORC_OUT_DONOTHING) return;
+    if (kind == ORC_OUT_MIRROR) {
+        outlet_mirror(P, S);
+        return;
+    }
     const double h = h_of(P);
     const double rc = P->rho0 * P->cs;
     int n = S->n;
@@ -748,16 +848,18 @@ static void outlet_update(const orc_params *P, orc_state *S, const nlist *L)
 #pragma omp parallel for schedule(static)
     for (int o = 0; o < n; o++) {
         if (S->tag[o] != ORC_OUTLET) continue;
-        double sw = 0.0, sj = 0.0, sjm = 0.0, sjp = 0.0, sadv = 0.0, dx, dy;
+        /* sf: Shepard sums of the fluid value (J2, or u for the modified do-nothing) */
+        double sw = 0.0, sf = 0.0, sfm = 0.0, sjp = 0.0, sadv = 0.0, dx, dy;
         int nf = 0, mr = 0;
         for (int t = L->start[o]; t < L->start[o + 1]; t++) {
             int j = L->idx[t];
             if (S->tag[j] == ORC_FLUID) {
                 double r = sqrt(sep(P, S->x[o], S->y[o], S->x[j], S->y[j], &dx, &dy));
                 double w = orc_W(r, h);
+                double fj = kind == ORC_OUT_MOD_DONOTHING ? S->u[j] : S->J2[j];
                 sw += w;
-                sj += w * S->J2[j];
-                sjm += S->J2[j];
+                sf += w * fj;
+                sfm += fj;
                 nf++;
             } else if (S->tag[j] == ORC_OUTLET && S->redp[j]) {
                 sjp += S->J2p[j];
@@ -767,17 +869,32 @@ static void outlet_update(const orc_params *P, orc_state *S, const nlist *L)
         }
         int red = nf > 0;
         /* all weights zero (every fluid neighbour at the support edge): plain mean */
-        double J2 = red ? (sw > 0.0 ? sj / sw : sjm / (double)nf)
-                        : (mr > 0 ? sjp / (double)mr : 0.0);
+        double shep = red ? (sw > 0.0 ? sf / sw : sfm / (double)nf) : 0.0;
+        double blue_adv = mr > 0 ? sadv / (double)mr : 0.0;
+        if (kind == ORC_OUT_MOD_DONOTHING) {
+            J2n[o] = 0.0;
+            advn[o] = red ? shep : (mr > 0 ? blue_adv : S->ubar[o]);
+            redn[o] = red;
+            continue;
+        }
+        double J2 = red ? shep : (mr > 0 ? sjp / (double)mr : 0.0);
         double pa = 0.5 * J2, ua = J2 / (2.0 * rc);
-        double u = S->ubar[o] + ua;
-        double adv = red ? u : (mr > 0 ? sadv / (double)mr : S->ubar[o]);
+        double u, p, adv;
+        if (kind == ORC_OUT_CHARACTERISTIC) {
+            u = P->U + ua;
+            p = pa;
+            adv = red ? u : (mr > 0 ? blue_adv : u);
+        } else {
+            u = S->ubar[o] + ua;
+            p = S->pbar[o] + pa;
+            adv = red ? u : (mr > 0 ? blue_adv : S->ubar[o]);
+        }
         J2n[o] = J2;
         advn[o] = adv;
         redn[o] = red;
         S->u[o] = u;
         S->v[o] = S->vbar[o];
-        S->p[o] = S->pbar[o] + pa;
+        S->p[o] = p;
         S->ut[o] = S->u[o];
         S->vt[o] = S->v[o];
     }
@@ -809,7 +926,8 @@ static void move_rec(orc_state *S, int a, int b)
 /* Particle recycling, end of Sec. 3.4: an inlet particle that crossed x_in
  * becomes fluid and a new inlet particle is created L_in = n_in dx upstream of
  * it; a fluid particle that crossed x_out becomes an outlet particle and keeps
- * its time averages; an outlet particle past x_out + L_out is deleted.
+ * its time averages (the other outlets: the values it has when it crosses); an
+ * outlet particle past x_out + L_out is deleted.
  * Reading: transitions are taken once per step after the outlet update, in
  * ascending id; new ids are handed out in ascending parent id; the new inlet
  * particle copies its parent's y, p and m and takes u = u(y), v = 0. */
@@ -828,9 +946,15 @@ static void recycle(const orc_params *P, orc_state *S, orc_hist *H)
             ndel++;
         } else if (P->has_outlet && t == ORC_FLUID && S->x[i] >= P->x_out) {
             S->tag[i] = ORC_OUTLET;
-            S->u[i] = S->ubar[i];
-            S->v[i] = S->vbar[i];
-            S->p[i] = S->pbar[i];
+            if (P->outlet_kind == ORC_OUT_HYBRID) {
+                S->u[i] = S->ubar[i];
+                S->v[i] = S->vbar[i];
+                S->p[i] = S->pbar[i];
+            } else { /* the other outlets freeze the values it crosses with */
+                S->ubar[i] = S->u[i];
+                S->vbar[i] = S->v[i];
+                S->pbar[i] = S->p[i];
+            }
             S->ut[i] = S->u[i];
             S->vt[i] = S->v[i];
             S->J2p[i] = 0.0;
@@ -1039,6 +1163,14 @@ int orc_mirror_points(const orc_params *P, const orc_state *S, int nq, const dou
         grady[t] = g[1];
     }
     nlist_free(&L);
+    return 0;
+}
+
+/* Debug: the mirrored outlet update alone at the current fields (pins Sec. 3.2 at
+ * the outlet with three fields). */
+int orc_outlet_mirror(const orc_params *P, orc_state *S)
+{
+    outlet_mirror(P, S);
     return 0;
 }
 

@@ -254,7 +254,8 @@ class Solver:
             self._call("edac_set_inlet", p.x_in, p.n_in_layers, len(modes),
                        _ptr(modes, C.c_double) if len(modes) else None, p.inlet_y0, p.inlet_h)
         if p.has_outlet:
-            self._call("edac_set_outlet", p.x_out, p.n_out_layers, 0, p.n_avg, p.i_thresh)
+            self._call("edac_set_outlet", p.x_out, p.n_out_layers, int(p.outlet_kind), p.n_avg,
+                       p.i_thresh)
         for tagv, w in ((_cases.WALL, 0), (_cases.SLIPWALL, 1)):
             self._call("edac_set_wall", tagv, int(p.wall_slip[w]), float(p.wall_u[w]),
                        float(p.wall_v[w]), int(p.wall_drag[w]))

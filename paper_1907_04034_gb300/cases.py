@@ -66,6 +66,9 @@ class Params:
     n_out_layers: int = 5
     n_avg: int = 6
     i_thresh: float = -1.0     # < 0: use the acoustic-intensity formula
+    # outlet treatment: 0 hybrid (Sec. 3.4), 1 do-nothing (Sec. 3.1), 2 modified do-nothing
+    # (Sec. 3.1.1), 3 method of characteristics (Sec. 3.3), 4 mirroring (Sec. 3.2)
+    outlet_kind: int = 0
     # walls: per wall tag (WALL, SLIPWALL): slip flag, wall velocity, counted in drag
     wall_slip: tuple = (0, 1)
     wall_u: tuple = (0.0, 0.0)

@@ -454,6 +454,117 @@ def test_characteristic_inversion_round_trip():
     assert np.all(np.abs(f["J2p"][red]) > 0.3 * J2)
 
 
+# --------------------------------------------------------- the other outlets (Sec. 3)
+OUTLET_KINDS = {"donothing": 1, "mod_donothing": 2, "characteristic": 3, "mirror": 4}
+
+
+@pytest.mark.parametrize("kind", list(OUTLET_KINDS))
+def test_uniform_flow_stays_uniform_with_every_outlet(kind):
+    # u = U, p = 0 on a lattice with 8 inlet and 8 outlet layers: frozen values (Sec. 3.1),
+    # the Shepard advection velocity of a constant field (Sec. 3.1.1), J2 = 0 against the free
+    # stream (Sec. 3.3) and the Taylor extrapolation of constant fields (Sec. 3.2) all keep it
+    c = cases.channel(jitter=0.0, pulse_amp=0.0, n_in=8, n_out=8)
+    c.params.outlet_kind = OUTLET_KINDS[kind]
+    o = oracle.OracleSim(c)
+    hist = o.step(120)
+    f = o.fields()
+    assert np.abs(f["u"] - 1.0).max() < 1e-12
+    assert np.abs(f["v"]).max() < 1e-12
+    assert np.abs(f["p"]).max() < 1e-12
+    assert sum(h["n_delete"] for h in hist) > 0
+
+
+def test_donothing_outlet_freezes_values_and_advects_with_them():
+    # Sec. 3.1: an outlet particle keeps u, v, p and moves x by u dt per step, y fixed
+    c = cases.channel(pulse_amp=0.3)
+    c.params.outlet_kind = OUTLET_KINDS["donothing"]
+    o = oracle.OracleSim(c)
+    o.step(40)
+    a = o.fields(("id", "tag", "x", "y", "u", "v", "p"))
+    o.step(1)
+    b = o.fields(("id", "tag", "x", "y", "u", "v", "p"))
+    ia = {int(i): k for k, i in enumerate(a["id"])}
+    kept = [(ia[int(i)], k) for k, i in enumerate(b["id"])
+            if b["tag"][k] == OUTLET and int(i) in ia and a["tag"][ia[int(i)]] == OUTLET]
+    assert len(kept) > 50
+    ka, kb = np.array(kept).T
+    for fld in ("u", "v", "p", "y"):
+        np.testing.assert_array_equal(b[fld][kb], a[fld][ka])
+    np.testing.assert_allclose(b["x"][kb], a["x"][ka] + c.params.dt * a["u"][ka], rtol=0,
+                               atol=1e-15)
+    assert np.ptp(a["p"][ka]) > 1e-4  # the frozen values are not all the same
+
+
+def test_modified_donothing_advects_with_the_fluid_velocity():
+    # Sec. 3.1.1: values frozen as in do-nothing, but a red outlet particle advects with the
+    # Shepard average of its fluid neighbours' u (a convex combination, Eq. shepard0), not
+    # with its own frozen u
+    c = cases.channel(jitter=0.0, pulse_amp=0.0, n_in=4, n_out=8)
+    c.params.outlet_kind = OUTLET_KINDS["mod_donothing"]
+    c.u[c.tag == OUTLET] = 1.3
+    o = oracle.OracleSim(c)
+    o.step(1)
+    f = o.fields(("id", "tag", "x", "u", "v", "p", "advp", "redp"))
+    start, idx = o.neighbors()
+    tag, u = f["tag"], f["u"]
+    out = np.nonzero(tag == OUTLET)[0]
+    red = [k for k in out if np.any(tag[idx[start[k]:start[k + 1]]] == FLUID)]
+    assert len(red) > 20
+    for k in red:
+        nb = idx[start[k]:start[k + 1]]
+        uf = u[nb[tag[nb] == FLUID]]
+        assert uf.min() - 1e-14 <= f["advp"][k] <= uf.max() + 1e-14
+        assert f["redp"][k] == 1
+    assert np.all(u[out] == 1.3)  # the particles' own velocity stays frozen
+    assert np.abs(f["advp"][red] - 1.3).min() > 0.2
+
+
+def test_characteristic_outlet_passes_a_right_running_wave():
+    # Sec. 3.3 with the free stream (U, p = 0) as reference: a fluid state u = U + a/(2 rho c),
+    # p = a/2 has J2 = a and J3 = 0; the red outlet particles reproduce it (p = J2/2,
+    # u = U + J2/(2 rho c)) and keep their transverse velocity
+    c = cases.channel(jitter=0.0, pulse_amp=0.0, n_in=4)
+    c.params.outlet_kind = OUTLET_KINDS["characteristic"]
+    a = 0.02
+    rho_c = c.params.rho0 * c.params.cs
+    fl = c.tag == FLUID
+    c.u[fl] += a / (2 * rho_c)
+    c.p[fl] += a / 2
+    c.v[c.tag == OUTLET] = 0.05
+    o = oracle.OracleSim(c)
+    o.step(1)
+    f = o.fields(("tag", "x", "u", "v", "p", "J2p", "redp"))
+    red = (f["tag"] == OUTLET) & (f["redp"] == 1)
+    assert red.sum() > 20
+    np.testing.assert_allclose(f["p"][red], 0.5 * f["J2p"][red], rtol=1e-13, atol=1e-16)
+    np.testing.assert_allclose(f["u"][red] - 1.0, f["J2p"][red] / (2 * rho_c), rtol=1e-12,
+                               atol=1e-16)
+    np.testing.assert_allclose(f["J2p"][red], a, rtol=0.1)
+    assert np.all(f["v"][f["tag"] == OUTLET] == 0.05)
+
+
+def test_mirrored_outlet_is_exact_for_linear_fields():
+    # Sec. 3.2 at the outlet: for linear f the first-order system returns f(x_k) and grad f
+    # exactly, so Eq. taylor2 gives f_o = f(x_k) - (x_o - x_k) f_x = f(4 x_out - 3 x_o, y_o)
+    c = cases.channel(jitter=0.0, pulse_amp=0.0, n_in=4, n_out=6)
+    c.params.outlet_kind = OUTLET_KINDS["mirror"]
+    o = oracle.OracleSim(c)
+    n = o.n
+    x, y = o.a["x"][:n], o.a["y"][:n]
+    # linear in x only: the channel is periodic in y, where a linear field would jump
+    lin = {"p": (0.3, -0.7, 0.0), "u": (1.0, 0.4, 0.0), "v": (-0.2, 0.1, 0.0)}
+    for k, (c0, cx, cy) in lin.items():
+        o.a[k][:n] = c0 + cx * x + cy * y
+    o.outlet_mirror()
+    tag = o.a["tag"][:n]
+    out = tag == OUTLET
+    xr = 4.0 * c.params.x_out - 3.0 * x[out]
+    for k, (c0, cx, cy) in lin.items():
+        want = c0 + cx * xr + cy * y[out]
+        np.testing.assert_allclose(o.a[k][:n][out], want, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(o.a["advp"][:n][out], o.a["u"][:n][out], rtol=0, atol=0)
+
+
 def _open_lattice(n=24):
     c = cases.taylor_green(n=n)
     c.params.periodic_x = 0
