@@ -114,10 +114,27 @@ edac_status edac_create(const edac_params *params, void *d_workspace, size_t byt
 edac_status edac_set_inlet(edac_ctx *ctx, double x_in, int n_layers, int n_modes,
                            const double *h_modes, double y0, double H);
 
-/* Outlet zone (Sec. 3.4): outlet particles sit in [x_out, x_out + n_layers dx);
- * kind must be 0 (hybrid).  n_avg: length of the time average (Eq. timeevg; 6 in
- * the paper, at most 8).  i_thresh < 0 selects I = (rho0 U^2/2)^2/(2 rho0 c_s)
- * of Eq. acouinten.  Call before edac_set_particles(). */
+/* Outlet zone: outlet particles sit in [x_out, x_out + n_layers dx) and move in x
+ * only; a fluid particle past x_out becomes an outlet particle, one past
+ * x_out + n_layers dx is deleted.  kind selects the treatment of Sec. 3:
+ *   EDAC_OUTLET_HYBRID (Sec. 3.4): frozen time averages plus the acoustic part
+ *     carried by J2 with J3 = 0; n_avg is the length of the time average
+ *     (Eq. timeevg; 6 in the paper, at most 8) and i_thresh < 0 selects
+ *     I = (rho0 U^2/2)^2/(2 rho0 c_s) of Eq. acouinten;
+ *   EDAC_OUTLET_DONOTHING (Sec. 3.1): u, v, p frozen at the crossing, advected
+ *     with that u;
+ *   EDAC_OUTLET_MOD_DONOTHING (Sec. 3.1.1): values frozen, advected with the
+ *     Shepard velocity of the fluid (Eq. shepard0);
+ *   EDAC_OUTLET_CHARACTERISTIC (Sec. 3.3): p = J2/2, u = U + J2/(2 rho0 c_s)
+ *     from the fluid's J2 against the free stream, v frozen;
+ *   EDAC_OUTLET_MIRROR (Sec. 3.2): p, u, v by the mirrored Taylor extrapolation
+ *     (Eqs. matform, taylor2) about (2 x_out - x, y).
+ * Call before edac_set_particles(). */
+#define EDAC_OUTLET_HYBRID 0
+#define EDAC_OUTLET_DONOTHING 1
+#define EDAC_OUTLET_MOD_DONOTHING 2
+#define EDAC_OUTLET_CHARACTERISTIC 3
+#define EDAC_OUTLET_MIRROR 4
 edac_status edac_set_outlet(edac_ctx *ctx, double x_out, int n_layers, int kind, int n_avg,
                             double i_thresh);
 

@@ -12,6 +12,12 @@
 #include "edac.h"
 #include "edac_internal.cuh"
 
+static_assert(edac::OUT_HYBRID == EDAC_OUTLET_HYBRID && edac::OUT_DONOTHING == EDAC_OUTLET_DONOTHING &&
+                  edac::OUT_MOD_DONOTHING == EDAC_OUTLET_MOD_DONOTHING &&
+                  edac::OUT_CHARACTERISTIC == EDAC_OUTLET_CHARACTERISTIC &&
+                  edac::OUT_MIRROR == EDAC_OUTLET_MIRROR,
+              "outlet kinds of the header and the kernels agree");
+
 using namespace edac;
 
 struct EventPair {
@@ -138,6 +144,7 @@ void make_phys(const edac_params &P, Phys &ph)
     ph.x_in = 0; ph.L_in = 0; ph.in_y0 = 0; ph.in_H = 1;
     for (int k = 0; k < MAX_MODES; ++k) ph.modes[k] = 0.0;
     ph.has_outlet = 0;
+    ph.outlet_kind = OUT_HYBRID;
     ph.n_avg = 6;
     ph.x_out = 0; ph.L_out = 0;
     const double q = 0.5 * P.rho0 * P.U * P.U;
@@ -393,11 +400,13 @@ edac_status edac_set_outlet(edac_ctx *ctx, double x_out, int n_layers, int kind,
                             double i_thresh)
 {
     if (!ctx) return EDAC_E_INVALID;
-    if (!is_fin(x_out) || n_layers < 1 || kind != 0 || n_avg < 1 || n_avg > NAVG_MAX ||
+    if (!is_fin(x_out) || n_layers < 1 || kind < EDAC_OUTLET_HYBRID || kind > EDAC_OUTLET_MIRROR ||
+        n_avg < 1 || n_avg > NAVG_MAX ||
         !is_fin(i_thresh))
         return fail(ctx, EDAC_E_INVALID, "bad outlet arguments");
     Phys &ph = ctx->d.ph;
     ph.has_outlet = 1;
+    ph.outlet_kind = kind;
     ph.x_out = x_out;
     ph.L_out = (double)n_layers * ctx->P.dx;
     ph.n_avg = n_avg;

@@ -276,12 +276,15 @@ __global__ void k_stage(Dev d, double tau)
             if (!(finite_bits(xn) & finite_bits(yn) & finite_bits(un) & finite_bits(vn) &
                   finite_bits(pn) & finite_bits(utn) & finite_bits(vtn)))
                 set_err(d, ERR_NONFINITE);
-            if (CORR && ph.has_outlet) {
+            if (CORR && ph.has_outlet && ph.outlet_kind == OUT_HYBRID) {
                 double ub, vb, pbv;
                 if (MIXED) ring_sample<float>(d, s, un, vn, pn, ub, vb, pbv);
                 else ring_sample<double>(d, s, un, vn, pn, ub, vb, pbv);
                 d.ubar[s] = ub; d.vbar[s] = vb; d.pbar[s] = pbv;
                 d.J2[s] = ph.rho0 * ph.cs * (un - ub) + (pn - pbv);
+            } else if (CORR && ph.has_outlet && ph.outlet_kind == OUT_CHARACTERISTIC) {
+                // Sec. 3.3 alone: J2 against the free stream (U, p = 0)
+                d.J2[s] = ph.rho0 * ph.cs * (un - ph.U) + pn;
             }
         } else if (t == INLET) {
             double x0;
@@ -315,7 +318,8 @@ __device__ __forceinline__ void ring_fill(const Dev &d, int s)
 
 // Transitions of the end of Sec. 3.4, taken once per step after the outlet update:
 // outlet past x_out + L_out -> deleted; fluid past x_out -> outlet (keeps its time
-// averages); inlet past x_in -> fluid (a new inlet particle is spawned by k_end_step).
+// averages; the other outlets: the values it crosses with); inlet past x_in -> fluid (a new
+// inlet particle is spawned by k_end_step).
 // Events go to per-kind lists by warp-aggregated appends; k_end_step puts them in
 // ascending id order before ids and slots are handed out.
 __global__ void k_recycle_mark(Dev d)
@@ -345,8 +349,12 @@ __global__ void k_recycle_mark(Dev d)
         }
         if (out) {
             d.tag[s] = OUTLET;
+            if (ph.outlet_kind == OUT_HYBRID) {  // keeps its time averages
+                d.u[s] = d.ubar[s]; d.v[s] = d.vbar[s]; d.p[s] = d.pbar[s];
+            } else {  // the other outlets freeze the values it crosses with
+                d.ubar[s] = d.u[s]; d.vbar[s] = d.v[s]; d.pbar[s] = d.p[s];
+            }
             const double ub = d.ubar[s];
-            d.u[s] = ub; d.v[s] = d.vbar[s]; d.p[s] = d.pbar[s];
             d.ut[s] = ub; d.vt[s] = d.vbar[s];
             d.J2p[s] = 0.0; d.redp[s] = 0; d.advp[s] = ub;
             if (iout < LIST_MAX) { d.ev_out_key[iout] = d.id[s]; d.ev_out_m[iout] = d.m[s]; }

@@ -21,6 +21,10 @@ enum : uint8_t { FLUID = 0, INLET = 1, OUTLET = 2, WALL = 3, SLIPWALL = 4 };
 // sticky device error bits
 enum : unsigned { ERR_CAPACITY = 1u, ERR_NONFINITE = 2u, ERR_DOMAIN = 4u, ERR_LIST = 8u,
                   ERR_TIMEOUT = 16u };
+// outlet treatments (Sec. 3): hybrid (3.4), do-nothing (3.1), modified do-nothing (3.1.1),
+// method of characteristics (3.3), mirroring (3.2)
+enum : int { OUT_HYBRID = 0, OUT_DONOTHING = 1, OUT_MOD_DONOTHING = 2, OUT_CHARACTERISTIC = 3,
+             OUT_MIRROR = 4 };
 
 // Geometry of the cell grid and the support radius.
 struct Geo {
@@ -45,6 +49,7 @@ struct Phys {
     double x_in, L_in, in_y0, in_H;
     double modes[MAX_MODES];
     int has_outlet, n_avg;
+    int outlet_kind;                 // EDAC_OUTLET_* (hybrid unless set)
     double x_out, L_out, I_thr;
     int wall_slip[2], wall_drag[2];
     double wall_u[2], wall_v[2];

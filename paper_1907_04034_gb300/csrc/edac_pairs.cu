@@ -58,9 +58,6 @@ __device__ __forceinline__ void listed_neighbors(const Dev &d, int k, double qx,
     for (int c = 0; c < cnt; ++c) body(lst[c * TPB]);
 }
 
-// r from r^2 without the IEEE square root: r^2 * rsqrt(r^2), 0 for coincident particles
-__device__ __forceinline__ float fast_r(float r2) { return r2 > 0.f ? r2 * rsqrtf(r2) : 0.f; }
-
 // ------------------------------------------------------------------ fp64 path: pass A
 // S_i = sum_j W_ij, V_i = 1/S_i (number-density volume, Sec. 2), rho_i = sum_j m_j W_ij
 // (Eq. summation-density), N_i = number of neighbours (self included).
@@ -959,12 +956,97 @@ __device__ bool solve3(const double (&M)[3][3], const double (&b)[3], double (&x
     return true;
 }
 
+// Mirrored Taylor extrapolation (Sec. 3.2): the first-order system of Eq. matform at the
+// mirror point k over its fluid neighbours l (r_lk = r_l - r_k, V_l = m_l/rho_l), solved with
+// partial pivoting for NF fluid fields (p, u, v in that order, one matrix), then
+// f_o = f_k - (r_o - r_k).grad f_k (Eq. taylor2).  No fluid in reach: f_o = 0; singular
+// system (|det| <= 1e-9 |M00 M11 M22|): the Shepard value sum f W V / sum W V; all weights
+// zero (every fluid neighbour at the support edge): the plain mean of f.  fp64 on both paths:
+// with disordered particles the system can be ill-conditioned and fp32 moment sums would
+// lose the solution.  Whole warp; lane 0 receives fo.
+template <int MIXED, int NF>
+__device__ __forceinline__ void mirror_extrapolate(const Dev &d, int lane, int *wbuf, double xo,
+                                                   double yo, double xk, double yk,
+                                                   double (&fo)[NF])
+{
+    const Geo &g = d.g;
+    const Phys &ph = d.ph;
+    const int cx = cell_coord(xk, g.x_min, g.inv_sx, g.nx);
+    const int cy = cell_coord(yk, g.y_min, g.inv_sy, g.ny);
+    const float rx = (float)(xk - (g.x_min + (double)cx * g.sx));
+    const float ry = (float)(yk - (g.y_min + (double)cy * g.sy));
+    // [M (9) | right-hand sides (3 per field) | count | plain sums (1 per field)]
+    constexpr int NA = 9 + 3 * NF + 1 + NF;
+    double a[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) a[i] = 0.0;
+    lane_fluid_compact(d, lane, wbuf, xk, yk, cx, cy, rx, ry, [&](int l) {
+        const double2 xyl = d.XY[l];
+        double xlk, ylk;  // r_lk = r_l - r_k, the canonical fp64 separation
+        const double r2 = exact_r2(g, xyl.x, xyl.y, xk, yk, xlk, ylk);
+        double fv[3], Vl;
+        fluid_fields<MIXED>(d, l, fv[0], fv[1], fv[2], Vl);
+        double w, wx = 0, wy = 0;
+        if (r2 > 1e-30) {
+            // fp64 path: IEEE square root and division (the oracle's arithmetic);
+            // mixed path: Newton-refined inverse square root, no fp64 division
+            double ir, r;
+            if (MIXED) { ir = rsqrt_newton(r2); r = r2 * ir; }
+            else { r = sqrt(r2); ir = 1.0 / r; }
+            double wq, dwq;
+            quintic_w_dw(r * ph.inv_h, wq, dwq);
+            w = ph.a2 * wq;
+            const double dwr = ph.a2h * dwq * ir;
+            wx = dwr * xlk;
+            wy = dwr * ylk;
+        } else {
+            w = ph.a2 * quintic_w(0.0);
+        }
+        const double row[3] = {w * Vl, wx * Vl, wy * Vl};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            a[3 * q + 0] += row[q];
+            a[3 * q + 1] += xlk * row[q];
+            a[3 * q + 2] += ylk * row[q];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) a[9 + 3 * f + q] += fv[f] * row[q];
+        }
+        a[9 + 3 * NF] += 1.0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) a[10 + 3 * NF + f] += fv[f];
+    });
+    warp_sum(a);
+    if (lane != 0) return;
+    double M[3][3];
+    for (int q = 0; q < 3; ++q)
+        for (int c = 0; c < 3; ++c) M[q][c] = a[3 * q + c];
+    const double cnt = a[9 + 3 * NF];
+    const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                       M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                       M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    const bool singular = fabs(det) <= 1e-9 * fabs(M[0][0] * M[1][1] * M[2][2]);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const double bb[3] = {a[9 + 3 * f], a[10 + 3 * f], a[11 + 3 * f]};
+        double pk = 0.0, gxp = 0.0, gyp = 0.0;
+        if (cnt > 0.0 && !(M[0][0] > 0.0)) {
+            pk = a[10 + 3 * NF + f] / cnt;
+        } else if (cnt > 0.0) {
+            pk = bb[0] / M[0][0];
+            if (!singular) {
+                double sol[3] = {0.0, 0.0, 0.0};
+                if (solve3(M, bb, sol)) { pk = sol[0]; gxp = sol[1]; gyp = sol[2]; }
+            }
+        }
+        fo[f] = pk - ((xo - xk) * gxp + (yo - yk) * gyp);
+    }
+}
+
 template <int MIXED>
 __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
 {
     typedef typename std::conditional<MIXED, float, double>::type T;
     __shared__ int wbuf[8][CMP_CAP];  // per-warp list of the mirror's fluid neighbours
-    const Geo &g = d.g;
     const Phys &ph = d.ph;
     const int lane = threadIdx.x & 31;
     const int nb = d.cnt->n_bnd;
@@ -1021,74 +1103,12 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                 d.p[s] = pw; d.u[s] = ug; d.v[s] = vg; d.ut[s] = ug; d.vt[s] = vg;
             }
         } else if (t == INLET && ph.has_inlet) {
-            // Mirrored inlet pressure (Sec. 3.2): first-order Taylor system (Eq. matform) at
-            // the mirror point k = (2 x_in - x_o, y_o) over fluid l with r_lk = r_l - r_k and
-            // V_l = m_l/rho_l, solved with partial pivoting; p_o = p_k - (r_o - r_k).grad p_k
-            // (Eq. taylor2).  No fluid in reach: p_o = 0; singular system
-            // (|det| <= 1e-9 |M00 M11 M22|): the Shepard value sum p W V / sum W V; all
-            // weights zero (every fluid neighbour at the support edge): the plain mean of p.
-            const double xk = 2.0 * ph.x_in - xy.x, yk = xy.y;
-            const int cx = cell_coord(xk, g.x_min, g.inv_sx, g.nx);
-            const int cy = cell_coord(yk, g.y_min, g.inv_sy, g.ny);
-            const float rx = (float)(xk - (g.x_min + (double)cx * g.sx));
-            const float ry = (float)(yk - (g.y_min + (double)cy * g.sy));
-            // fp64 on both paths: with disordered particles the system can be ill-conditioned
-            // and fp32 moment sums would lose the solution
-            double a[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-            lane_fluid_compact(d, lane, wbuf[threadIdx.x >> 5], xk, yk, cx, cy, rx, ry, [&](int l) {
-                const double2 xyl = d.XY[l];
-                double xlk, ylk;  // r_lk = r_l - r_k, the canonical fp64 separation
-                const double r2 = exact_r2(g, xyl.x, xyl.y, xk, yk, xlk, ylk);
-                double p, u, v, Vl;
-                fluid_fields<MIXED>(d, l, p, u, v, Vl);
-                double w, wx = 0, wy = 0;
-                if (r2 > 1e-30) {
-                    // fp64 path: IEEE square root and division (the oracle's arithmetic);
-                    // mixed path: Newton-refined inverse square root, no fp64 division
-                    double ir, r;
-                    if (MIXED) { ir = rsqrt_newton(r2); r = r2 * ir; }
-                    else { r = sqrt(r2); ir = 1.0 / r; }
-                    double wq, dwq;
-                    quintic_w_dw(r * ph.inv_h, wq, dwq);
-                    w = ph.a2 * wq;
-                    const double dwr = ph.a2h * dwq * ir;
-                    wx = dwr * xlk;
-                    wy = dwr * ylk;
-                } else {
-                    w = ph.a2 * quintic_w(0.0);
-                }
-                const double row[3] = {w * Vl, wx * Vl, wy * Vl};
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    a[3 * q + 0] += row[q];
-                    a[3 * q + 1] += xlk * row[q];
-                    a[3 * q + 2] += ylk * row[q];
-                    a[9 + q] += p * row[q];
-                }
-                a[12] += 1.0;
-                a[13] += p;
-            });
-            warp_sum(a);
+            // Mirrored inlet pressure (Sec. 3.2) about k = (2 x_in - x_o, y_o)
+            double fo[1];
+            mirror_extrapolate<MIXED, 1>(d, lane, wbuf[threadIdx.x >> 5], xy.x, xy.y,
+                                         2.0 * ph.x_in - xy.x, xy.y, fo);
             if (lane == 0) {
-                double M[3][3], bb[3];
-                for (int q = 0; q < 3; ++q) {
-                    for (int c = 0; c < 3; ++c) M[q][c] = (double)a[3 * q + c];
-                    bb[q] = (double)a[9 + q];
-                }
-                double pk = 0.0, gxp = 0.0, gyp = 0.0;
-                if (a[12] > 0.0 && !(M[0][0] > 0.0)) {
-                    pk = a[13] / a[12];  // all weights zero (fluid at the support edge): mean
-                } else if (a[12] > 0.0) {
-                    const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
-                                       M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
-                                       M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
-                    pk = bb[0] / M[0][0];
-                    if (!(fabs(det) <= 1e-9 * fabs(M[0][0] * M[1][1] * M[2][2]))) {
-                        double sol[3] = {0.0, 0.0, 0.0};
-                        if (solve3(M, bb, sol)) { pk = sol[0]; gxp = sol[1]; gyp = sol[2]; }
-                    }
-                }
-                const double po = pk - ((xy.x - xk) * gxp + (xy.y - yk) * gyp);
+                const double po = fo[0];
                 if (MIXED) {
                     float4 q = d.Qf[k];
                     q.x = (float)po;
@@ -1098,25 +1118,44 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                 }
                 d.p[s] = po;
             }
-        } else if (t == OUTLET && end_of_step && ph.has_outlet) {
-            // Hybrid outlet (Sec. 3.4): red particles (fluid in reach) take the Shepard J2
-            // of the fluid; blue ones the mean previous-step J2 of red outlet neighbours.
-            // J3 = 0 gives p' = J2/2, u' = J2/(2 rho0 c); value = frozen average + acoustic
-            // part (Eq. acou).  Written to the slot arrays only: the rates of this
-            // evaluation still see the outlet values of the step.
+        } else if (t == OUTLET && end_of_step && ph.has_outlet &&
+                   (ph.outlet_kind == OUT_HYBRID || ph.outlet_kind == OUT_CHARACTERISTIC ||
+                    ph.outlet_kind == OUT_MOD_DONOTHING)) {
+            // Outlet update (Sec. 3), once per step; red particles have fluid in reach.
+            //   hybrid (Sec. 3.4): red take the Shepard J2 of the fluid, blue the mean
+            //     previous-step J2 of their red outlet neighbours; J3 = 0 gives p' = J2/2,
+            //     u' = J2/(2 rho0 c); value = frozen average + acoustic part (Eq. acou);
+            //   characteristic (Sec. 3.3): the same J2 against the free stream (U, p = 0),
+            //     v stays frozen;
+            //   modified do-nothing (Sec. 3.1.1): values stay frozen, red advect with the
+            //     Shepard u of the fluid (Eq. shepard0), blue with the mean previous-step
+            //     advection velocity of their red neighbours.
+            // Do-nothing (Sec. 3.1) needs no update; mirroring runs in k_outlet_mirror.
+            // Written to the slot arrays only: the rates of this evaluation still see the
+            // outlet values of the step.
+            const int kind = ph.outlet_kind;
             int cx, cy;
             cell_of(d, k, cx, cy);
             const float4 pk = d.P[k];
+            // [sum W, sum W f, fluid count, sum J2p, sum adv of red, red count, sum f] with
+            // f = J2 of the fluid (u for the modified do-nothing)
             T a[7] = {0, 0, 0, 0, 0, 0, 0};
             lane_neighbors<MIXED>(d, lane, xy.x, xy.y, cx, cy, pk.x, pk.y, [&](int j, T, T, T r2) {
                 const uint8_t tj = d.stag[j];
                 if ((tj & 0x7f) == FLUID) {
                     const T w = a2 * quintic_w(sqrt_t<T>(r2) * inv_h);
-                    const T J2j = (T)d.AUX[j].x;  // J2 of the fluid particle
+                    T fj;
+                    if (kind == OUT_MOD_DONOTHING) {
+                        T p, u, v, mr;
+                        fluid_fields<MIXED>(d, j, p, u, v, mr);
+                        fj = u;
+                    } else {
+                        fj = (T)d.AUX[j].x;  // J2 of the fluid particle
+                    }
                     a[0] += w;
-                    a[1] += w * J2j;
+                    a[1] += w * fj;
                     a[2] += (T)1;
-                    a[6] += J2j;
+                    a[6] += fj;
                 } else if (tj == (OUTLET | TAG_REDP)) {
                     const double2 x2 = d.AUX[j];
                     a[3] += (T)x2.x;
@@ -1128,21 +1167,62 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
             if (lane == 0) {
                 const bool red = a[2] > (T)0;
                 const T mr = a[5];
-                // Shepard J2; all weights zero (fluid at the support edge): plain mean
-                const T J2 = red ? (a[0] > (T)0 ? a[1] / a[0] : a[6] / a[2])
-                                 : (mr > (T)0 ? a[3] / mr : (T)0);
-                const double ub = d.ubar[s];
-                const double un = ub + (double)(J2 * (MIXED ? (T)ph.inv_2rcf : (T)ph.inv_2rc));
-                const double adv = red ? un : (mr > (T)0 ? (double)(a[4] / mr) : ub);
-                d.u[s] = un;
-                d.v[s] = d.vbar[s];
-                d.p[s] = d.pbar[s] + (double)((T)0.5 * J2);
-                d.ut[s] = un;
-                d.vt[s] = d.vbar[s];
-                d.J2p[s] = (double)J2;
-                d.advp[s] = adv;
-                d.redp[s] = red ? 1 : 0;
+                // Shepard average; all weights zero (fluid at the support edge): plain mean
+                const T shep = red ? (a[0] > (T)0 ? a[1] / a[0] : a[6] / a[2]) : (T)0;
+                const double blue_adv = mr > (T)0 ? (double)(a[4] / mr) : 0.0;
+                if (kind == OUT_MOD_DONOTHING) {
+                    d.J2p[s] = 0.0;
+                    d.advp[s] = red ? (double)shep : (mr > (T)0 ? blue_adv : d.ubar[s]);
+                    d.redp[s] = red ? 1 : 0;
+                } else {
+                    const bool ch = kind == OUT_CHARACTERISTIC;
+                    const T J2 = red ? shep : (mr > (T)0 ? a[3] / mr : (T)0);
+                    const double ub = ch ? ph.U : d.ubar[s];
+                    const double pb = ch ? 0.0 : d.pbar[s];
+                    const double un = ub + (double)(J2 * (MIXED ? (T)ph.inv_2rcf : (T)ph.inv_2rc));
+                    const double adv = red ? un : (mr > (T)0 ? blue_adv : (ch ? un : ub));
+                    d.u[s] = un;
+                    d.v[s] = d.vbar[s];
+                    d.p[s] = pb + (double)((T)0.5 * J2);
+                    d.ut[s] = un;
+                    d.vt[s] = d.vbar[s];
+                    d.J2p[s] = (double)J2;
+                    d.advp[s] = adv;
+                    d.redp[s] = red ? 1 : 0;
+                }
             }
+        }
+    }
+}
+
+// Mirrored outlet (Sec. 3.2 at the outlet), once per step: p, u, v of every outlet particle
+// by the Taylor extrapolation about k = (2 x_out - x_o, y_o); the particle advects with that
+// u.  One warp per boundary particle, outlet particles only.
+template <int MIXED>
+__global__ void __launch_bounds__(256) k_outlet_mirror(Dev d)
+{
+    __shared__ int wbuf[8][CMP_CAP];
+    const Phys &ph = d.ph;
+    const int lane = threadIdx.x & 31;
+    const int nb = d.cnt->n_bnd;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nwarps) {
+        const int k = d.bnd[b];
+        if ((d.stag[k] & 0x7f) != OUTLET) continue;
+        const int s = d.order[k];
+        const double2 xy = d.XY[k];
+        double fo[3];
+        mirror_extrapolate<MIXED, 3>(d, lane, wbuf[threadIdx.x >> 5], xy.x, xy.y,
+                                     2.0 * ph.x_out - xy.x, xy.y, fo);
+        if (lane == 0) {
+            d.p[s] = fo[0];
+            d.u[s] = fo[1];
+            d.v[s] = fo[2];
+            d.ut[s] = fo[1];
+            d.vt[s] = fo[2];
+            d.advp[s] = fo[1];
+            d.J2p[s] = 0.0;
+            d.redp[s] = 0;
         }
     }
 }
@@ -1193,6 +1273,11 @@ int launch_boundary(const Dev &d, cudaStream_t s, int mixed, int end_of_step)
     const int blocks = min(grid_for(d.cap, 64), 152 * 16);
     if (mixed) k_boundary<1><<<blocks, 256, 0, s>>>(d, end_of_step);
     else k_boundary<0><<<blocks, 256, 0, s>>>(d, end_of_step);
+    if (end_of_step && d.ph.has_outlet && d.ph.outlet_kind == OUT_MIRROR) {
+        if (mixed) k_outlet_mirror<1><<<blocks, 256, 0, s>>>(d);
+        else k_outlet_mirror<0><<<blocks, 256, 0, s>>>(d);
+        return 2;
+    }
     return 1;
 }
 

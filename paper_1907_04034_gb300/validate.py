@@ -24,14 +24,18 @@ import numpy as np
 from . import binding, cases
 
 
+OUTLETS = {"hybrid": 0, "donothing": 1, "mod_donothing": 2, "characteristic": 3, "mirror": 4}
+
+
 def paper_cylinder(dx_over_d: float = 30.0, Re: float = 200.0, D: float = 1.0,
-                   layers: int = 6) -> cases.Case:
+                   layers: int = 6, outlet: str = "hybrid") -> cases.Case:
     """The Sec. 4.6 geometry at spacing D / dx_over_d (D = 1 instead of 2 m: only D/dx, Re and
-    the convective time matter for the coefficients)."""
+    the convective time matter for the coefficients), with one of the outlets of Sec. 3."""
     dx = D / dx_over_d
-    return cases.cylinder(dx=dx, D=D, Re=Re, Lx=15.0 * D, H=15.0 * D, xc=5.0 * D,
-                          n_solid=int(0.5 * D / dx) + 1, n_in=layers, n_out=layers,
-                          n_wall=layers)
+    c = cases.cylinder(dx=dx, D=D, Re=Re, Lx=15.0 * D, H=15.0 * D, xc=5.0 * D,
+                       n_solid=int(0.5 * D / dx) + 1, n_in=layers, n_out=layers, n_wall=layers)
+    c.params.outlet_kind = OUTLETS[outlet]
+    return c
 
 
 def moving_average(a: np.ndarray, k: int = 5) -> np.ndarray:
@@ -74,17 +78,18 @@ def coefficients(fx, fy, dt: float, D: float, U: float, rho0: float, t_from: flo
 
 def run(dx_over_d: float = 30.0, Re: float = 200.0, t_end: float = 75.0, t_from: float = None,
         precision: str = "mixed", chunk: int = 5000, device: str = "cuda:0",
-        diagnose: bool = False) -> dict:
+        diagnose: bool = False, outlet: str = "hybrid") -> dict:
     import torch
 
-    case = paper_cylinder(dx_over_d, Re)
+    case = paper_cylinder(dx_over_d, Re, outlet=outlet)
     p = case.params
     D, U = p.drag_length, p.U
     nsteps = int(math.ceil(t_end * U / D / p.dt)) if D > 0 else 0
     solver = binding.Solver(case, precision=precision, use_graphs=True, device=device,
                             max_history=nsteps + 16)
     torch.cuda.synchronize(torch.device(device))
-    out = {"case": f"cylinder Re={Re:g}, 15D x 15D, dx=D/{dx_over_d:g}", "precision": precision,
+    out = {"case": f"cylinder Re={Re:g}, 15D x 15D, dx=D/{dx_over_d:g}", "outlet": outlet,
+           "precision": precision,
            "particles": case.n, "fluid": int(np.sum(case.tag == cases.FLUID)), "dt": p.dt}
     t0 = time.perf_counter()
     done = 0
@@ -135,9 +140,10 @@ def main():
     ap.add_argument("--chunk", type=int, default=5000, help="steps per edac_step call")
     ap.add_argument("--diagnose", action="store_true",
                     help="record the per-tag field ranges after every chunk")
+    ap.add_argument("--outlet", default="hybrid", choices=tuple(OUTLETS))
     a = ap.parse_args()
     print(json.dumps(run(a.dx_over_d, a.re, a.t_end, a.t_from, a.precision, a.chunk,
-                         diagnose=a.diagnose)))
+                         diagnose=a.diagnose, outlet=a.outlet)))
 
 
 if __name__ == "__main__":
