@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--batch-channels", type=int, default=64,
+                    help="uneven channels of the batched measurement (0: skip it)")
+    ap.add_argument("--batch-steps", type=int, default=200)
     return ap.parse_args()
 
 
@@ -164,6 +167,61 @@ def load_peaks():
 def fp32_peak_tflops(sm_count, max_mhz):
     """FP32 FMA pipe: 128 lanes per SM, 2 flops per FMA, at the maximum SM clock."""
     return sm_count * 128 * 2 * max_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------------------ batched
+def run_batched(n_chan, steps, dev):
+    """The batched workload: uneven pulse channels (seeded sizes, spacings, Re and pulse
+    centres), mixed path, every member's tiling picked by the autotuner, all advanced by one
+    graph launch per step.  Also timed: the same members stepped one after the other."""
+    import torch
+    from paper_1907_04034_gb300 import binding, cases
+
+    chans = cases.batch_channels(n=n_chan, seed=0)
+    sol = [binding.Solver(c, precision="mixed", use_graphs=True, device=str(dev),
+                          max_history=2 * steps + 64) for c in chans]
+    tilings = [s.autotune(trials=2)[:2] for s in sol]
+    b = binding.Batch(sol)
+    warm = 5
+    b.step(warm)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(steps)
+    e1.record(b.stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    ps = 0.0
+    for s in sol:
+        h = s.history(warm + steps)
+        ps += float(np.sum(h["n_active"][warm:warm + steps]))
+    kps = b.kernels_per_step()
+    b.close()
+    # the same members one after the other (each its own graph, one host thread)
+    seq_steps = max(1, steps // 4)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for s in sol:
+        s.step(seq_steps)
+    torch.cuda.synchronize(dev)
+    seq = time.perf_counter() - t0
+    seq_ps = sum(float(np.sum(s.history(warm + steps + seq_steps)["n_active"][warm + steps:]))
+                 for s in sol)
+    for s in sol:
+        s.close()
+    sizes = [c.n for c in chans]
+    from collections import Counter
+    return {"value": ps / (ms * 1e-3), "unit": UNIT, "channels": n_chan, "steps": steps,
+            "ms_per_step": ms / steps, "particles": int(sum(sizes)),
+            "particles_min_max": [int(min(sizes)), int(max(sizes))],
+            "kernels_per_graph_launch": kps,
+            "tilings": {f"{tx}x{tpb}": k for (tx, tpb), k in Counter(tilings).items()},
+            "members_one_after_another": {"value": seq_ps / seq, "unit": UNIT,
+                                          "steps": seq_steps,
+                                          "note": "host wall clock, each member its own graph"},
+            "workload": "uneven pulse channels: N ~ U[2k, 60k], dx ~ U[0.005, 0.03], "
+                        "Re ~ U[50, 500], pulse centre uniform (seed 0); mixed path"}
 
 
 # -------------------------------------------------------------------------- reference
@@ -353,6 +411,11 @@ def main():
     se.close()
     del se
 
+    # ------------------------------------------- batched uneven channels (one graph launch)
+    batched = None
+    if args.batch_channels > 0:
+        batched = run_batched(args.batch_channels, args.batch_steps, dev)
+
     # ---------------------------------------------------------------------- CPU baseline
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -376,6 +439,7 @@ def main():
                               "pair_kernels": roof64},
                 "mixed_over_fp64": value / v64 if v64 else None,
                 "drag_rel_err_mixed_vs_fp64": drag_err, "drag_steps_compared": nc,
+                "batched": batched,
                 "kernel_ms_per_launch": kernels, "eager_step_ms": step_ms_eager}
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -251,6 +251,52 @@ edac_status edac_density_static(const edac_params *params, int n, const double *
 #define EDAC_PEAK_FP64 1
 edac_status edac_fma_peak(int kind, void *cuda_stream, double *tflops);
 
+/* ---------------------------------------------------------------------------
+ * Tiling of the mixed path's pair passes (no effect on the fp64 path): a tile
+ * is a row segment of tile_cells cells (1..EDAC_TILE_MAX_CELLS) whose block has
+ * `threads` threads (64 or 128).  The default, 8 cells and 128 threads, suits
+ * large systems; small ones fill the GPU better with smaller tiles.  Results
+ * differ only in the rounding of the fp32 sums (the candidate order changes).
+ * EDAC_E_INVALID outside those values.  Drops the captured step graph. */
+#define EDAC_TILE_MAX_CELLS 8
+edac_status edac_set_tiling(edac_ctx *ctx, int tile_cells, int threads);
+
+/* Autotuner of that tiling: times `trials` evaluations (edac_evaluate, which
+ * recomputes the rates of the current state: positions, velocities and
+ * pressures stay as they are) for each candidate tiling on the context's
+ * stream, keeps the fastest, evaluates once more with it and returns it
+ * (tile_cells, threads, ms per evaluation; any of them may be NULL).  On the
+ * fp64 path it only times the one configuration.  Synchronises the stream. */
+edac_status edac_autotune(edac_ctx *ctx, int trials, int *tile_cells, int *threads, double *ms);
+
+/* ---------------------------------------------------------------------------
+ * Batches of independent systems (uneven channels, parameter sweeps): one call
+ * advances every member one step per graph launch.  The paper has no
+ * counterpart; this is the throughput mode for many small systems, which one
+ * at a time cannot fill the GPU.  edac_batch_create captures one step of each
+ * member, each on its own stream (a non-default stream other than cuda_stream,
+ * the batch's own; members that share a stream run one after the other), into
+ * one CUDA graph whose branches run concurrently.  Configure the members (inlet, outlet, walls,
+ * tiling, particles) first: a member changed afterwards needs a new batch.
+ * Members must outlive the batch.  The members' results are bitwise those of
+ * stepping each alone.  Errors: EDAC_E_INVALID (NULL, repeated members, a
+ * member on the default or the batch stream), EDAC_E_STATE (a member without particles, in error or
+ * profiling), EDAC_E_CUDA (capture failed).  Errors of the calls without a
+ * context are read with edac_last_error(NULL). */
+typedef struct edac_batch edac_batch;
+edac_status edac_batch_create(edac_ctx *const *ctxs, int n, void *cuda_stream, edac_batch **out);
+
+/* nsteps steps of every member: nsteps graph launches on the batch stream, which
+ * first waits for the work queued on the members' streams; the members' streams
+ * then wait for the batch.  Asynchronous. */
+edac_status edac_batch_step(edac_batch *batch, int nsteps);
+
+/* Kernels launched per batch step (all members). */
+edac_status edac_batch_launch_count(edac_batch *batch, int64_t *kernels_per_step);
+
+/* Release the batch (synchronises its stream); the members stay valid. */
+void edac_batch_destroy(edac_batch *batch);
+
 /* Text of the last error of this context (valid until the next call); with
  * ctx = NULL, the last error of a context-less call (edac_workspace_bytes,
  * edac_create) made on this host thread. */

@@ -40,7 +40,9 @@ EXPORTS = ("edac_workspace_bytes", "edac_create", "edac_set_inlet", "edac_set_ou
            "edac_set_wall", "edac_set_particles", "edac_step", "edac_evaluate", "edac_get_count",
            "edac_read_state", "edac_read_history", "edac_neighbor_scratch_bytes",
            "edac_read_neighbors", "edac_profile", "edac_read_profile", "edac_launch_count",
-           "edac_density_static", "edac_fma_peak", "edac_last_error", "edac_destroy")
+           "edac_density_static", "edac_fma_peak", "edac_set_tiling", "edac_autotune",
+           "edac_batch_create", "edac_batch_step", "edac_batch_launch_count", "edac_batch_destroy",
+           "edac_last_error", "edac_destroy")
 
 
 class EdacError(RuntimeError):
@@ -145,8 +147,9 @@ def load(path: Optional[str] = None):
         L.edac_last_error.restype = C.c_char_p
         L.edac_destroy.argtypes = [_P]
         L.edac_destroy.restype = None
+        L.edac_batch_destroy.restype = None
         for name in EXPORTS:
-            if name not in ("edac_last_error", "edac_destroy"):
+            if name not in ("edac_last_error", "edac_destroy", "edac_batch_destroy"):
                 getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -349,6 +352,17 @@ class Solver:
         self._call("edac_read_profile", KERNELS[kernel], C.byref(ms), C.byref(ln), int(reset))
         return ms.value, ln.value
 
+    def set_tiling(self, tile_cells: int, threads: int):
+        """Tiling of the mixed pair passes (edac_set_tiling)."""
+        self._call("edac_set_tiling", int(tile_cells), int(threads))
+
+    def autotune(self, trials: int = 3):
+        """Pick the fastest tiling by timing evaluations (edac_autotune); returns
+        (tile_cells, threads, ms per evaluation)."""
+        tx, tpb, ms = C.c_int(0), C.c_int(0), C.c_double(0.0)
+        self._call("edac_autotune", int(trials), C.byref(tx), C.byref(tpb), C.byref(ms))
+        return tx.value, tpb.value, ms.value
+
     def launch_count(self) -> int:
         c = C.c_int64(0)
         self._call("edac_launch_count", C.byref(c))
@@ -359,6 +373,60 @@ class Solver:
             with self.torch.cuda.device(self.device):
                 self.lib.edac_destroy(self.ctx)
             self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent systems advanced together: one graph launch per step whose branches are
+    the members' steps (edac_batch_create / edac_batch_step).  The members are ``Solver``
+    objects on one device, each with its own stream; configure them first."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+
+        self.lib = load()
+        self.solvers = list(solvers)
+        dev = self.solvers[0].device
+        self.device = dev
+        # torch hands out streams from per-priority pools: the members' default-priority
+        # streams may repeat (that only serialises them), the batch's own comes from the
+        # high-priority pool so that it differs from every member's
+        self.stream = stream if stream is not None else torch.cuda.Stream(dev, priority=-1)
+        arr = (C.c_void_p * len(self.solvers))(*[s.ctx.value for s in self.solvers])
+        self.b = C.c_void_p()
+        with torch.cuda.device(dev):
+            rc = self.lib.edac_batch_create(arr, len(self.solvers), C.c_void_p(self.stream.cuda_stream),
+                                            C.byref(self.b))
+        if rc != 0:
+            raise EdacError(rc, self.lib.edac_last_error(None).decode())
+
+    def step(self, n: int = 1):
+        import torch
+
+        with torch.cuda.device(self.device):
+            rc = self.lib.edac_batch_step(self.b, int(n))
+        if rc != 0:
+            raise EdacError(rc, self.lib.edac_last_error(None).decode())
+
+    def kernels_per_step(self) -> int:
+        k = C.c_int64(0)
+        rc = self.lib.edac_batch_launch_count(self.b, C.byref(k))
+        if rc != 0:
+            raise EdacError(rc, "edac_batch_launch_count")
+        return k.value
+
+    def close(self):
+        if getattr(self, "b", None) and self.b.value:
+            import torch
+
+            with torch.cuda.device(self.device):
+                self.lib.edac_batch_destroy(self.b)
+            self.b = C.c_void_p()
 
     def __del__(self):
         try:

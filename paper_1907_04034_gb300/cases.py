@@ -163,6 +163,32 @@ def channel(dx: float = 0.02, nu: float = 0.01, seed: int = 0, jitter: float = 0
     return c
 
 
+def batch_channels(n: int = 64, seed: int = 0, n_min: int = 2000, n_max: int = 60000,
+                   dx_min: float = 0.005, dx_max: float = 0.03, re_min: float = 50.0,
+                   re_max: float = 500.0, U: float = 1.0) -> list:
+    """Independent pulse channels of uneven size (the batched workload).  Per channel, from
+    one seeded generator: a fluid count N ~ U[n_min, n_max], a spacing dx ~ U[dx_min, dx_max],
+    Re = U H / nu ~ U[re_min, re_max] and a pulse centre uniform in the channel.  Each channel
+    is L x H = L x L/2 with L = dx sqrt(2 N) rounded to whole spacings (so it holds about N
+    fluid particles), periodic in y, with the pulse of the channel workload scaled to L
+    (amplitude 0.1, exp(-r^2 / (0.005 L^2)))."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        N = int(rng.integers(n_min, n_max + 1))
+        dx = float(rng.uniform(dx_min, dx_max))
+        Re = float(rng.uniform(re_min, re_max))
+        nx = max(32, int(round(math.sqrt(2.0 * N))))
+        ny = max(16, int(round(0.5 * nx)))
+        L, H = nx * dx, ny * dx
+        px, py = float(rng.uniform(0.0, L)), float(rng.uniform(0.0, H))
+        c = channel(dx=dx, nu=U * H / Re, seed=seed * 1000 + i, L=L, H=H, U=U,
+                    pulse_xy=(px, py), pulse_w=0.005 * L * L)
+        c.name = f"channel{i}"
+        out.append(c)
+    return out
+
+
 def cylinder(dx: float = 1.0 / 40.0, D: float = 1.0, Re: float = 200.0, Lx: float = 15.0,
              H: float = 10.0, xc: float = 5.0, n_solid: int = 3, n_in: int = 3, n_out: int = 5,
              n_wall: int = 4, U: float = 1.0, inlet_modes=()) -> Case:

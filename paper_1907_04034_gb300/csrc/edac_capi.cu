@@ -370,6 +370,8 @@ edac_status edac_create(const edac_params *params, void *d_workspace, size_t byt
     c->d.cap = params->capacity;
     c->d.mixed = c->mixed;
     c->d.max_history = params->max_history;
+    c->d.tile_tx = 8;
+    c->d.tile_tpb = 128;
     layout(c->d, g, params->capacity, params->max_history, c->mixed, c->ws);
     *out = c;
     return EDAC_OK;
@@ -784,6 +786,193 @@ edac_status edac_launch_count(edac_ctx *ctx, int64_t *count)
 const char *edac_last_error(edac_ctx *ctx)
 {
     return ctx ? ctx->err.c_str() : g_err.c_str();
+}
+
+edac_status edac_set_tiling(edac_ctx *ctx, int tile_cells, int threads)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    if (tile_cells < 1 || tile_cells > EDAC_TILE_MAX_CELLS || (threads != 64 && threads != 128))
+        return fail(ctx, EDAC_E_INVALID, "tiling: 1 <= tile_cells <= 8, threads 64 or 128");
+    ctx->d.tile_tx = tile_cells;
+    ctx->d.tile_tpb = threads;
+    drop_graph(ctx);
+    return EDAC_OK;
+}
+
+edac_status edac_autotune(edac_ctx *ctx, int trials, int *tile_cells, int *threads, double *ms)
+{
+    if (!ctx || trials < 1) return EDAC_E_INVALID;
+    if (!ctx->loaded) return fail(ctx, EDAC_E_STATE, "no particles");
+    if (ctx->failed) return fail(ctx, EDAC_E_STATE, "context in error");
+    if (any_profiling(ctx)) return fail(ctx, EDAC_E_STATE, "autotune with kernel profiling on");
+    // candidate tilings of the mixed pair passes; the fp64 path has none to choose
+    static const int cand[][2] = {{8, 128}, {6, 128}, {4, 64}, {6, 64}, {3, 64}, {2, 64}};
+    const int ncand = ctx->mixed ? (int)(sizeof(cand) / sizeof(cand[0])) : 1;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, EDAC_E_CUDA, "event create");
+    }
+    const int tx0 = ctx->d.tile_tx, tpb0 = ctx->d.tile_tpb;
+    int best = -1;
+    float best_ms = 0.0f;
+    edac_status st = EDAC_OK;
+    for (int c = 0; c < ncand && st == EDAC_OK; ++c) {
+        if (ctx->mixed) {
+            ctx->d.tile_tx = cand[c][0];
+            ctx->d.tile_tpb = cand[c][1];
+        }
+        // an evaluation is idempotent (it recomputes the rates of the current state), so
+        // the trials leave the state as they found it
+        issue_eval(ctx, 0);  // warm-up of this tiling
+        cudaEventRecord(e0, ctx->stream);
+        for (int t = 0; t < trials; ++t) ctx->launches += issue_eval(ctx, 0);
+        cudaEventRecord(e1, ctx->stream);
+        float t_ms = 0.0f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t_ms, e0, e1) != cudaSuccess)
+            st = fail(ctx, EDAC_E_CUDA, "autotune timing");
+        else if (best < 0 || t_ms < best_ms) {
+            best = c;
+            best_ms = t_ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != EDAC_OK) {
+        ctx->d.tile_tx = tx0;
+        ctx->d.tile_tpb = tpb0;
+        return st;
+    }
+    if (ctx->mixed) {
+        ctx->d.tile_tx = cand[best][0];
+        ctx->d.tile_tpb = cand[best][1];
+    }
+    ctx->launches += issue_eval(ctx, 0);  // the rates of the state under the chosen tiling
+    drop_graph(ctx);
+    if (tile_cells) *tile_cells = ctx->d.tile_tx;
+    if (threads) *threads = ctx->d.tile_tpb;
+    if (ms) *ms = (double)best_ms / (double)trials;
+    CK(cudaGetLastError());
+    return check_device(ctx);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------ batches
+struct edac_batch {
+    std::vector<edac_ctx *> ctx;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> ev;  // [0] fork, [1..n] joins, [n+1] done
+    std::vector<int> kper;        // kernels per step of each member
+    int kernels = 0;
+};
+
+namespace {
+
+void batch_free(edac_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+edac_status edac_batch_create(edac_ctx *const *ctxs, int n, void *cuda_stream, edac_batch **out)
+{
+    if (!out) return fail(nullptr, EDAC_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || n < 1) return fail(nullptr, EDAC_E_INVALID, "no contexts");
+    cudaStream_t ms = (cudaStream_t)cuda_stream;
+    if (!ms) return fail(nullptr, EDAC_E_INVALID, "a batch needs a non-default stream");
+    for (int i = 0; i < n; ++i) {
+        edac_ctx *c = ctxs[i];
+        if (!c) return fail(nullptr, EDAC_E_INVALID, "NULL context in the batch");
+        if (!c->loaded || c->failed) return fail(nullptr, EDAC_E_STATE, "batch member without particles or in error");
+        if (!c->stream || c->stream == ms) return fail(nullptr, EDAC_E_INVALID, "each member needs a non-default stream other than the batch's");
+        if (any_profiling(c)) return fail(nullptr, EDAC_E_STATE, "batch member with kernel profiling on");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) return fail(nullptr, EDAC_E_INVALID, "batch members must be distinct");
+    }
+    edac_batch *b = new edac_batch();
+    b->ctx.assign(ctxs, ctxs + n);
+    b->stream = ms;
+    b->ev.assign((size_t)n + 2, nullptr);
+    for (auto &e : b->ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            batch_free(b);
+            return fail(nullptr, EDAC_E_CUDA, "event create");
+        }
+    // one step of every member, each on its own stream, forked from and joined back to the
+    // batch stream inside one capture: the members' kernels form independent graph branches
+    cudaError_t e = cudaStreamBeginCapture(ms, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev[0], ms);
+    int k = 0;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        edac_ctx *c = b->ctx[i];
+        e = cudaStreamWaitEvent(c->stream, b->ev[0], 0);
+        if (e != cudaSuccess) break;
+        const int ki = issue_step(c);
+        b->kper.push_back(ki);
+        k += ki;
+        e = cudaEventRecord(b->ev[1 + i], c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ms, b->ev[1 + i], 0);
+    }
+    cudaGraph_t gr = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(ms, &gr);
+    if (e == cudaSuccess) e = e2;
+    b->graph = gr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, gr, 0);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return fail(nullptr, EDAC_E_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    }
+    b->kernels = k;
+    *out = b;
+    return EDAC_OK;
+}
+
+edac_status edac_batch_step(edac_batch *b, int nsteps)
+{
+    if (!b || nsteps < 0) return fail(nullptr, EDAC_E_INVALID, "bad batch step arguments");
+    for (edac_ctx *c : b->ctx)
+        if (c->failed) return fail(c, EDAC_E_STATE, "batch member in error");
+    if (nsteps == 0) return EDAC_OK;
+    const int n = (int)b->ctx.size();
+    cudaError_t e = cudaSuccess;
+    // the batch stream waits for work queued on the members' streams (uploads, reads) ...
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(b->ev[1 + i], b->ctx[i]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev[1 + i], 0);
+    }
+    for (int s = 0; s < nsteps && e == cudaSuccess; ++s) e = cudaGraphLaunch(b->exec, b->stream);
+    // ... and the members' later calls wait for the batch
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev[n + 1], b->stream);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->ctx[i]->stream, b->ev[n + 1], 0);
+    if (e != cudaSuccess) return fail(nullptr, EDAC_E_CUDA, std::string("batch step: ") + cudaGetErrorString(e));
+    for (int i = 0; i < n; ++i) b->ctx[i]->launches += (long long)b->kper[i] * nsteps;
+    return EDAC_OK;
+}
+
+edac_status edac_batch_launch_count(edac_batch *b, int64_t *kernels_per_step)
+{
+    if (!b || !kernels_per_step) return EDAC_E_INVALID;
+    *kernels_per_step = b->kernels;
+    return EDAC_OK;
+}
+
+void edac_batch_destroy(edac_batch *b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
 }
 
 void edac_destroy(edac_ctx *ctx)

@@ -347,7 +347,9 @@ struct MixB {
 };
 
 // ------------------------------------------------------------ cell-tiled mixed passes
-// A block owns a row segment of CT_TX cells.  It stages the particles of the 3 x (CT_TX + 2)
+// A block owns a row segment of d.tile_tx (at most CT_TX) cells; its d.tile_tpb threads (at
+// most CT_TPB; both set by edac_set_tiling or the autotuner).  It stages the particles of the
+// 3 x (cells + 2)
 // cells around the segment into shared memory once (positions relative to the tile origin,
 // fields of the pass), then each thread takes one particle of the segment.  Pass A lists
 // the particle's neighbours (itself included) as 16-bit shared-memory indices (phase 1),
@@ -357,9 +359,9 @@ struct MixB {
 // row (pass A) or per 32 candidates (pass B).  A tile whose halo exceeds CT_HMAX particles
 // is processed from global memory instead (same membership test, same pair arithmetic), and
 // a particle with more than 128 candidates repeats the test in pass B.
-constexpr int CT_TX = 8;          // ~104 particles per tile at 13 per cell, for 128 threads
+constexpr int CT_TX = 8;          // most cells of a tile (default: ~104 particles at 13 a cell)
 constexpr int CT_NV = CT_TX + 2;  // cells per staged row (halo included)
-constexpr int CT_TPB = 128;
+constexpr int CT_TPB = 128;       // most threads of a tile block
 constexpr int CT_HMAX = 480;
 
 struct TileHdr {
@@ -404,7 +406,7 @@ __device__ __forceinline__ void tile_setup(const Dev &d, int cx0, int cy, TileHd
 {
     static_assert(3 * CT_NV <= 64, "tile header: at most two cells per lane");
     const int lane = threadIdx.x & 31;
-    const int txe = min(CT_TX, d.g.nx - cx0);  // cells of this segment
+    const int txe = min(d.tile_tx, d.g.nx - cx0);  // cells of this segment
     int a0, n0, a1, n1;
     tile_cell(d, cx0, cy, txe, lane, a0, n0);
     tile_cell(d, cx0, cy, txe, lane + 32, a1, n1);
@@ -446,7 +448,7 @@ __device__ __forceinline__ void tile_stage(const Dev &d, const TileHdr &th, floa
                                            Fetch &&fetch)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int cv = w; cv < 3 * CT_NV; cv += CT_TPB / 32) {
+    for (int cv = w; cv < 3 * CT_NV; cv += blockDim.x >> 5) {
         const int r = cv / CT_NV, v = cv - r * CT_NV;
         const int g0 = th.gstart[r][v];
         if (g0 < 0) continue;
@@ -484,9 +486,9 @@ struct CandRows {
 
 __device__ __forceinline__ int tile_of_block(const Dev &d, int &cx0, int &cy)
 {
-    const int tpr = (d.g.nx + CT_TX - 1) / CT_TX;
+    const int tpr = (d.g.nx + d.tile_tx - 1) / d.tile_tx;
     cy = blockIdx.x / tpr;
-    cx0 = (blockIdx.x - cy * tpr) * CT_TX;
+    cx0 = (blockIdx.x - cy * tpr) * d.tile_tx;
     return cy < d.g.ny;
 }
 
@@ -584,7 +586,7 @@ __global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled(Dev d)
     if (fits) tile_stage(d, th, spos, sgj, [&](int t, int, const float4 &pj) { smass[t] = pj.z; });
     __syncthreads();
     const float a2 = d.ph.a2f;
-    for (int ii = threadIdx.x; ii < th.ni; ii += CT_TPB) {
+    for (int ii = threadIdx.x; ii < th.ni; ii += blockDim.x) {
         const int k = th.i0 + ii;
         const float4 pk = d.P[k];
         const double2 xy = d.XY[k];
@@ -736,7 +738,7 @@ __global__ void __launch_bounds__(CT_TPB) k_pass_b_tiled(Dev d)
             stg[t] = d.stag[j];
         });
     __syncthreads();
-    for (int ii = threadIdx.x; ii < th.ni; ii += CT_TPB) {
+    for (int ii = threadIdx.x; ii < th.ni; ii += blockDim.x) {
         const int t = d.stag[th.i0 + ii] & 0x7f;
         if (t == FLUID || t == INLET)
             pass_b_particle<false>(d, th, fits, cy, cx0, ii, spos, sq, sb, stg, sgj);
@@ -1258,11 +1260,11 @@ int grid_for(int n, int tpb)
 
 }  // namespace
 
-int tiles(const Dev &d) { return d.g.ny * ((d.g.nx + CT_TX - 1) / CT_TX); }
+int tiles(const Dev &d) { return d.g.ny * ((d.g.nx + d.tile_tx - 1) / d.tile_tx); }
 
 int launch_pass_a(const Dev &d, cudaStream_t s, int mixed)
 {
-    if (mixed) k_pass_a_tiled<<<tiles(d), CT_TPB, 0, s>>>(d);
+    if (mixed) k_pass_a_tiled<<<tiles(d), d.tile_tpb, 0, s>>>(d);
     else k_pass_a64<<<grid_for(d.cap, TPB), TPB, 0, s>>>(d);
     return 1;
 }
@@ -1283,7 +1285,7 @@ int launch_boundary(const Dev &d, cudaStream_t s, int mixed, int end_of_step)
 
 int launch_pass_b(const Dev &d, cudaStream_t s, int mixed)
 {
-    if (mixed) k_pass_b_tiled<<<tiles(d), CT_TPB, 0, s>>>(d);
+    if (mixed) k_pass_b_tiled<<<tiles(d), d.tile_tpb, 0, s>>>(d);
     else k_pass_b64<<<grid_for(d.cap, TPB), TPB, 0, s>>>(d);
     return 1;
 }

@@ -437,3 +437,69 @@ def test_cylinder_re20_drag_matches_table_hybridconv():
     assert "error" not in out, out
     assert abs(out["cd_mean"] - cd_ref) < 0.05 * cd_ref, out
     assert abs(out["cl_mean"]) < 0.02, out
+
+
+# ------------------------------------------------------------ batches and tiling (NEXT-2)
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_steps_equal_members_stepped_alone(prec):
+    """A batch (one graph launch per step over all members) gives bitwise the fields and
+    histories of each member stepped on its own."""
+    chans = cases.batch_channels(n=4, seed=3, n_min=2000, n_max=5000)
+    alone = [binding.Solver(c, precision=prec) for c in chans]
+    mem = [binding.Solver(c, precision=prec) for c in chans]
+    if prec == "mixed":
+        for s, (tx, tpb) in zip(mem + alone, [(8, 128), (4, 64), (6, 128), (2, 64)] * 2):
+            s.set_tiling(tx, tpb)
+    b = binding.Batch(mem)
+    assert b.kernels_per_step() > 0
+    b.step(25)
+    b.step(15)
+    for s in alone:
+        s.step(40)
+    for s, a in zip(mem, alone):
+        g = s.state(("x", "y", "u", "v", "p", "rho"))
+        r = a.state(("x", "y", "u", "v", "p", "rho"))
+        for k in g:
+            np.testing.assert_array_equal(g[k], r[k], err_msg=k)
+        hs, ha = s.history(), a.history()
+        for k in hs:
+            np.testing.assert_array_equal(hs[k], ha[k], err_msg=k)
+    b.close()
+    for s in mem + alone:
+        s.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("tiling", [(2, 64), (4, 64), (6, 128), (3, 64)])
+@pytest.mark.parametrize("name", ["random_open", "cylinder_coarse", "channel"])
+def test_tilings_match_oracle(tiling, name):
+    """Every tiling of the mixed pair passes stays within the mixed tolerance of the oracle,
+    with the neighbour counts exact."""
+    c = _small_cases()[name]()
+    ref = oracle.OracleSim(c)
+    s = binding.Solver(c, precision="mixed")
+    s.set_tiling(*tiling)
+    s.evaluate()
+    compare_eval(s, ref, "mixed")
+    s.close()
+
+
+@pytest.mark.gpu
+def test_autotune_leaves_the_state_unchanged():
+    c = cases.batch_channels(n=1, seed=5, n_min=20000, n_max=20000)[0]
+    s = binding.Solver(c, precision="mixed")
+    s.step(10)
+    before = s.state(("x", "y", "u", "v", "p", "rho"))
+    tx, tpb, ms = s.autotune(trials=2)
+    assert 1 <= tx <= 8 and tpb in (64, 128) and ms > 0.0
+    after = s.state(("x", "y", "u", "v", "p", "rho"))
+    for k in ("x", "y", "u", "v"):
+        np.testing.assert_array_equal(before[k], after[k], err_msg=k)
+    # density, and the pressures projected on inlet and walls from it, are recomputed under
+    # the chosen tiling: equal up to the order of the fp32 sums
+    assert _rel_err(after["rho"], before["rho"], 1.0) < 1e-6
+    assert _rel_err(after["p"], before["p"], 0.5) < 1e-5
+    s.step(5)  # the chosen tiling runs
+    assert s.count() > 0
+    s.close()
