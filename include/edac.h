@@ -114,6 +114,26 @@ edac_status edac_create(const edac_params *params, void *d_workspace, size_t byt
 edac_status edac_set_inlet(edac_ctx *ctx, double x_in, int n_layers, int n_modes,
                            const double *h_modes, double y0, double H);
 
+/* Inlet velocity in time (the outlet test problems of Sec. 4; default: the steady
+ * modes of edac_set_inlet).  With t the time of the state (steps done x dt; an
+ * inlet particle takes the value at the end of each integrator stage, a new one
+ * the value at the end of the step), y0 and H those of edac_set_inlet:
+ *   EDAC_INLET_MODES  (nprm 0): the steady u(y) of edac_set_inlet, v = 0;
+ *   EDAC_INLET_PULSE  (nprm 4, prm = A, t0, t1, delta; Eq. velfunc2, read with a
+ *     decaying exponent): u = U + A cos(pi (y - y0)/12) exp(-(t - t0)^2/delta)
+ *     for t0 < t < t1, else U; v = 0;
+ *   EDAC_INLET_RAMP   (nprm 1, prm = T; Sec. 4.3): u = U min(t/T, 1), v = 0;
+ *   EDAC_INLET_VORTEX (nprm 4, prm = G, c, d0, y_c; Eqs. vortex, vortexx): a
+ *     vortex whose centre starts d0 upstream and moves at U: x_r = U (d0 - t),
+ *     y_r = y - y_c, u = U + G y_r/(x_r^2 + y_r^2 + c), v = -G x_r/(...).
+ * Inlet particles move in x only, with u.  EDAC_E_INVALID for a bad kind,
+ * parameter count or range (delta, T, c > 0, t1 > t0).  Drops the step graph. */
+#define EDAC_INLET_MODES 0
+#define EDAC_INLET_PULSE 1
+#define EDAC_INLET_RAMP 2
+#define EDAC_INLET_VORTEX 3
+edac_status edac_set_inlet_transient(edac_ctx *ctx, int kind, int nprm, const double *prm);
+
 /* Outlet zone: outlet particles sit in [x_out, x_out + n_layers dx) and move in x
  * only; a fluid particle past x_out becomes an outlet particle, one past
  * x_out + n_layers dx is deleted.  kind selects the treatment of Sec. 3:
@@ -135,6 +155,11 @@ edac_status edac_set_inlet(edac_ctx *ctx, double x_in, int n_layers, int n_modes
 #define EDAC_OUTLET_MOD_DONOTHING 2
 #define EDAC_OUTLET_CHARACTERISTIC 3
 #define EDAC_OUTLET_MIRROR 4
+
+/* Reference state (u_ref, p_ref) of EDAC_OUTLET_CHARACTERISTIC (Sec. 3.3): the
+ * fluid's J2 = rho0 c (u - u_ref) + (p - p_ref), the outlet's u = u_ref +
+ * J2/(2 rho0 c), p = p_ref + J2/2.  Default (U, 0). */
+edac_status edac_set_outlet_reference(edac_ctx *ctx, double u_ref, double p_ref);
 edac_status edac_set_outlet(edac_ctx *ctx, double x_out, int n_layers, int kind, int n_avg,
                             double i_thresh);
 
@@ -296,6 +321,16 @@ edac_status edac_batch_launch_count(edac_batch *batch, int64_t *kernels_per_step
 
 /* Release the batch (synchronises its stream); the members stay valid. */
 void edac_batch_destroy(edac_batch *batch);
+
+/* Probes (the measurement points of Sec. 4's test problems): at n points (1..
+ * EDAC_MAX_PROBES, host arrays h_x, h_y) the Shepard averages sum f W / sum W of
+ * the fluid p, u, v over the fluid particles within 3h of the point (the exact
+ * membership test of the passes), in fp64 on both paths, and the fluid count:
+ * h_out[4 i + 0..3] = (p, u, v, count).  All weights zero: the plain means;
+ * no fluid in reach: zeros.  Uses the state after the last step (tags after
+ * recycling).  Synchronises the stream. */
+#define EDAC_MAX_PROBES 8
+edac_status edac_probe(edac_ctx *ctx, int n, const double *h_x, const double *h_y, double *h_out);
 
 /* Text of the last error of this context (valid until the next call); with
  * ctx = NULL, the last error of a context-less call (edac_workspace_bytes,

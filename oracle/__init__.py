@@ -54,8 +54,10 @@ class CParams(C.Structure):
         ("has_inlet", C.c_int), ("x_in", C.c_double), ("n_in_layers", C.c_int),
         ("n_modes", C.c_int), ("modes", C.c_double * MAX_MODES),
         ("inlet_y0", C.c_double), ("inlet_h", C.c_double),
+        ("inlet_kind", C.c_int), ("inlet_prm", C.c_double * 4),
         ("has_outlet", C.c_int), ("x_out", C.c_double), ("n_out_layers", C.c_int),
         ("n_avg", C.c_int), ("i_thresh", C.c_double), ("outlet_kind", C.c_int),
+        ("moc_u_ref", C.c_double), ("moc_p_ref", C.c_double),
         ("wall_slip", C.c_int * 2), ("wall_u", C.c_double * 2), ("wall_v", C.c_double * 2),
         ("wall_drag", C.c_int * 2), ("drag_length", C.c_double),
         ("neighbor_mode", C.c_int), ("mirror_sign", C.c_int),
@@ -78,7 +80,7 @@ class CState(C.Structure):
         ("ubar", _DP), ("vbar", _DP), ("pbar", _DP), ("J2", _DP),
         ("J2p", _DP), ("advp", _DP), ("redp", _IP),
         ("x0", _DP), ("y0", _DP), ("u0", _DP), ("v0", _DP), ("p0", _DP),
-        ("next_id", C.c_uint64), ("error", C.c_int),
+        ("next_id", C.c_uint64), ("error", C.c_int), ("t", C.c_double), ("nstep", C.c_int),
     ]
 
 
@@ -114,6 +116,8 @@ def lib():
             L.orc_mirror_points.restype = C.c_int
             L.orc_outlet_mirror.argtypes = [C.POINTER(CParams), C.POINTER(CState)]
             L.orc_outlet_mirror.restype = C.c_int
+            L.orc_probe.argtypes = [C.POINTER(CParams), C.POINTER(CState), C.c_int, _DP, _DP, _DP]
+            L.orc_probe.restype = C.c_int
             assert L.orc_sizeof_params() == C.sizeof(CParams), "orc_params layout mismatch"
             assert L.orc_sizeof_state() == C.sizeof(CState), "orc_state layout mismatch"
             assert L.orc_sizeof_hist() == C.sizeof(CHist), "orc_hist layout mismatch"
@@ -153,6 +157,13 @@ def make_params(p, neighbor_mode: int = 0, mirror_sign: int = -1) -> CParams:
         cp.modes[k] = float(a)
     cp.inlet_y0 = float(getattr(p, "inlet_y0", 0.0))
     cp.inlet_h = float(getattr(p, "inlet_h", p.y_max - p.y_min))
+    cp.inlet_kind = int(getattr(p, "inlet_kind", 0))
+    prm = tuple(getattr(p, "inlet_prm", ()))
+    assert len(prm) <= 4
+    for k, v in enumerate(prm):
+        cp.inlet_prm[k] = float(v)
+    ref = tuple(getattr(p, "moc_ref", ())) or (p.U, 0.0)
+    cp.moc_u_ref, cp.moc_p_ref = float(ref[0]), float(ref[1])
     for k in range(2):
         cp.wall_slip[k] = int(p.wall_slip[k])
         cp.wall_u[k] = float(p.wall_u[k])
@@ -253,6 +264,19 @@ class OracleSim:
                                 qy.ctypes.data_as(_DP), pk.ctypes.data_as(_DP),
                                 gx.ctypes.data_as(_DP), gy.ctypes.data_as(_DP))
         return pk, gx, gy
+
+    def probe(self, qx, qy):
+        """Shepard (p, u, v) of the fluid and the fluid count at points: array (n, 4)."""
+        qx = np.ascontiguousarray(qx, dtype=np.float64)
+        qy = np.ascontiguousarray(qy, dtype=np.float64)
+        out = np.zeros((len(qx), 4))
+        lib().orc_probe(C.byref(self.cp), C.byref(self.st), len(qx), qx.ctypes.data_as(_DP),
+                        qy.ctypes.data_as(_DP), out.ctypes.data_as(_DP))
+        return out
+
+    @property
+    def t(self) -> float:
+        return float(self.st.t)
 
     def outlet_mirror(self):
         """Run the mirrored outlet update (Sec. 3.2 at the outlet) on the current fields."""

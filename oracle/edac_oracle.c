@@ -37,6 +37,12 @@
 #define ORC_OUT_MOD_DONOTHING 2
 #define ORC_OUT_CHARACTERISTIC 3
 #define ORC_OUT_MIRROR 4
+/* inlet velocity in time: steady modes; the 2D pulse (Sec. 4.2), ramp (Sec. 4.3) and
+ * passing vortex (Sec. 4.4) of the outlet test problems */
+#define ORC_IN_MODES 0
+#define ORC_IN_PULSE 1
+#define ORC_IN_RAMP 2
+#define ORC_IN_VORTEX 3
 #define ORC_MAX_MODES 16
 
 typedef struct {
@@ -50,12 +56,15 @@ typedef struct {
     int n_modes;
     double modes[ORC_MAX_MODES];
     double inlet_y0, inlet_h;
+    int inlet_kind;        /* ORC_IN_*: the inlet velocity in time (Sec. 4 test problems) */
+    double inlet_prm[4];   /* its parameters (see inlet_velocity) */
     int has_outlet;
     double x_out;
     int n_out_layers;
     int n_avg;
     double i_thresh;
     int outlet_kind; /* ORC_OUT_*: the outlet treatment of Sec. 3 */
+    double moc_u_ref, moc_p_ref; /* reference state of the characteristic outlet */
     int wall_slip[2];
     double wall_u[2], wall_v[2];
     int wall_drag[2];
@@ -84,6 +93,8 @@ typedef struct {
     double *x0, *y0, *u0, *v0, *p0;
     uint64_t next_id;
     int error; /* 1: capacity exceeded, 2: particle outside the domain box */
+    double t;  /* time of the state: nstep dt */
+    int nstep; /* steps done */
 } orc_state;
 
 /* one history record per step */
@@ -318,12 +329,36 @@ static int in_box(const orc_params *P, const orc_state *S)
 }
 
 /* Inlet velocity profile u(y) = U + sum_k a_k sin(k pi (y - y0)/H). */
-static double inlet_u(const orc_params *P, double y)
+/* Inlet velocity (u, v) at height y and time t (Sec. 3 and the test problems of Sec. 4):
+ *   modes:  u = U + sum_k a_k sin(k pi (y - y0) / H), v = 0 (steady);
+ *   pulse:  u = U + A cos(pi (y - y0) / 12) exp(-(t - t0)^2 / delta) for t0 < t < t1, else U,
+ *           v = 0, prm = (A, t0, t1, delta) (Eq. velfunc2, read with a negative exponent);
+ *   ramp:   u = U min(t / T, 1), v = 0, prm = (T) (Sec. 4.3);
+ *   vortex: with x_r = U (d0 - t) the distance of the vortex centre, which starts d0 upstream
+ *           and moves at U, y_r = y - y_c and r^2 = x_r^2 + y_r^2:
+ *           u = U + G y_r / (r^2 + c), v = -G x_r / (r^2 + c), prm = (G, c, d0, y_c)
+ *           (Eqs. vortex, vortexx). */
+static void inlet_velocity(const orc_params *P, double y, double t, double *u, double *v)
 {
-    double u = P->U;
-    for (int k = 0; k < P->n_modes; k++)
-        u += P->modes[k] * sin((double)(k + 1) * M_PI * (y - P->inlet_y0) / P->inlet_h);
-    return u;
+    const double *q = P->inlet_prm;
+    *v = 0.0;
+    if (P->inlet_kind == ORC_IN_PULSE) {
+        *u = P->U;
+        if (t > q[1] && t < q[2])
+            *u += q[0] * cos(M_PI * (y - P->inlet_y0) / 12.0) * exp(-(t - q[1]) * (t - q[1]) / q[3]);
+    } else if (P->inlet_kind == ORC_IN_RAMP) {
+        *u = P->U * (t < q[0] ? t / q[0] : 1.0);
+    } else if (P->inlet_kind == ORC_IN_VORTEX) {
+        double xr = P->U * (q[2] - t), yr = y - q[3];
+        double den = xr * xr + yr * yr + q[1];
+        *u = P->U + q[0] * yr / den;
+        *v = -q[0] * xr / den;
+    } else {
+        double uu = P->U;
+        for (int k = 0; k < P->n_modes; k++)
+            uu += P->modes[k] * sin((double)(k + 1) * M_PI * (y - P->inlet_y0) / P->inlet_h);
+        *u = uu;
+    }
 }
 
 static int is_wall(int t) { return t == ORC_WALL || t == ORC_SLIPWALL; }
@@ -630,7 +665,8 @@ static void pass_b(const orc_params *P, orc_state *S, const nlist *L)
             double uij = S->u[i] - S->u[j], vij = S->v[i] - S->v[j];
             double gdotr = gx * dxs + gy * dys;
             double etai = rhoi * P->nu, etaj = rhoj * P->nu;
-            double etil = 2.0 * etai * etaj / (etai + etaj);
+            /* the harmonic mean of two zero viscosities (inviscid runs) is zero */
+            double etil = etai + etaj > 0.0 ? 2.0 * etai * etaj / (etai + etaj) : 0.0;
             double visc = etil * gdotr / (r2 + eh2);
             if (do_solid) {
                 sx += cij * (-ptil * gx + visc * uij);
@@ -644,7 +680,7 @@ static void pass_b(const orc_params *P, orc_state *S, const nlist *L)
             sx += cij * (-ptil * gx + 0.5 * (Aix + Ajx) + visc * uij);
             sy += cij * (-ptil * gy + 0.5 * (Aiy + Ajy) + visc * vij);
             double ei = rhoi * nu_edac, ej = rhoj * nu_edac;
-            double etile = 2.0 * ei * ej / (ei + ej);
+            double etile = ei + ej > 0.0 ? 2.0 * ei * ej / (ei + ej) : 0.0;
             sp_rate += (S->m[j] * rhoi / rhoj) * c2 * (uij * gx + vij * gy)
                      + (cij / mi) * etile * (S->p[i] - S->p[j]) * gdotr / (r2 + eh2);
             bx += cij * gx;
@@ -721,8 +757,8 @@ static void ring_update(const orc_params *P, orc_state *S)
     for (int i = 0; i < S->n; i++) {
         if (S->tag[i] != ORC_FLUID) continue;
         if (P->outlet_kind == ORC_OUT_CHARACTERISTIC) {
-            /* Sec. 3.3 alone: the reference state is the free stream (U, 0) */
-            S->J2[i] = rc * (S->u[i] - P->U) + S->p[i];
+            /* Sec. 3.3 alone: J2 against the fixed reference state (u_ref, p_ref) */
+            S->J2[i] = rc * (S->u[i] - P->moc_u_ref) + (S->p[i] - P->moc_p_ref);
             continue;
         }
         if (P->outlet_kind != ORC_OUT_HYBRID) continue;
@@ -766,8 +802,9 @@ static void ring_update(const orc_params *P, orc_state *S)
  * outlet and fluid particles move together.
  *
  * Method of characteristics (Sec. 3.3): the same red/blue extrapolation of J2, with
- * the free stream (U, p = 0) as the fixed reference state instead of the time
- * averages: p = J2/2, u = U + J2/(2 rho0 c); the transverse velocity keeps the
+ * a fixed reference state (u_ref, p_ref) instead of the time averages (the free
+ * stream (U, 0) unless set; Sec. 4 fixes (1 m/s, 1 Pa) for its test problems):
+ * p = p_ref + J2/2, u = u_ref + J2/(2 rho0 c); the transverse velocity keeps the
  * value frozen at the crossing.  A blue particle without red neighbours advects
  * with its own u.
  *
@@ -881,8 +918,8 @@ static void outlet_update(const orc_params *P, orc_state *S, const nlist *L)
         double pa = 0.5 * J2, ua = J2 / (2.0 * rc);
         double u, p, adv;
         if (kind == ORC_OUT_CHARACTERISTIC) {
-            u = P->U + ua;
-            p = pa;
+            u = P->moc_u_ref + ua;
+            p = P->moc_p_ref + pa;
             adv = red ? u : (mr > 0 ? blue_adv : u);
         } else {
             u = S->ubar[o] + ua;
@@ -993,13 +1030,14 @@ static void recycle(const orc_params *P, orc_state *S, orc_hist *H)
             break;
         }
         int i = S->n++;
-        double uin = inlet_u(P, ny_[k]);
+        double uin, vin;
+        inlet_velocity(P, ny_[k], S->t, &uin, &vin);
         S->x[i] = nx_[k];
         S->y[i] = ny_[k];
         S->u[i] = uin;
-        S->v[i] = 0.0;
+        S->v[i] = vin;
         S->ut[i] = uin;
-        S->vt[i] = 0.0;
+        S->vt[i] = vin;
         S->p[i] = np_[k];
         S->m[i] = nm_[k];
         S->tag[i] = ORC_INLET;
@@ -1071,11 +1109,12 @@ static void stage(const orc_params *P, orc_state *S, double tau)
             S->y[i] = wrap(S->y0[i] + tau * S->vt[i], P->periodic_y, P->y_min, P->y_max);
             S->p[i] = S->p0[i] + tau * S->ap[i];
         } else if (t == ORC_INLET) {
-            double uin = inlet_u(P, S->y0[i]);
+            double uin, vin;
+            inlet_velocity(P, S->y0[i], S->t + tau, &uin, &vin);
             S->u[i] = uin;
-            S->v[i] = 0.0;
+            S->v[i] = vin;
             S->ut[i] = uin;
-            S->vt[i] = 0.0;
+            S->vt[i] = vin;
             S->x[i] = S->x0[i] + tau * uin;
         } else if (t == ORC_OUTLET) {
             S->x[i] = S->x0[i] + tau * S->advp[i];
@@ -1088,6 +1127,8 @@ static void stage(const orc_params *P, orc_state *S, double tau)
 int orc_init(const orc_params *P, orc_state *S)
 {
     S->error = 0;
+    S->t = 0.0;
+    S->nstep = 0;
     for (int i = 0; i < S->n; i++) {
         S->ut[i] = S->u[i];
         S->vt[i] = S->v[i];
@@ -1130,6 +1171,8 @@ int orc_step(const orc_params *P, orc_state *S, int nsteps, orc_hist *hist)
         }
         if (P->has_outlet) outlet_update(P, S, &L);
         nlist_free(&L);
+        S->nstep += 1;
+        S->t = (double)S->nstep * P->dt;
         recycle(P, S, &H);
         if (hist) hist[s] = H;
         if (S->error) return S->error;
@@ -1171,6 +1214,47 @@ int orc_mirror_points(const orc_params *P, const orc_state *S, int nq, const dou
 int orc_outlet_mirror(const orc_params *P, orc_state *S)
 {
     outlet_mirror(P, S);
+    return 0;
+}
+
+/* Probes (the measurement points of the Sec. 4 test problems): at each point the
+ * Shepard average of the fluid p, u, v over fluid particles within 3h (all weights
+ * zero: the plain mean; none: zeros) and their count; out[4 t + (0..3)]. */
+int orc_probe(const orc_params *P, const orc_state *S, int nq, const double *qx,
+              const double *qy, double *out)
+{
+    const double h = h_of(P), rc2 = rc2_of(P);
+    for (int t = 0; t < nq; t++) {
+        double sw = 0.0, sp = 0.0, su = 0.0, sv = 0.0, mp = 0.0, mu = 0.0, mv = 0.0, dx, dy;
+        int nf = 0;
+        for (int j = 0; j < S->n; j++) {
+            if (S->tag[j] != ORC_FLUID) continue;
+            double r2 = sep(P, qx[t], qy[t], S->x[j], S->y[j], &dx, &dy);
+            if (!(r2 < rc2)) continue;
+            double w = orc_W(sqrt(r2), h);
+            sw += w;
+            sp += w * S->p[j];
+            su += w * S->u[j];
+            sv += w * S->v[j];
+            mp += S->p[j];
+            mu += S->u[j];
+            mv += S->v[j];
+            nf++;
+        }
+        double *o = out + 4 * t;
+        if (nf == 0) {
+            o[0] = o[1] = o[2] = 0.0;
+        } else if (sw > 0.0) {
+            o[0] = sp / sw;
+            o[1] = su / sw;
+            o[2] = sv / sw;
+        } else {
+            o[0] = mp / (double)nf;
+            o[1] = mu / (double)nf;
+            o[2] = mv / (double)nf;
+        }
+        o[3] = (double)nf;
+    }
     return 0;
 }
 

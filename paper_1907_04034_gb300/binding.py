@@ -42,6 +42,7 @@ EXPORTS = ("edac_workspace_bytes", "edac_create", "edac_set_inlet", "edac_set_ou
            "edac_read_neighbors", "edac_profile", "edac_read_profile", "edac_launch_count",
            "edac_density_static", "edac_fma_peak", "edac_set_tiling", "edac_autotune",
            "edac_batch_create", "edac_batch_step", "edac_batch_launch_count", "edac_batch_destroy",
+           "edac_set_inlet_transient", "edac_set_outlet_reference", "edac_probe",
            "edac_last_error", "edac_destroy")
 
 
@@ -256,9 +257,15 @@ class Solver:
             modes = np.ascontiguousarray(p.inlet_modes, dtype=np.float64)
             self._call("edac_set_inlet", p.x_in, p.n_in_layers, len(modes),
                        _ptr(modes, C.c_double) if len(modes) else None, p.inlet_y0, p.inlet_h)
+        if p.has_inlet and int(getattr(p, "inlet_kind", 0)) != 0:
+            prm = np.ascontiguousarray(p.inlet_prm, dtype=np.float64)
+            self._call("edac_set_inlet_transient", int(p.inlet_kind), len(prm),
+                       _ptr(prm, C.c_double) if len(prm) else None)
         if p.has_outlet:
             self._call("edac_set_outlet", p.x_out, p.n_out_layers, int(p.outlet_kind), p.n_avg,
                        p.i_thresh)
+            ref = tuple(getattr(p, "moc_ref", ())) or (p.U, 0.0)
+            self._call("edac_set_outlet_reference", float(ref[0]), float(ref[1]))
         for tagv, w in ((_cases.WALL, 0), (_cases.SLIPWALL, 1)):
             self._call("edac_set_wall", tagv, int(p.wall_slip[w]), float(p.wall_u[w]),
                        float(p.wall_v[w]), int(p.wall_drag[w]))
@@ -351,6 +358,16 @@ class Solver:
         ln = C.c_int64(0)
         self._call("edac_read_profile", KERNELS[kernel], C.byref(ms), C.byref(ln), int(reset))
         return ms.value, ln.value
+
+    def probe(self, xs, ys) -> np.ndarray:
+        """Shepard (p, u, v) of the fluid and the fluid count at points (edac_probe):
+        array (n, 4)."""
+        xs = np.ascontiguousarray(xs, dtype=np.float64)
+        ys = np.ascontiguousarray(ys, dtype=np.float64)
+        out = np.zeros((len(xs), 4))
+        self._call("edac_probe", len(xs), _ptr(xs, C.c_double), _ptr(ys, C.c_double),
+                   _ptr(out, C.c_double))
+        return out
 
     def set_tiling(self, tile_cells: int, threads: int):
         """Tiling of the mixed pair passes (edac_set_tiling)."""

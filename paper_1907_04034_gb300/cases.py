@@ -60,6 +60,10 @@ class Params:
     inlet_modes: tuple = ()    # a_k of u(y) = U + sum a_k sin(k pi (y - inlet_y0) / inlet_h)
     inlet_y0: float = 0.0
     inlet_h: float = 1.0
+    # inlet velocity in time: 0 steady modes, 1 2D pulse (A, t0, t1, delta), 2 ramp (T),
+    # 3 passing vortex (Gamma, core, d0, y_c) of the Sec. 4 test problems
+    inlet_kind: int = 0
+    inlet_prm: tuple = ()
     # outlet (hybrid)
     has_outlet: int = 0
     x_out: float = 1.0
@@ -69,6 +73,7 @@ class Params:
     # outlet treatment: 0 hybrid (Sec. 3.4), 1 do-nothing (Sec. 3.1), 2 modified do-nothing
     # (Sec. 3.1.1), 3 method of characteristics (Sec. 3.3), 4 mirroring (Sec. 3.2)
     outlet_kind: int = 0
+    moc_ref: tuple = ()        # (u_ref, p_ref) of the characteristic outlet; () = (U, 0)
     # walls: per wall tag (WALL, SLIPWALL): slip flag, wall velocity, counted in drag
     wall_slip: tuple = (0, 1)
     wall_u: tuple = (0.0, 0.0)
@@ -110,7 +115,7 @@ class Case:
 def default_dt(dx: float, hdx: float, cs: float, U: float, nu: float) -> float:
     """Time step recipe of the channel workload: min(0.25 h/(c+U), 0.125 h^2/nu)."""
     h = hdx * dx
-    return min(0.25 * h / (cs + U), 0.125 * h * h / nu)
+    return min(0.25 * h / (cs + U), 0.125 * h * h / nu if nu > 0 else math.inf)
 
 
 def _lattice(x0: float, nx: int, y0: float, ny: int, dx: float):
@@ -160,6 +165,58 @@ def channel(dx: float = 0.02, nu: float = 0.01, seed: int = 0, jitter: float = 0
                   capacity_extra=4 * ny + 64)
     c.u[:] = U
     c.p[:] = pulse_amp * np.exp(-((c.x - pulse_xy[0]) ** 2 + (c.y - pulse_xy[1]) ** 2) / pulse_w)
+    return c
+
+
+def outlet_problem(problem: str = "pulse2d", outlet: int = 0, long: bool = False,
+                   dx: float = 0.1, t_end: float = 3.0, probe_d: float = 1.7,
+                   delta: float = 1e-3) -> Case:
+    """The outlet test problems of Sec. 4: a channel of length 2 and width 2 (4 for the
+    vortex) between inviscid (slip) walls, inviscid fluid, U = 1, c = 10 U, six layers of
+    inlet, outlet and wall particles, spacing 0.1, the probe at d = 1.7 on the centre line.
+    The long-domain reference has length d + c t_end, so that nothing the outlet reflects
+    reaches the probe before t_end.
+      pulse2d (Sec. 4.2): fluid at u = U; the inlet adds A cos(pi y / 12) exp(-(t-1)^2/delta)
+        for 1 < t < 1.1, A = 0.5 (delta is not given; 1e-3 is the reading);
+      ramp (Sec. 4.3): fluid at rest; the inlet ramps from 0 to U over 1 s;
+      vortex (Sec. 4.4): fluid at u = U; the inlet carries a vortex of strength 0.1 and core
+        0.2 whose centre starts 1 upstream of the inlet and moves at U.
+    The characteristic outlet's reference is (1 m/s, 1 Pa) at rho = 1000 (Sec. 4.1), i.e.
+    (U, 0.001) at rho0 = 1."""
+    U, cs, n_lay = 1.0, 10.0, 6
+    W = 4.0 if problem == "vortex" else 2.0
+    L = probe_d + cs * t_end if long else 2.0
+    hdx = 1.2
+    rc = 3.0 * hdx * dx
+    nx, ny = int(round(L / dx)), int(round(W / dx))
+    if problem == "pulse2d":
+        kind, prm, u0 = 1, (0.5, 1.0, 1.1, delta), U
+    elif problem == "ramp":
+        kind, prm, u0 = 2, (1.0,), 0.0
+    elif problem == "vortex":
+        kind, prm, u0 = 3, (0.1, 0.2, 1.0, 0.5 * W), U
+    else:
+        raise ValueError(f"unknown problem {problem!r}")
+    params = Params(x_min=-n_lay * dx - rc, x_max=L + n_lay * dx + rc,
+                    y_min=-n_lay * dx - rc, y_max=W + n_lay * dx + rc, periodic_y=0,
+                    dx=dx, hdx=hdx, rho0=1.0, U=U, nu=0.0, cs=cs, pb=cs * cs,
+                    dt=default_dt(dx, hdx, cs, U, 0.0),
+                    has_inlet=1, x_in=0.0, n_in_layers=n_lay, inlet_y0=0.0, inlet_h=W,
+                    inlet_kind=kind, inlet_prm=prm,
+                    has_outlet=1, x_out=L, n_out_layers=n_lay, outlet_kind=int(outlet),
+                    moc_ref=(1.0, 1e-3), wall_slip=(0, 1), wall_drag=(0, 0))
+    fx, fy = _lattice(0.0, nx, 0.0, ny, dx)
+    ix, iy = _lattice(-n_lay * dx, n_lay, 0.0, ny, dx)
+    ox, oy = _lattice(L, n_lay, 0.0, ny, dx)
+    nxw = 2 * n_lay + nx
+    bx, by = _lattice(-n_lay * dx, nxw, -n_lay * dx, n_lay, dx)
+    tx, ty = _lattice(-n_lay * dx, nxw, W, n_lay, dx)
+    c = _assemble(problem + ("_long" if long else ""), params,
+                  [(fx, fy, FLUID), (ix, iy, INLET), (ox, oy, OUTLET),
+                   (np.concatenate([bx, tx]), np.concatenate([by, ty]), SLIPWALL)],
+                  capacity_extra=4 * ny + 64)
+    c.u[:] = np.where(c.tag == SLIPWALL, 0.0, u0)
+    c.p[:] = 0.0
     return c
 
 

@@ -12,6 +12,10 @@
 #include "edac.h"
 #include "edac_internal.cuh"
 
+static_assert(edac::IN_MODES == EDAC_INLET_MODES && edac::IN_PULSE == EDAC_INLET_PULSE &&
+                  edac::IN_RAMP == EDAC_INLET_RAMP && edac::IN_VORTEX == EDAC_INLET_VORTEX &&
+                  edac::PROBE_MAX == EDAC_MAX_PROBES,
+              "inlet kinds and probe limit of the header and the kernels agree");
 static_assert(edac::OUT_HYBRID == EDAC_OUTLET_HYBRID && edac::OUT_DONOTHING == EDAC_OUTLET_DONOTHING &&
                   edac::OUT_MOD_DONOTHING == EDAC_OUTLET_MOD_DONOTHING &&
                   edac::OUT_CHARACTERISTIC == EDAC_OUTLET_CHARACTERISTIC &&
@@ -145,6 +149,10 @@ void make_phys(const edac_params &P, Phys &ph)
     for (int k = 0; k < MAX_MODES; ++k) ph.modes[k] = 0.0;
     ph.has_outlet = 0;
     ph.outlet_kind = OUT_HYBRID;
+    ph.moc_u_ref = P.U;
+    ph.moc_p_ref = 0.0;
+    ph.in_kind = IN_MODES;
+    for (int k = 0; k < 4; ++k) ph.in_prm[k] = 0.0;
     ph.n_avg = 6;
     ph.x_out = 0; ph.L_out = 0;
     const double q = 0.5 * P.rho0 * P.U * P.U;
@@ -237,6 +245,8 @@ size_t layout(Dev &d, const Geo &g, int cap, int max_history, int mixed, char *b
     DARR(drag_slots, int, C);
     DARR(scratch_m, double, LIST_MAX);
     DARR(hist, double, (size_t)max_history * 8);
+    DARR(probe_part, double, (size_t)PROBE_BLK * PROBE_MAX * 8);
+    DARR(probe_out, double, (size_t)PROBE_MAX * 4);
 #undef DARR
     return (off + 255) & ~(size_t)255;
 }
@@ -415,6 +425,57 @@ edac_status edac_set_outlet(edac_ctx *ctx, double x_out, int n_layers, int kind,
     ph.inv_navg = 1.0 / (double)n_avg;
     if (i_thresh >= 0) ph.I_thr = i_thresh;
     drop_graph(ctx);
+    return EDAC_OK;
+}
+
+edac_status edac_set_inlet_transient(edac_ctx *ctx, int kind, int nprm, const double *prm)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    static const int need[4] = {0, 4, 1, 4};
+    if (kind < EDAC_INLET_MODES || kind > EDAC_INLET_VORTEX || nprm != need[kind] || (nprm > 0 && !prm))
+        return fail(ctx, EDAC_E_INVALID, "bad inlet kind or parameter count");
+    for (int k = 0; k < nprm; ++k)
+        if (!is_fin(prm[k])) return fail(ctx, EDAC_E_INVALID, "non-finite inlet parameter");
+    if ((kind == EDAC_INLET_PULSE && !(prm[3] > 0 && prm[2] > prm[1])) ||
+        (kind == EDAC_INLET_RAMP && !(prm[0] > 0)) || (kind == EDAC_INLET_VORTEX && !(prm[1] > 0)))
+        return fail(ctx, EDAC_E_INVALID, "inlet parameters out of range");
+    Phys &ph = ctx->d.ph;
+    ph.in_kind = kind;
+    for (int k = 0; k < 4; ++k) ph.in_prm[k] = k < nprm ? prm[k] : 0.0;
+    drop_graph(ctx);
+    return EDAC_OK;
+}
+
+edac_status edac_set_outlet_reference(edac_ctx *ctx, double u_ref, double p_ref)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    if (!is_fin(u_ref) || !is_fin(p_ref)) return fail(ctx, EDAC_E_INVALID, "non-finite reference");
+    ctx->d.ph.moc_u_ref = u_ref;
+    ctx->d.ph.moc_p_ref = p_ref;
+    drop_graph(ctx);
+    return EDAC_OK;
+}
+
+edac_status edac_probe(edac_ctx *ctx, int n, const double *h_x, const double *h_y, double *h_out)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    if (n < 1 || n > EDAC_MAX_PROBES || !h_x || !h_y || !h_out)
+        return fail(ctx, EDAC_E_INVALID, "1 <= n <= EDAC_MAX_PROBES points and non-NULL arrays");
+    if (!ctx->loaded) return fail(ctx, EDAC_E_STATE, "no particles");
+    edac_status st = check_device(ctx);
+    if (st) return st;
+    ProbePts q;
+    q.n = n;
+    for (int i = 0; i < PROBE_MAX; ++i) {
+        q.x[i] = i < n ? h_x[i] : 0.0;
+        q.y[i] = i < n ? h_y[i] : 0.0;
+        if (i < n && (!is_fin(q.x[i]) || !is_fin(q.y[i]))) return fail(ctx, EDAC_E_INVALID, "non-finite probe point");
+    }
+    ctx->launches += launch_probe(ctx->d, ctx->stream, q);
+    CK(cudaMemcpyAsync(h_out, ctx->d.probe_out, sizeof(double) * 4 * (size_t)n, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaGetLastError());
     return EDAC_OK;
 }
 

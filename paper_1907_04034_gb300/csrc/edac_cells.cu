@@ -283,14 +283,15 @@ __global__ void k_stage(Dev d, double tau)
                 d.ubar[s] = ub; d.vbar[s] = vb; d.pbar[s] = pbv;
                 d.J2[s] = ph.rho0 * ph.cs * (un - ub) + (pn - pbv);
             } else if (CORR && ph.has_outlet && ph.outlet_kind == OUT_CHARACTERISTIC) {
-                // Sec. 3.3 alone: J2 against the free stream (U, p = 0)
-                d.J2[s] = ph.rho0 * ph.cs * (un - ph.U) + pn;
+                // Sec. 3.3 alone: J2 against the fixed reference state (u_ref, p_ref)
+                d.J2[s] = ph.rho0 * ph.cs * (un - ph.moc_u_ref) + (pn - ph.moc_p_ref);
             }
         } else if (t == INLET) {
             double x0;
             if (!CORR) { x0 = d.x[s]; d.x0[s] = x0; } else { x0 = d.x0[s]; }
-            const double uin = inlet_u(ph, d.y[s]);
-            d.u[s] = uin; d.v[s] = 0.0; d.ut[s] = uin; d.vt[s] = 0.0;
+            double uin, vin;  // the inlet velocity at the end of the stage
+            inlet_uv(ph, d.y[s], (double)d.cnt->step * ph.dt + tau, uin, vin);
+            d.u[s] = uin; d.v[s] = vin; d.ut[s] = uin; d.vt[s] = vin;
             d.x[s] = x0 + tau * uin;
         } else if (t == OUTLET) {
             double x0;
@@ -436,10 +437,11 @@ __global__ void __launch_bounds__(1024) k_end_step(Dev d, double *scratch_m)
         const int ps = d.ev_spawn_slot[i];
         const int s = d.free_stack[top1 - 1 - r];
         const double yv = d.y[ps];
-        const double uin = inlet_u(ph, yv);
+        double uin, vin;  // the inlet velocity at the end of the step
+        inlet_uv(ph, yv, (double)(C->step + 1) * ph.dt, uin, vin);
         d.x[s] = d.x[ps] - ph.L_in;
         d.y[s] = yv;
-        d.u[s] = uin; d.v[s] = 0.0; d.ut[s] = uin; d.vt[s] = 0.0;
+        d.u[s] = uin; d.v[s] = vin; d.ut[s] = uin; d.vt[s] = vin;
         d.p[s] = d.p[ps];
         d.m[s] = d.m[ps];
         d.id[s] = id0 + (unsigned long long)r;
@@ -535,6 +537,76 @@ int launch_init(const Dev &d, cudaStream_t s)
 {
     k_init<<<grid_for(d.cap), TPB, 0, s>>>(d);
     return 1;
+}
+
+}  // namespace edac
+
+// ------------------------------------------------------------------------------ probes
+namespace edac {
+namespace {
+
+// Per block and probe: [sum W, sum W p, sum W u, sum W v, sum p, sum u, sum v, count] over
+// the fluid particles within 3h of the probe (exact membership test), over the slot arrays.
+__global__ void __launch_bounds__(256) k_probe_part(Dev d, ProbePts q, double *part)
+{
+    __shared__ double red[8][8];
+    const Geo &g = d.g;
+    const Phys &ph = d.ph;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int t = 0; t < q.n; ++t) {
+        double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.cap; s += gridDim.x * blockDim.x) {
+            if (d.tag[s] != FLUID) continue;
+            double dx, dy;
+            const double r2 = exact_r2(g, q.x[t], q.y[t], d.x[s], d.y[s], dx, dy);
+            if (!(r2 < g.rc2)) continue;
+            const double wv = ph.a2 * quintic_w(sqrt(r2) * ph.inv_h);
+            const double p = d.p[s], u = d.u[s], v = d.v[s];
+            a[0] += wv; a[1] += wv * p; a[2] += wv * u; a[3] += wv * v;
+            a[4] += p; a[5] += u; a[6] += v; a[7] += 1.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            for (int o = 16; o > 0; o >>= 1) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
+        if (lane == 0)
+            for (int i = 0; i < 8; ++i) red[w][i] = a[i];
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            double sum = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) sum += red[k][threadIdx.x];
+            part[((size_t)blockIdx.x * PROBE_MAX + t) * 8 + threadIdx.x] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// Sum the per-block parts in block order and form (p, u, v, count) per probe: the Shepard
+// average, the plain mean when every weight is zero, zeros without fluid.
+__global__ void k_probe_final(ProbePts q, const double *part, int nblk, double *out)
+{
+    const int t = threadIdx.x;
+    if (t >= q.n) return;
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nblk; ++b)
+        for (int i = 0; i < 8; ++i) a[i] += part[((size_t)b * PROBE_MAX + t) * 8 + i];
+    double *o = out + 4 * t;
+    if (a[7] == 0.0) {
+        o[0] = o[1] = o[2] = 0.0;
+    } else if (a[0] > 0.0) {
+        o[0] = a[1] / a[0]; o[1] = a[2] / a[0]; o[2] = a[3] / a[0];
+    } else {
+        o[0] = a[4] / a[7]; o[1] = a[5] / a[7]; o[2] = a[6] / a[7];
+    }
+    o[3] = a[7];
+}
+
+}  // namespace
+
+int launch_probe(const Dev &d, cudaStream_t s, const ProbePts &q)
+{
+    k_probe_part<<<PROBE_BLK, 256, 0, s>>>(d, q, d.probe_part);
+    k_probe_final<<<1, 32, 0, s>>>(q, d.probe_part, PROBE_BLK, d.probe_out);
+    return 2;
 }
 
 }  // namespace edac

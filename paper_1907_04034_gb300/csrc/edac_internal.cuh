@@ -21,6 +21,9 @@ enum : uint8_t { FLUID = 0, INLET = 1, OUTLET = 2, WALL = 3, SLIPWALL = 4 };
 // sticky device error bits
 enum : unsigned { ERR_CAPACITY = 1u, ERR_NONFINITE = 2u, ERR_DOMAIN = 4u, ERR_LIST = 8u,
                   ERR_TIMEOUT = 16u };
+// inlet velocity in time: steady modes, and the 2D pulse, ramp and passing vortex of the
+// outlet test problems (Secs. 4.2-4.4)
+enum : int { IN_MODES = 0, IN_PULSE = 1, IN_RAMP = 2, IN_VORTEX = 3 };
 // outlet treatments (Sec. 3): hybrid (3.4), do-nothing (3.1), modified do-nothing (3.1.1),
 // method of characteristics (3.3), mirroring (3.2)
 enum : int { OUT_HYBRID = 0, OUT_DONOTHING = 1, OUT_MOD_DONOTHING = 2, OUT_CHARACTERISTIC = 3,
@@ -50,6 +53,9 @@ struct Phys {
     double modes[MAX_MODES];
     int has_outlet, n_avg;
     int outlet_kind;                 // EDAC_OUTLET_* (hybrid unless set)
+    double moc_u_ref, moc_p_ref;     // reference state of the characteristic outlet
+    int in_kind;                     // IN_*: inlet velocity in time
+    double in_prm[4];                // its parameters
     double x_out, L_out, I_thr;
     int wall_slip[2], wall_drag[2];
     double wall_u[2], wall_v[2];
@@ -125,6 +131,16 @@ struct Dev {
     int *drag_slots;   // [n_drag], ascending slot
     double *scratch_m; // [LIST_MAX]
     double *hist;      // [max_history][8]
+    double *probe_part;  // [PROBE_BLK][PROBE_MAX][8] per-block probe sums
+    double *probe_out;   // [PROBE_MAX][4] probe values
+};
+
+// Probe points (by value into the probe kernels).
+constexpr int PROBE_MAX = 8;
+constexpr int PROBE_BLK = 304;
+struct ProbePts {
+    int n;
+    double x[PROBE_MAX], y[PROBE_MAX];
 };
 
 // -------------------------------------------------------------------------------------------
@@ -251,18 +267,40 @@ __device__ __forceinline__ void set_err(const Dev &d, unsigned bits)
     atomicOr(&d.cnt->err, bits);
 }
 
-// Inlet profile u(y) = U + sum_k a_k sin(k pi (y - y0) / H).
-__device__ __forceinline__ double inlet_u(const Phys &ph, double y)
+// Inlet velocity (u, v) at height y and time t:
+//   modes:  u = U + sum_k a_k sin(k pi (y - y0) / H), v = 0;
+//   pulse:  u = U + A cos(pi (y - y0) / 12) exp(-(t - t0)^2 / delta) for t0 < t < t1 (Eq.
+//           velfunc2 with a decaying exponent), prm = (A, t0, t1, delta);
+//   ramp:   u = U min(t / T, 1), prm = (T);
+//   vortex: x_r = U (d0 - t), y_r = y - y_c, r^2 = x_r^2 + y_r^2: u = U + G y_r / (r^2 + c),
+//           v = -G x_r / (r^2 + c) (Eqs. vortex, vortexx), prm = (G, c, d0, y_c).
+__device__ __forceinline__ void inlet_uv(const Phys &ph, double y, double t, double &u, double &v)
 {
-    double u = ph.U;
-    for (int k = 0; k < ph.n_modes; ++k)
-        u += ph.modes[k] * sin((double)(k + 1) * 3.141592653589793 * (y - ph.in_y0) / ph.in_H);
-    return u;
+    const double *q = ph.in_prm;
+    v = 0.0;
+    if (ph.in_kind == IN_PULSE) {
+        u = ph.U;
+        if (t > q[1] && t < q[2]) u += q[0] * cos(3.141592653589793 * (y - ph.in_y0) / 12.0) *
+                                       exp(-(t - q[1]) * (t - q[1]) / q[3]);
+    } else if (ph.in_kind == IN_RAMP) {
+        u = ph.U * (t < q[0] ? t / q[0] : 1.0);
+    } else if (ph.in_kind == IN_VORTEX) {
+        const double xr = ph.U * (q[2] - t), yr = y - q[3];
+        const double den = xr * xr + yr * yr + q[1];
+        u = ph.U + q[0] * yr / den;
+        v = -q[0] * xr / den;
+    } else {
+        u = ph.U;
+        for (int k = 0; k < ph.n_modes; ++k)
+            u += ph.modes[k] * sin((double)(k + 1) * 3.141592653589793 * (y - ph.in_y0) / ph.in_H);
+    }
 }
 
 // ------------------------------------------------------------------- host-side launchers
 // Every launcher issues its kernels on `s` and returns the number of launches issued.
 int launch_rebuild(const Dev &d, cudaStream_t s, int mixed);
+// probe values (p, u, v, fluid count) into d.probe_out
+int launch_probe(const Dev &d, cudaStream_t s, const ProbePts &q);
 int launch_pass_a(const Dev &d, cudaStream_t s, int mixed);
 int launch_boundary(const Dev &d, cudaStream_t s, int mixed, int end_of_step);
 int launch_pass_b(const Dev &d, cudaStream_t s, int mixed);

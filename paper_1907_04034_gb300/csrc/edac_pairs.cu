@@ -1127,8 +1127,8 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
             //   hybrid (Sec. 3.4): red take the Shepard J2 of the fluid, blue the mean
             //     previous-step J2 of their red outlet neighbours; J3 = 0 gives p' = J2/2,
             //     u' = J2/(2 rho0 c); value = frozen average + acoustic part (Eq. acou);
-            //   characteristic (Sec. 3.3): the same J2 against the free stream (U, p = 0),
-            //     v stays frozen;
+            //   characteristic (Sec. 3.3): the same J2 against a fixed reference state
+            //     (u_ref, p_ref), v stays frozen;
             //   modified do-nothing (Sec. 3.1.1): values stay frozen, red advect with the
             //     Shepard u of the fluid (Eq. shepard0), blue with the mean previous-step
             //     advection velocity of their red neighbours.
@@ -1179,8 +1179,8 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                 } else {
                     const bool ch = kind == OUT_CHARACTERISTIC;
                     const T J2 = red ? shep : (mr > (T)0 ? a[3] / mr : (T)0);
-                    const double ub = ch ? ph.U : d.ubar[s];
-                    const double pb = ch ? 0.0 : d.pbar[s];
+                    const double ub = ch ? ph.moc_u_ref : d.ubar[s];
+                    const double pb = ch ? ph.moc_p_ref : d.pbar[s];
                     const double un = ub + (double)(J2 * (MIXED ? (T)ph.inv_2rcf : (T)ph.inv_2rc));
                     const double adv = red ? un : (mr > (T)0 ? blue_adv : (ch ? un : ub));
                     d.u[s] = un;

@@ -565,6 +565,117 @@ def test_mirrored_outlet_is_exact_for_linear_fields():
     np.testing.assert_allclose(o.a["advp"][:n][out], o.a["u"][:n][out], rtol=0, atol=0)
 
 
+# ------------------------------------------------- inlet in time, probes (Sec. 4 problems)
+def test_ramp_inlet_moves_particles_by_the_integral_of_the_ramp():
+    # Sec. 4.3: u = U t / T for t < T, so an inlet particle moves by U t^2 / (2 T); the
+    # integrator stage takes the inlet velocity at the end of each stage, which adds at most
+    # U t dt / (2 T)
+    c = cases.outlet_problem("ramp")
+    o = oracle.OracleSim(c, neighbor_mode=1)
+    x0 = {int(i): x for i, x, t in zip(o.field("id"), o.field("x"), o.field("tag")) if t == INLET}
+    o.step(180)
+    t = o.t
+    T = c.params.inlet_prm[0]
+    f = o.fields(("id", "x", "u", "v", "tag"))
+    inl = [(x0[int(i)], x, u) for i, x, u, tg in zip(f["id"], f["x"], f["u"], f["tag"])
+           if tg == INLET and int(i) in x0]
+    assert len(inl) > 50 and t < T
+    want = t * t / (2 * T)
+    for a, b, u in inl:
+        assert want <= b - a <= want + t * c.params.dt / (2 * T) + 1e-12
+        assert u == pytest.approx(t / T, rel=1e-12)
+    assert np.all(f["v"][f["tag"] == INLET] == 0.0)
+
+
+def test_vortex_inlet_velocity_is_antisymmetric_about_the_centre_line():
+    # Eqs. vortex, vortexx: u - U is odd and v even in y - y_c; on the centre line u = U and,
+    # at t = 0 (centre d0 = 1 upstream), v = -G d0 / (d0^2 + c)
+    c = cases.outlet_problem("vortex")
+    G, core, d0, yc = c.params.inlet_prm
+    o = oracle.OracleSim(c, neighbor_mode=1)
+    o.step(1)
+    f = o.fields(("x", "y", "u", "v", "tag"))
+    inl = f["tag"] == INLET
+    y, u, v = f["y"][inl], f["u"][inl], f["v"][inl]
+    up = {round(a - yc, 9): (b, w) for a, b, w in zip(y, u, v)}
+    pairs = [(up[k], up[-k]) for k in up if k > 0 and -k in up]
+    assert len(pairs) > 10
+    for (ua, va), (ub, vb) in pairs:
+        assert ua - 1.0 == pytest.approx(-(ub - 1.0), rel=1e-12, abs=1e-15)
+        assert va == pytest.approx(vb, rel=1e-12)
+    t = c.params.dt
+    xr = 1.0 * (d0 - t)
+    ymin = np.min(np.abs(y - yc))
+    k = np.argmin(np.abs(y - yc))
+    assert v[k] == pytest.approx(-G * xr / (xr * xr + ymin * ymin + core), rel=1e-12)
+
+
+def test_pulse_inlet_is_quiet_outside_its_window():
+    c = cases.outlet_problem("pulse2d")
+    o = oracle.OracleSim(c, neighbor_mode=1)
+    o.step(300)  # t = 0.82 < t0
+    f = o.fields(("u", "tag"))
+    assert np.all(f["u"][f["tag"] == INLET] == 1.0)
+    o.step(70)   # t = 1.009: inside (1, 1.1), A cos(pi y/12) exp(-(t-1)^2/delta) added
+    f = o.fields(("y", "u", "tag"))
+    inl = f["tag"] == INLET
+    A, t0, t1, dl = c.params.inlet_prm
+    t = o.t
+    want = 1.0 + A * np.cos(np.pi * f["y"][inl] / 12.0) * np.exp(-(t - t0) ** 2 / dl)
+    np.testing.assert_allclose(f["u"][inl], want, rtol=1e-12)
+    assert f["u"][inl].min() > 1.4
+
+
+def test_probe_is_the_shepard_average_of_the_fluid():
+    # on a lattice, the kernel weights around a lattice node are symmetric, so the Shepard
+    # average of a linear field at the node is the field's value there; the count is the
+    # number of lattice points within 3h (brute force)
+    c = cases.taylor_green(n=30)
+    c.params.periodic_x = c.params.periodic_y = 0
+    c.u[:] = 0.5 - 2.0 * c.x + 0.25 * c.y
+    c.v[:] = 0.0
+    c.p[:] = 1.0 + 3.0 * c.x - 1.5 * c.y
+    o = oracle.OracleSim(c)
+    k = int(np.argmin((c.x - 0.5) ** 2 + (c.y - 0.5) ** 2))
+    qx, qy = c.x[k], c.y[k]
+    out = o.probe([qx], [qy])[0]
+    assert out[0] == pytest.approx(1.0 + 3.0 * qx - 1.5 * qy, rel=1e-12)
+    assert out[1] == pytest.approx(0.5 - 2.0 * qx + 0.25 * qy, rel=1e-12)
+    rc = 3.0 * c.params.h
+    assert out[3] == np.count_nonzero((c.x - qx) ** 2 + (c.y - qy) ** 2 < rc * rc)
+    # far from every particle: zeros
+    assert np.all(o.probe([5.0], [5.0])[0] == 0.0)
+
+
+def test_inviscid_rates_are_finite():
+    # nu = 0 (Sec. 4 test problems): the harmonic mean of two zero viscosities is zero
+    c = cases.outlet_problem("vortex")
+    o = oracle.OracleSim(c, neighbor_mode=1)
+    o.step(3)
+    for k in ("au", "av", "ap", "u", "p"):
+        assert np.all(np.isfinite(o.field(k)))
+
+
+def test_characteristic_outlet_with_a_reference_state():
+    # Sec. 3.3 with (u_ref, p_ref) = (1.2, 0.3): a fluid state u = u_ref + a/(2 rho c),
+    # p = p_ref + a/2 has J2 = a, J3 = 0 and reaches the red outlet particles unchanged
+    c = cases.channel(jitter=0.0, pulse_amp=0.0, n_in=4)
+    c.params.outlet_kind = OUTLET_KINDS["characteristic"]
+    c.params.moc_ref = (1.2, 0.3)
+    a = 0.02
+    rho_c = c.params.rho0 * c.params.cs
+    c.u[:] = 1.2 + a / (2 * rho_c)
+    c.p[:] = 0.3 + a / 2
+    o = oracle.OracleSim(c)
+    o.step(1)
+    f = o.fields(("tag", "u", "p", "J2p", "redp"))
+    red = (f["tag"] == OUTLET) & (f["redp"] == 1)
+    assert red.sum() > 20
+    np.testing.assert_allclose(f["p"][red], 0.3 + 0.5 * f["J2p"][red], rtol=1e-13)
+    np.testing.assert_allclose(f["u"][red], 1.2 + f["J2p"][red] / (2 * rho_c), rtol=1e-13)
+    np.testing.assert_allclose(f["J2p"][red], a, rtol=0.1)
+
+
 def _open_lattice(n=24):
     c = cases.taylor_green(n=n)
     c.params.periodic_x = 0
