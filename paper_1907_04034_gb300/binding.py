@@ -144,6 +144,16 @@ def load(path: Optional[str] = None):
         L.edac_read_profile.argtypes = [_P, i32, _DP, C.POINTER(i64), i32]
         L.edac_launch_count.argtypes = [_P, C.POINTER(i64)]
         L.edac_density_static.argtypes = [C.POINTER(Params), i32] + [_P] * 6
+        L.edac_fma_peak.argtypes = [i32, _P, _DP]
+        L.edac_set_tiling.argtypes = [_P, i32, i32]
+        L.edac_autotune.argtypes = [_P, i32, C.POINTER(i32), C.POINTER(i32), _DP]
+        L.edac_batch_create.argtypes = [C.POINTER(_P), i32, _P, C.POINTER(_P)]
+        L.edac_batch_step.argtypes = [_P, i32]
+        L.edac_batch_launch_count.argtypes = [_P, C.POINTER(i64)]
+        L.edac_batch_destroy.argtypes = [_P]
+        L.edac_set_inlet_transient.argtypes = [_P, i32, i32, _DP]
+        L.edac_set_outlet_reference.argtypes = [_P, C.c_double, C.c_double]
+        L.edac_probe.argtypes = [_P, i32, _DP, _DP, _DP]
         L.edac_last_error.argtypes = [_P]
         L.edac_last_error.restype = C.c_char_p
         L.edac_destroy.argtypes = [_P]

@@ -211,10 +211,12 @@ def outlet_problem(problem: str = "pulse2d", outlet: int = 0, long: bool = False
     nxw = 2 * n_lay + nx
     bx, by = _lattice(-n_lay * dx, nxw, -n_lay * dx, n_lay, dx)
     tx, ty = _lattice(-n_lay * dx, nxw, W, n_lay, dx)
+    # headroom for the inflow over t_end: the outlet may not remove as much as enters (a
+    # frozen outlet at rest, or a long domain whose outlet the flow does not reach)
     c = _assemble(problem + ("_long" if long else ""), params,
                   [(fx, fy, FLUID), (ix, iy, INLET), (ox, oy, OUTLET),
                    (np.concatenate([bx, tx]), np.concatenate([by, ty]), SLIPWALL)],
-                  capacity_extra=4 * ny + 64)
+                  capacity_extra=int((2.0 * U * t_end / dx + 2) * ny) + 64)
     c.u[:] = np.where(c.tag == SLIPWALL, 0.0, u0)
     c.p[:] = 0.0
     return c

@@ -1,6 +1,7 @@
-"""Long-run physics of the flow past a cylinder (Sec. 4.6): drag and lift coefficients and
-the Strouhal number from the library's force history, for comparison with Table clcd
-(Re = 200) and Table hybridconv (Re = 20).
+"""Long-run physics (Sec. 4): the flow past a cylinder (Sec. 4.6), drag and lift coefficients
+and the Strouhal number from the library's force history, for comparison with Table clcd
+(Re = 200) and Table hybridconv (Re = 20); and the outlet test problems (2D pulse, ramp,
+passing vortex; Secs. 4.2-4.4), L2 errors at a probe against a long domain (Eq. l2norm).
 
 The paper's setup: cylinder of diameter D, channel 15D x 15D with the cylinder 5D behind the
 inlet interface, slip walls, uniform inlet velocity U, hybrid outlet, six layers of inlet,
@@ -130,6 +131,55 @@ def run(dx_over_d: float = 30.0, Re: float = 200.0, t_end: float = 75.0, t_from:
     return out
 
 
+# --------------------------------------------------------- outlet test problems (Sec. 4)
+def l2_error(f, f_long) -> float:
+    """Eq. l2norm: (sum_n (f^n - f_l^n)^2 / sum_n (f_l^n)^2)^(1/2) over the time steps."""
+    f, f_long = np.asarray(f), np.asarray(f_long)
+    return float(np.sqrt(np.sum((f - f_long) ** 2) / np.sum(f_long ** 2)))
+
+
+def probe_history(case, t_end: float, probe_d: float = 1.7, precision: str = "mixed",
+                  device: str = "cuda:0") -> np.ndarray:
+    """Step the case to t_end; after every step the probe (p, u, v) at (d, W/2)."""
+    p = case.params
+    n = int(round(t_end / p.dt))
+    s = binding.Solver(case, precision=precision, use_graphs=True, device=device,
+                       max_history=n + 16)
+    qx, qy = np.array([probe_d]), np.array([0.5 * p.inlet_h])
+    out = np.zeros((n, 3))
+    for k in range(n):
+        s.step(1)
+        out[k] = s.probe(qx, qy)[0, :3]
+    s.close()
+    return out
+
+
+def outlet_problem_errors(problem: str, t_end: float = None, precision: str = "mixed",
+                          outlets=("characteristic", "donothing", "hybrid", "mirror",
+                                   "mod_donothing")) -> dict:
+    """e(p*), e(u*) (and e(v*)) at the probe for each outlet, against the long domain, with
+    p* = 2 p / (rho u_ref^2), u* = u / u_ref, v* = v / u_ref and u_ref = U (Sec. 4.2)."""
+    if t_end is None:
+        t_end = 4.0 if problem == "vortex" else 3.0
+    ref_case = cases.outlet_problem(problem, outlet=OUTLETS["hybrid"], long=True, t_end=t_end)
+    rho0, U = ref_case.params.rho0, ref_case.params.U
+    scale = np.array([2.0 / (rho0 * U * U), 1.0 / U, 1.0 / U])
+    ref = probe_history(ref_case, t_end, precision=precision) * scale
+    out = {"problem": problem, "t_end": t_end, "precision": precision, "errors": {}}
+    for name in outlets:
+        c = cases.outlet_problem(problem, outlet=OUTLETS[name], t_end=t_end)
+        try:
+            h = probe_history(c, t_end, precision=precision) * scale
+        except binding.EdacError as e:
+            out["errors"][name] = {"error": str(e)}
+            continue
+        e = {"p": l2_error(h[:, 0], ref[:, 0]), "u": l2_error(h[:, 1], ref[:, 1])}
+        if problem == "vortex":
+            e["v"] = l2_error(h[:, 2], ref[:, 2])
+        out["errors"][name] = e
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--dx-over-d", type=float, default=30.0)
@@ -141,7 +191,13 @@ def main():
     ap.add_argument("--diagnose", action="store_true",
                     help="record the per-tag field ranges after every chunk")
     ap.add_argument("--outlet", default="hybrid", choices=tuple(OUTLETS))
+    ap.add_argument("--problem", default=None, choices=("pulse2d", "ramp", "vortex"),
+                    help="an outlet test problem of Sec. 4 instead of the cylinder: L2 errors "
+                         "at the probe for every outlet against the long domain")
     a = ap.parse_args()
+    if a.problem:
+        print(json.dumps(outlet_problem_errors(a.problem, precision=a.precision)))
+        return
     print(json.dumps(run(a.dx_over_d, a.re, a.t_end, a.t_from, a.precision, a.chunk,
                          diagnose=a.diagnose, outlet=a.outlet)))
 

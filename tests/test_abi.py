@@ -86,3 +86,9 @@ def test_fma_peak_rejects_bad_arguments_before_any_gpu_call(lib):
     out = C.c_double(-1.0)  # status 1 = EDAC_E_INVALID
     assert lib.edac_fma_peak(7, None, C.byref(out)) == 1
     assert lib.edac_fma_peak(binding.EDAC_PEAK_FP32, None, None) == 1
+
+
+def test_binding_declares_the_argument_types_of_every_entry(lib):
+    # ctypes converts floats and pointers only for declared signatures
+    for name in binding.EXPORTS:
+        assert getattr(lib, name).argtypes is not None, name
