@@ -903,17 +903,6 @@ __device__ __forceinline__ void fluid_fields(const Dev &d, int j, T &p, T &u, T 
     }
 }
 
-// 1/sqrt(x) in fp64 for x > 0: the fp32 hardware estimate refined by two Newton-Raphson
-// steps on f(y) = 1/y^2 - x, y <- y (3 - x y^2)/2; each step squares the relative error
-// (2^-23 -> 2^-46 -> below the fp64 rounding), with no fp64 division or square root.
-__device__ __forceinline__ double rsqrt_newton(double x)
-{
-    double y = (double)rsqrt_approx((float)x);
-    y = y * (1.5 - 0.5 * x * y * y);
-    y = y * (1.5 - 0.5 * x * y * y);
-    return y;
-}
-
 template <class T>
 __device__ __forceinline__ T sqrt_t(T x);
 template <>
@@ -986,25 +975,49 @@ __device__ __forceinline__ void mirror_extrapolate(const Dev &d, int lane, int *
         const double2 xyl = d.XY[l];
         double xlk, ylk;  // r_lk = r_l - r_k, the canonical fp64 separation
         const double r2 = exact_r2(g, xyl.x, xyl.y, xk, yk, xlk, ylk);
-        double fv[3], Vl;
-        fluid_fields<MIXED>(d, l, fv[0], fv[1], fv[2], Vl);
-        double w, wx = 0, wy = 0;
-        if (r2 > 1e-30) {
-            // fp64 path: IEEE square root and division (the oracle's arithmetic);
-            // mixed path: Newton-refined inverse square root, no fp64 division
-            double ir, r;
-            if (MIXED) { ir = rsqrt_newton(r2); r = r2 * ir; }
-            else { r = sqrt(r2); ir = 1.0 / r; }
-            double wq, dwq;
-            quintic_w_dw(r * ph.inv_h, wq, dwq);
-            w = ph.a2 * wq;
-            const double dwr = ph.a2h * dwq * ir;
-            wx = dwr * xlk;
-            wy = dwr * ylk;
+        double fv[3], row[3];
+        if (MIXED) {
+            // mixed path: the kernel terms W V, W_x V, W_y V in fp32 (relative error ~1e-7
+            // each, on the fp32 pipe); the moment sums, where the cancellation is, stay fp64
+            const float4 q = d.Qf[l];
+            const float4 b = d.Bf[l];
+            fv[0] = (double)q.x; fv[1] = (double)b.x; fv[2] = (double)b.y;
+            const float Vl = q.w, r2f = (float)r2;
+            float w, wx = 0.0f, wy = 0.0f;
+            if (r2f > 1e-30f) {
+                const float ir = rsqrt_approx(r2f);
+                float wq, dwq;
+                quintic_w_dw(r2f * ir * ph.inv_hf, wq, dwq);
+                w = ph.a2f * wq;
+                const float dwr = ph.a2hf * dwq * ir;
+                wx = dwr * (float)xlk;
+                wy = dwr * (float)ylk;
+            } else {
+                w = ph.a2f * quintic_w(0.0f);
+            }
+            row[0] = (double)(w * Vl);
+            row[1] = (double)(wx * Vl);
+            row[2] = (double)(wy * Vl);
         } else {
-            w = ph.a2 * quintic_w(0.0);
+            // fp64 path: IEEE square root and division (the oracle's arithmetic)
+            double Vl;
+            fluid_fields<MIXED>(d, l, fv[0], fv[1], fv[2], Vl);
+            double w, wx = 0, wy = 0;
+            if (r2 > 1e-30) {
+                const double r = sqrt(r2), ir = 1.0 / r;
+                double wq, dwq;
+                quintic_w_dw(r * ph.inv_h, wq, dwq);
+                w = ph.a2 * wq;
+                const double dwr = ph.a2h * dwq * ir;
+                wx = dwr * xlk;
+                wy = dwr * ylk;
+            } else {
+                w = ph.a2 * quintic_w(0.0);
+            }
+            row[0] = w * Vl;
+            row[1] = wx * Vl;
+            row[2] = wy * Vl;
         }
-        const double row[3] = {w * Vl, wx * Vl, wy * Vl};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             a[3 * q + 0] += row[q];
