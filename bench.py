@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--batch-channels", type=int, default=64,
                     help="uneven channels of the batched measurement (0: skip it)")
     ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--tangent-steps", type=int, default=100,
+                    help="steps of the gradient workload (0: skip it)")
     return ap.parse_args()
 
 
@@ -222,6 +224,44 @@ def run_batched(n_chan, steps, dev):
                                           "note": "host wall clock, each member its own graph"},
             "workload": "uneven pulse channels: N ~ U[2k, 60k], dx ~ U[0.005, 0.03], "
                         "Re ~ U[50, 500], pulse centre uniform (seed 0); mixed path"}
+
+
+# ------------------------------------------------------------------------------ gradient
+def run_tangent(steps, dev):
+    """The gradient workload: cylinder at dx = D/25, inlet modes a_k ~ N(0, 0.02) (seed 0),
+    mean drag over `steps` steps; the gradient with respect to the 8 modes from the
+    tangent-linear model, its time against the fp64 forward run of the same steps, and one
+    central difference (mode 1, eps = 1e-6) as a check."""
+    import torch
+    from paper_1907_04034_gb300 import binding, cases, gradient
+
+    c = cases.cylinder(dx=1.0 / 25.0)
+    a = np.random.default_rng(0).normal(0.0, 0.02, 8)
+    # forward: fp64 steps on graphs, timed with events
+    cc = gradient._with_modes(c, a)
+    s = binding.Solver(cc, precision="fp64", use_graphs=True, device=str(dev),
+                       max_history=steps + 16)
+    s.step(2)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    s.step(steps)
+    e1.record(s.stream)
+    torch.cuda.synchronize(dev)
+    fwd_ms = e0.elapsed_time(e1)
+    s.close()
+    L, g, tm = gradient.drag_gradient(c, a, steps, device=str(dev))
+    gf, same = gradient.central_differences(c, a, steps, eps=1e-6, modes=[0], device=str(dev))
+    return {"workload": f"cylinder Re=200, dx=D/25 ({c.n} particles), 8 inlet modes "
+                        f"a_k ~ N(0, 0.02) seed 0, mean c_d over {steps} steps",
+            "method": "tangent-linear model of the fp64 step (forward mode, 8 directions)",
+            "loss": L, "dL_da": [float(v) for v in g],
+            "tangent_s": tm["tangent_s"], "forward_s": fwd_ms / 1e3,
+            "tangent_over_forward": tm["tangent_s"] / (fwd_ms / 1e3),
+            "fd_check_mode1": {"fd": float(gf[0]), "tangent": float(g[0]),
+                               "rel_diff": float(abs(g[0] - gf[0]) / max(abs(gf[0]), 1e-300)),
+                               "same_events": bool(same[0])}}
 
 
 # -------------------------------------------------------------------------- reference
@@ -416,6 +456,11 @@ def main():
     if args.batch_channels > 0:
         batched = run_batched(args.batch_channels, args.batch_steps, dev)
 
+    # ------------------------------------ gradient workload: tangent-linear model vs forward
+    tangent = None
+    if args.tangent_steps > 0:
+        tangent = run_tangent(args.tangent_steps, dev)
+
     # ---------------------------------------------------------------------- CPU baseline
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -440,6 +485,7 @@ def main():
                 "mixed_over_fp64": value / v64 if v64 else None,
                 "drag_rel_err_mixed_vs_fp64": drag_err, "drag_steps_compared": nc,
                 "batched": batched,
+                "gradient": tangent,
                 "kernel_ms_per_launch": kernels, "eager_step_ms": step_ms_eager}
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -332,6 +332,31 @@ void edac_batch_destroy(edac_batch *batch);
 #define EDAC_MAX_PROBES 8
 edac_status edac_probe(edac_ctx *ctx, int n, const double *h_x, const double *h_y, double *h_out);
 
+/* ---------------------------------------------------------------------------
+ * Tangent-linear model (fp64 path, steady inlet modes, hybrid outlet): the
+ * derivatives of the step with respect to the inlet modes a_1..a_8 of
+ * u(y) = U + sum_k a_k sin(k pi (y - y0)/H) (edac_set_inlet), carried forward
+ * next to the values, with the neighbour sets, the gate decisions, the outlet
+ * classes and the recycling events the values produce held fixed.  Gives the
+ * gradient of any functional of the force history, such as the time-averaged
+ * drag, with respect to the modes.  It is forward-mode: each step costs about
+ * EDAC_TANGENT_DIRECTIONS times the fp64 step, in return for no checkpoints.
+ *   edac_tangent_workspace_bytes: device bytes the tangents need (caller-owned,
+ *     256-byte aligned, kept alive while tangents are stepped);
+ *   edac_tangent_enable: set the tangents of the current state (zero except the
+ *     inlet velocities, whose derivatives are the mode shapes) and of its rates;
+ *     EDAC_E_STATE on the mixed path or with other inlet/outlet kinds;
+ *   edac_step_tangent: nsteps steps of values and tangents (no graph);
+ *   edac_read_tangent_history: for the last steps (at most max_steps, and not
+ *     before the enable) d F_x / d a_k into h_dfx[step * 8 + k] and d F_y / d a_k
+ *     into h_dfy, aligned with edac_read_history; synchronises the stream. */
+#define EDAC_TANGENT_DIRECTIONS 8
+edac_status edac_tangent_workspace_bytes(edac_ctx *ctx, size_t *bytes);
+edac_status edac_tangent_enable(edac_ctx *ctx, void *d_workspace, size_t bytes);
+edac_status edac_step_tangent(edac_ctx *ctx, int nsteps);
+edac_status edac_read_tangent_history(edac_ctx *ctx, int max_steps, double *h_dfx,
+                                      double *h_dfy, int *nsteps);
+
 /* Text of the last error of this context (valid until the next call); with
  * ctx = NULL, the last error of a context-less call (edac_workspace_bytes,
  * edac_create) made on this host thread. */

@@ -24,7 +24,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libedac.so")
-SOURCES = ("edac_capi.cu", "edac_cells.cu", "edac_pairs.cu", "edac_static.cu", "edac_peaks.cu")
+SOURCES = ("edac_capi.cu", "edac_cells.cu", "edac_pairs.cu", "edac_static.cu", "edac_peaks.cu",
+           "edac_tangent.cu")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 EDAC_FP64, EDAC_MIXED = 0, 1
@@ -43,7 +44,8 @@ EXPORTS = ("edac_workspace_bytes", "edac_create", "edac_set_inlet", "edac_set_ou
            "edac_density_static", "edac_fma_peak", "edac_set_tiling", "edac_autotune",
            "edac_batch_create", "edac_batch_step", "edac_batch_launch_count", "edac_batch_destroy",
            "edac_set_inlet_transient", "edac_set_outlet_reference", "edac_probe",
-           "edac_last_error", "edac_destroy")
+           "edac_tangent_workspace_bytes", "edac_tangent_enable", "edac_step_tangent",
+           "edac_read_tangent_history", "edac_last_error", "edac_destroy")
 
 
 class EdacError(RuntimeError):
@@ -154,6 +156,10 @@ def load(path: Optional[str] = None):
         L.edac_set_inlet_transient.argtypes = [_P, i32, i32, _DP]
         L.edac_set_outlet_reference.argtypes = [_P, C.c_double, C.c_double]
         L.edac_probe.argtypes = [_P, i32, _DP, _DP, _DP]
+        L.edac_tangent_workspace_bytes.argtypes = [_P, C.POINTER(sz)]
+        L.edac_tangent_enable.argtypes = [_P, _P, sz]
+        L.edac_step_tangent.argtypes = [_P, i32]
+        L.edac_read_tangent_history.argtypes = [_P, i32, _DP, _DP, C.POINTER(i32)]
         L.edac_last_error.argtypes = [_P]
         L.edac_last_error.restype = C.c_char_p
         L.edac_destroy.argtypes = [_P]
@@ -378,6 +384,29 @@ class Solver:
         self._call("edac_probe", len(xs), _ptr(xs, C.c_double), _ptr(ys, C.c_double),
                    _ptr(out, C.c_double))
         return out
+
+    # ------------------------------------------------------------ tangent-linear model
+    def tangent_enable(self):
+        """Allocate the tangent workspace and set the tangents (edac_tangent_enable)."""
+        nb = C.c_size_t(0)
+        self._call("edac_tangent_workspace_bytes", C.byref(nb))
+        with self.torch.cuda.device(self.device):
+            self.tangent_ws = self.torch.empty(int(nb.value), dtype=self.torch.uint8,
+                                               device=self.device)
+        self._call("edac_tangent_enable", C.c_void_p(self.tangent_ws.data_ptr()), nb.value)
+
+    def step_tangent(self, n: int = 1):
+        self._call("edac_step_tangent", int(n))
+
+    def tangent_history(self, max_steps: Optional[int] = None):
+        """(dFx/da, dFy/da): arrays (steps, 8) aligned with history()."""
+        m = int(max_steps or self.cparams.max_history)
+        dfx = np.zeros((m, 8))
+        dfy = np.zeros((m, 8))
+        ns = C.c_int(0)
+        self._call("edac_read_tangent_history", m, _ptr(dfx, C.c_double), _ptr(dfy, C.c_double),
+                   C.byref(ns))
+        return dfx[: ns.value].copy(), dfy[: ns.value].copy()
 
     def set_tiling(self, tile_cells: int, threads: int):
         """Tiling of the mixed pair passes (edac_set_tiling)."""

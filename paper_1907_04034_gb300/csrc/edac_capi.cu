@@ -12,6 +12,7 @@
 #include "edac.h"
 #include "edac_internal.cuh"
 
+static_assert(edac::T_DIR == EDAC_TANGENT_DIRECTIONS, "tangent directions of header and kernels");
 static_assert(edac::IN_MODES == EDAC_INLET_MODES && edac::IN_PULSE == EDAC_INLET_PULSE &&
                   edac::IN_RAMP == EDAC_INLET_RAMP && edac::IN_VORTEX == EDAC_INLET_VORTEX &&
                   edac::PROBE_MAX == EDAC_MAX_PROBES,
@@ -48,6 +49,9 @@ struct edac_ctx {
     double prof_ms[EDAC_NUM_KERNELS] = {};
     long long prof_launches[EDAC_NUM_KERNELS] = {};
     std::string err;
+    void *tws = nullptr;        // tangent workspace (edac_tangent_enable)
+    size_t tws_bytes = 0;
+    long long tangent_steps = 0;
 };
 
 namespace {
@@ -243,6 +247,7 @@ size_t layout(Dev &d, const Geo &g, int cap, int max_history, int mixed, char *b
     DARR(ev_del_key, unsigned long long, LIST_MAX); DARR(ev_del_slot, int, LIST_MAX);
     DARR(ev_out_key, unsigned long long, LIST_MAX); DARR(ev_out_m, double, LIST_MAX);
     DARR(drag_slots, int, C);
+    DARR(spawn_map, int2, LIST_MAX);
     DARR(scratch_m, double, LIST_MAX);
     DARR(hist, double, (size_t)max_history * 8);
     DARR(probe_part, double, (size_t)PROBE_BLK * PROBE_MAX * 8);
@@ -847,6 +852,114 @@ edac_status edac_launch_count(edac_ctx *ctx, int64_t *count)
 const char *edac_last_error(edac_ctx *ctx)
 {
     return ctx ? ctx->err.c_str() : g_err.c_str();
+}
+
+// ------------------------------------------------------------ tangent-linear model
+edac_status edac_tangent_workspace_bytes(edac_ctx *ctx, size_t *bytes)
+{
+    if (!ctx || !bytes) return EDAC_E_INVALID;
+    *bytes = tangent_bytes(ctx->d);
+    return EDAC_OK;
+}
+
+namespace {
+
+// One evaluation with its tangents (value kernel, then the tangent kernel of the same part).
+int tangent_eval(edac_ctx *c, int end_of_step)
+{
+    const Dev &d = c->d;
+    cudaStream_t s = c->stream;
+    int n = 0;
+    n += launch_rebuild(d, s, 0);
+    n += launch_pass_a(d, s, 0);
+    n += launch_tangent(d, c->tws, s, TG_PASS_A, 0.0);
+    n += launch_boundary(d, s, 0, end_of_step);
+    n += launch_tangent(d, c->tws, s, TG_BOUNDARY, 0.0);
+    n += launch_pass_b(d, s, 0);
+    n += launch_tangent(d, c->tws, s, TG_PASS_B, 0.0);
+    // the outlet update of this evaluation: its values went to the slot arrays only, after the
+    // rates of this evaluation were fixed on the step's outlet values; so are its tangents
+    if (end_of_step && d.ph.has_outlet) n += launch_tangent(d, c->tws, s, TG_OUTLET, 0.0);
+    return n;
+}
+
+}  // namespace
+
+edac_status edac_tangent_enable(edac_ctx *ctx, void *d_workspace, size_t bytes)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    if (ctx->mixed) return fail(ctx, EDAC_E_STATE, "the tangent model is built on the fp64 path");
+    if (!ctx->loaded) return fail(ctx, EDAC_E_STATE, "no particles");
+    if (ctx->failed) return fail(ctx, EDAC_E_STATE, "context in error");
+    const Phys &ph = ctx->d.ph;
+    if (ph.in_kind != IN_MODES || (ph.has_outlet && ph.outlet_kind != OUT_HYBRID))
+        return fail(ctx, EDAC_E_STATE, "the tangent model needs the steady inlet modes and the hybrid outlet");
+    if (!d_workspace || bytes < tangent_bytes(ctx->d) || ((uintptr_t)d_workspace & 255u))
+        return fail(ctx, EDAC_E_INVALID, "tangent workspace missing, too small or not 256-byte aligned");
+    ctx->tws = d_workspace;
+    ctx->tws_bytes = bytes;
+    ctx->tangent_steps = 0;
+    CK(cudaMemsetAsync(d_workspace, 0, bytes, ctx->stream));
+    ctx->launches += launch_tangent(ctx->d, ctx->tws, ctx->stream, TG_INIT, 0.0);
+    // the rates of the current state, with their tangents
+    ctx->launches += tangent_eval(ctx, 0);
+    CK(cudaGetLastError());
+    return check_device(ctx);
+}
+
+edac_status edac_step_tangent(edac_ctx *ctx, int nsteps)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    if (nsteps < 0) return fail(ctx, EDAC_E_INVALID, "nsteps < 0");
+    if (!ctx->tws) return fail(ctx, EDAC_E_STATE, "call edac_tangent_enable first");
+    if (ctx->failed) return fail(ctx, EDAC_E_STATE, "context in error");
+    const Dev &d = ctx->d;
+    cudaStream_t s = ctx->stream;
+    for (int k = 0; k < nsteps; ++k) {
+        int n = 0;
+        n += launch_stage(d, s, 0, 0);
+        n += launch_tangent(d, ctx->tws, s, TG_STAGE_PRED, 0.5 * d.ph.dt);
+        n += tangent_eval(ctx, 0);
+        n += launch_stage(d, s, 0, 1);
+        n += launch_tangent(d, ctx->tws, s, TG_STAGE_CORR, d.ph.dt);
+        n += tangent_eval(ctx, 1);
+        n += launch_tangent(d, ctx->tws, s, TG_RECYCLE_PRE, 0.0);
+        n += launch_recycle(d, s);
+        n += launch_tangent(d, ctx->tws, s, TG_RECYCLE_POST, 0.0);
+        ctx->launches += n;
+    }
+    ctx->tangent_steps += nsteps;
+    CK(cudaGetLastError());
+    return EDAC_OK;
+}
+
+edac_status edac_read_tangent_history(edac_ctx *ctx, int max_steps, double *h_dfx, double *h_dfy,
+                                      int *nsteps)
+{
+    if (!ctx || !nsteps || max_steps < 0) return EDAC_E_INVALID;
+    if (!ctx->tws) return fail(ctx, EDAC_E_STATE, "call edac_tangent_enable first");
+    edac_status st = check_device(ctx);
+    if (st) return st;
+    Counters h;
+    CK(cudaMemcpyAsync(&h, ctx->d.cnt, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    const int H = ctx->d.max_history;
+    std::vector<double> hist((size_t)H * 2 * T_DIR);
+    const double *dev_hist = (const double *)ctx->tws + (size_t)T_NF * T_DIR * ctx->d.cap;
+    CK(cudaMemcpyAsync(hist.data(), dev_hist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const long long avail = std::min<long long>(std::min(h.hist_len, H), ctx->tangent_steps);
+    const int k = (int)std::min<long long>(avail, max_steps);
+    for (int r = 0; r < k; ++r) {
+        const int stepi = h.step - k + r;
+        const double *rec = hist.data() + (size_t)(stepi % H) * 2 * T_DIR;
+        for (int c = 0; c < T_DIR; ++c) {
+            if (h_dfx) h_dfx[(size_t)r * T_DIR + c] = rec[c];
+            if (h_dfy) h_dfy[(size_t)r * T_DIR + c] = rec[T_DIR + c];
+        }
+    }
+    *nsteps = k;
+    return EDAC_OK;
 }
 
 edac_status edac_set_tiling(edac_ctx *ctx, int tile_cells, int threads)

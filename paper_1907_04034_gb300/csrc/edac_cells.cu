@@ -436,6 +436,7 @@ __global__ void __launch_bounds__(1024) k_end_step(Dev d, double *scratch_m)
         if (r >= n_new) continue;
         const int ps = d.ev_spawn_slot[i];
         const int s = d.free_stack[top1 - 1 - r];
+        d.spawn_map[r] = make_int2(ps, s);
         const double yv = d.y[ps];
         double uin, vin;  // the inlet velocity at the end of the step
         inlet_uv(ph, yv, (double)(C->step + 1) * ph.dt, uin, vin);
@@ -462,6 +463,7 @@ __global__ void __launch_bounds__(1024) k_end_step(Dev d, double *scratch_m)
         if (n_new < n_spawn) atomicOr(&C->err, ERR_CAPACITY);
         C->free_top = top1 - n_new;
         C->next_id = id0 + (unsigned long long)n_new;
+        C->last_spawn = n_new;
         C->n_alive = C->n_alive - n_del + n_new;
         const int slot = C->step % d.max_history;
         double *h = d.hist + (size_t)slot * 8;

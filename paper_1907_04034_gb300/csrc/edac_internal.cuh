@@ -72,6 +72,7 @@ struct Counters {
     int n_drag;      // solid particles in the drag sum (static)
     int hist_len;    // history records written (saturates at max_history)
     unsigned long long next_id;
+    int last_spawn;  // inlet particles spawned by the last k_end_step (spawn_map entries)
     // the first particle found outside the domain box (error context for the host)
     int err_rec, err_tag;
     unsigned long long err_id;
@@ -129,6 +130,7 @@ struct Dev {
     unsigned long long *ev_del_key;   int *ev_del_slot;     // [LIST_MAX]
     unsigned long long *ev_out_key;   double *ev_out_m;     // [LIST_MAX]
     int *drag_slots;   // [n_drag], ascending slot
+    int2 *spawn_map;   // [LIST_MAX] (parent slot, new slot) of the last step's spawns
     double *scratch_m; // [LIST_MAX]
     double *hist;      // [max_history][8]
     double *probe_part;  // [PROBE_BLK][PROBE_MAX][8] per-block probe sums
@@ -301,6 +303,19 @@ __device__ __forceinline__ void inlet_uv(const Phys &ph, double y, double t, dou
 int launch_rebuild(const Dev &d, cudaStream_t s, int mixed);
 // probe values (p, u, v, fluid count) into d.probe_out
 int launch_probe(const Dev &d, cudaStream_t s, const ProbePts &q);
+
+// Tangent-linear model of the fp64 step (edac_tangent.cu): slot-indexed tangent fields,
+// T_DIR directions (inlet modes) each, in a workspace of their own.
+constexpr int T_DIR = 8;
+enum : int {
+    T_X, T_Y, T_U, T_V, T_UT, T_VT, T_P, T_X0, T_Y0, T_U0, T_V0, T_P0, T_RHO, T_VOL,
+    T_AU, T_AV, T_AP, T_ABU, T_ABV, T_FX, T_FY, T_UBAR, T_VBAR, T_PBAR, T_J2, T_J2P, T_ADVP,
+    T_J2P_OLD, T_ADVP_OLD, T_RING, T_NF = T_RING + 3 * NAVG_MAX
+};
+enum : int { TG_INIT, TG_PASS_A, TG_BOUNDARY, TG_PASS_B, TG_OUTLET, TG_STAGE_PRED, TG_STAGE_CORR,
+             TG_RECYCLE_PRE, TG_RECYCLE_POST };
+size_t tangent_bytes(const Dev &d);
+int launch_tangent(const Dev &d, void *ws, cudaStream_t s, int what, double tau);
 int launch_pass_a(const Dev &d, cudaStream_t s, int mixed);
 int launch_boundary(const Dev &d, cudaStream_t s, int mixed, int end_of_step);
 int launch_pass_b(const Dev &d, cudaStream_t s, int mixed);

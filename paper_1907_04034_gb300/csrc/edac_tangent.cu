@@ -1,0 +1,626 @@
+// Tangent-linear model of the fp64 step: the derivatives of every particle field with respect
+// to the inlet-profile modes a_k of u(y) = U + sum_k a_k sin(k pi (y - y0) / H), carried
+// forward step by step next to the values (forward-mode differentiation of the discrete step,
+// with the neighbour sets, the acoustic-gate decisions, the red/blue outlet classes and the
+// recycling events those values produce held fixed).
+//
+// Each tangent kernel follows the value kernel it differentiates (same formulas, same
+// neighbour walk, same branch decisions, taken on the values) in dual numbers D1 = value +
+// one derivative; blockIdx.y is the direction (mode) k.  Tangents are slot-indexed,
+// [field][direction][capacity] fp64, in a workspace of their own.  The value kernels run
+// unchanged; the tangent kernels are interleaved after them (see edac_step_tangent).
+#include "edac_internal.cuh"
+
+namespace edac {
+namespace {
+
+// ------------------------------------------------------------------------ dual numbers
+struct D1 {
+    double v, d;
+    __device__ D1() : v(0.0), d(0.0) {}
+    __device__ D1(double a) : v(a), d(0.0) {}
+    __device__ D1(double a, double b) : v(a), d(b) {}
+};
+__device__ __forceinline__ D1 operator+(D1 a, D1 b) { return D1(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ D1 operator-(D1 a, D1 b) { return D1(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ D1 operator-(D1 a) { return D1(-a.v, -a.d); }
+__device__ __forceinline__ D1 operator*(D1 a, D1 b) { return D1(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ __forceinline__ D1 operator/(D1 a, D1 b)
+{
+    const double q = a.v / b.v;
+    return D1(q, (a.d - q * b.d) / b.v);
+}
+__device__ __forceinline__ D1 &operator+=(D1 &a, D1 b) { a = a + b; return a; }
+__device__ __forceinline__ D1 &operator-=(D1 &a, D1 b) { a = a - b; return a; }
+__device__ __forceinline__ D1 dsqrt(D1 a)
+{
+    const double s = sqrt(a.v);
+    return D1(s, s > 0.0 ? 0.5 * a.d / s : 0.0);
+}
+
+// quintic spline w(q), w'(q) with their derivatives along q (w'' for the derivative of w')
+__device__ __forceinline__ void quintic_dual(D1 q, D1 &w, D1 &dw)
+{
+    const double t3 = q.v < 3.0 ? 3.0 - q.v : 0.0;
+    const double t2 = q.v < 2.0 ? 2.0 - q.v : 0.0;
+    const double t1 = q.v < 1.0 ? 1.0 - q.v : 0.0;
+    const double a = t3 * t3, b = t2 * t2, c = t1 * t1;
+    const double wv = t3 * a * a - 6.0 * (t2 * b * b) + 15.0 * (t1 * c * c);
+    const double w1 = -5.0 * (a * a - 6.0 * b * b + 15.0 * c * c);
+    const double w2 = 20.0 * (t3 * a - 6.0 * (t2 * b) + 15.0 * (t1 * c));
+    w = D1(wv, w1 * q.d);
+    dw = D1(w1, w2 * q.d);
+}
+
+// ------------------------------------------------------------------ tangent storage
+struct TDev {
+    double *f[T_NF];  // [direction][capacity] per field
+    double *hist;     // [max_history][2][T_DIR]: d(F_x), d(F_y)
+    int ndir;         // directions in use (modes)
+};
+
+__device__ __forceinline__ double &tg(const TDev &t, const Dev &d, int f, int c, int s)
+{
+    return t.f[f][(size_t)c * d.cap + s];
+}
+
+__device__ __forceinline__ D1 dual(const TDev &t, const Dev &d, double v, int f, int c, int s)
+{
+    return D1(v, t.f[f][(size_t)c * d.cap + s]);
+}
+
+// sin(k pi (y - y0)/H): the derivative of the inlet velocity with respect to mode k
+__device__ __forceinline__ double mode_shape(const Phys &ph, int c, double y)
+{
+    return sin((double)(c + 1) * 3.141592653589793 * (y - ph.in_y0) / ph.in_H);
+}
+
+// Walk the fluid-or-all neighbours of sorted particle k / of a point, exact fp64 test
+template <class F>
+__device__ __forceinline__ void t_walk(const Dev &d, double qx, double qy, int cx, int cy, F &&f)
+{
+    const Geo &g = d.g;
+    for_block(d, cx, cy, [&](int, int, int j0, int j1) {
+        for (int j = j0; j < j1; ++j) {
+            const double2 xy = d.XY[j];
+            double dx, dy;
+            const double r2 = exact_r2(g, qx, qy, xy.x, xy.y, dx, dy);
+            if (r2 < g.rc2) f(j);
+        }
+    });
+}
+
+// ---------------------------------------------------------------------------- pass A
+// S_i = sum_j W_ij, rho_i = sum_j m_j W_ij, V_i = 1/S_i (self included).
+__global__ void t_pass_a(Dev d, TDev t)
+{
+    const int c = blockIdx.y;
+    const int n = d.cnt->n_alive;
+    const Phys &ph = d.ph;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int i = d.order[k];
+        const double2 xi = d.XY[k];
+        const int cc = d.cellk[k];
+        D1 S(0.0), R(0.0);
+        t_walk(d, xi.x, xi.y, cc % d.g.nx, cc / d.g.nx, [&](int j) {
+            const int sj = d.order[j];
+            const double2 xj = d.XY[j];
+            double ex, ey;
+            exact_r2(d.g, xi.x, xi.y, xj.x, xj.y, ex, ey);  // minimum-image separation
+            const D1 dx(ex, tg(t, d, T_X, c, i) - tg(t, d, T_X, c, sj));
+            const D1 dy(ey, tg(t, d, T_Y, c, i) - tg(t, d, T_Y, c, sj));
+            const D1 r = dsqrt(dx * dx + dy * dy);
+            D1 w, dw;
+            quintic_dual(r * D1(ph.inv_h), w, dw);
+            const D1 W = D1(ph.a2) * w;
+            S += W;
+            R += D1(d.Ms[j]) * W;
+        });
+        tg(t, d, T_RHO, c, i) = R.d;
+        tg(t, d, T_VOL, c, i) = -S.d / (S.v * S.v);
+    }
+}
+
+// Fluid fields of sorted neighbour j as duals.
+struct FluidD {
+    D1 p, u, v, rho, V, mrho, dut, dvt;
+};
+__device__ __forceinline__ FluidD fluid_dual(const Dev &d, const TDev &t, int c, int j)
+{
+    const int s = d.order[j];
+    FluidD f;
+    const double2 pv = d.PV[j], rm = d.RM[j], uv = d.UV[j], duv = d.DUV[j];
+    f.p = dual(t, d, pv.x, T_P, c, s);
+    f.V = dual(t, d, pv.y, T_VOL, c, s);
+    f.rho = dual(t, d, rm.x, T_RHO, c, s);
+    f.mrho = D1(d.Ms[j]) / f.rho;
+    f.u = dual(t, d, uv.x, T_U, c, s);
+    f.v = dual(t, d, uv.y, T_V, c, s);
+    f.dut = D1(duv.x, tg(t, d, T_UT, c, s) - tg(t, d, T_U, c, s));
+    f.dvt = D1(duv.y, tg(t, d, T_VT, c, s) - tg(t, d, T_V, c, s));
+    return f;
+}
+
+// 3x3 solve with partial pivoting (pivots chosen on the values)
+__device__ bool solve3_dual(D1 (&M)[3][3], D1 (&b)[3], D1 (&x)[3])
+{
+    int piv[3] = {0, 1, 2};
+    for (int col = 0; col < 3; ++col) {
+        int p = col;
+        for (int r = col + 1; r < 3; ++r)
+            if (fabs(M[piv[r]][col].v) > fabs(M[piv[p]][col].v)) p = r;
+        const int tmp = piv[col];
+        piv[col] = piv[p];
+        piv[p] = tmp;
+        const int pr = piv[col];
+        if (M[pr][col].v == 0.0) return false;
+        for (int r = col + 1; r < 3; ++r) {
+            const int rr = piv[r];
+            const D1 f = M[rr][col] / M[pr][col];
+            for (int cc = col; cc < 3; ++cc) M[rr][cc] -= f * M[pr][cc];
+            b[rr] -= f * b[pr];
+        }
+    }
+    for (int col = 2; col >= 0; --col) {
+        const int pr = piv[col];
+        D1 s = b[pr];
+        for (int cc = col + 1; cc < 3; ++cc) s -= M[pr][cc] * x[cc];
+        x[col] = s / M[pr][col];
+    }
+    return true;
+}
+
+// ------------------------------------------------------------- walls and inlet mirror
+__global__ void t_walls_inlet(Dev d, TDev t)
+{
+    const int c = blockIdx.y;
+    const Geo &g = d.g;
+    const Phys &ph = d.ph;
+    const int nb = d.cnt->n_bnd;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        const int k = d.bnd[b];
+        const int tag = d.stag[k] & 0x7f;
+        const int s = d.order[k];
+        const double2 xy = d.XY[k];
+        const D1 Xi = dual(t, d, xy.x, T_X, c, s), Yi = dual(t, d, xy.y, T_Y, c, s);
+        if (tag == WALL || tag == SLIPWALL) {
+            const int cc = d.cellk[k];
+            D1 sw(0.0), sp(0.0), su(0.0), sv(0.0), mp(0.0), mu(0.0), mv(0.0);
+            int nf = 0;
+            t_walk(d, xy.x, xy.y, cc % g.nx, cc / g.nx, [&](int j) {
+                if ((d.stag[j] & 0x7f) != FLUID) return;
+                const int sj = d.order[j];
+                const double2 xj = d.XY[j];
+                double ex, ey;
+                exact_r2(g, xy.x, xy.y, xj.x, xj.y, ex, ey);
+                const D1 dx(ex, Xi.d - tg(t, d, T_X, c, sj)), dy(ey, Yi.d - tg(t, d, T_Y, c, sj));
+                const D1 r = dsqrt(dx * dx + dy * dy);
+                D1 w, dw;
+                quintic_dual(r * D1(ph.inv_h), w, dw);
+                const D1 W = D1(ph.a2) * w;
+                const FluidD f = fluid_dual(d, t, c, j);
+                sw += W; sp += W * f.p; su += W * f.u; sv += W * f.v;
+                mp += f.p; mu += f.u; mv += f.v;
+                ++nf;
+            });
+            const int wi = tag == WALL ? 0 : 1;
+            D1 pw(0.0), ug(ph.wall_u[wi]), vg(ph.wall_v[wi]);
+            if (nf > 0) {
+                D1 uf, vf;
+                if (sw.v > 0.0) { pw = sp / sw; uf = su / sw; vf = sv / sw; }
+                else { pw = mp / D1((double)nf); uf = mu / D1((double)nf); vf = mv / D1((double)nf); }
+                if (ph.wall_slip[wi]) { ug = uf; vg = -vf; }
+                else { ug = D1(2.0 * ph.wall_u[wi]) - uf; vg = D1(2.0 * ph.wall_v[wi]) - vf; }
+            }
+            tg(t, d, T_P, c, s) = pw.d;
+            tg(t, d, T_U, c, s) = ug.d;
+            tg(t, d, T_V, c, s) = vg.d;
+            tg(t, d, T_UT, c, s) = ug.d;
+            tg(t, d, T_VT, c, s) = vg.d;
+        } else if (tag == INLET && ph.has_inlet) {
+            // mirrored inlet pressure (Eqs. matform, taylor2) about k = (2 x_in - x_o, y_o)
+            const D1 xk = D1(2.0 * ph.x_in) - Xi, yk = Yi;
+            const int cx = cell_coord(xk.v, g.x_min, g.inv_sx, g.nx);
+            const int cy = cell_coord(yk.v, g.y_min, g.inv_sy, g.ny);
+            D1 M[3][3], bb[3], mean(0.0);
+            int nl = 0;
+            t_walk(d, xk.v, yk.v, cx, cy, [&](int l) {
+                if ((d.stag[l] & 0x7f) != FLUID) return;
+                const int sl = d.order[l];
+                const double2 xl = d.XY[l];
+                double ex, ey;
+                exact_r2(g, xl.x, xl.y, xk.v, yk.v, ex, ey);
+                const D1 xlk(ex, tg(t, d, T_X, c, sl) - xk.d), ylk(ey, tg(t, d, T_Y, c, sl) - yk.d);
+                const FluidD f = fluid_dual(d, t, c, l);
+                const D1 r2 = xlk * xlk + ylk * ylk;
+                D1 w, wx(0.0), wy(0.0);
+                if (r2.v > 1e-30) {
+                    const D1 r = dsqrt(r2);
+                    D1 wq, dwq;
+                    quintic_dual(r * D1(ph.inv_h), wq, dwq);
+                    w = D1(ph.a2) * wq;
+                    const D1 dwr = D1(ph.a2h) * dwq / r;
+                    wx = dwr * xlk;
+                    wy = dwr * ylk;
+                } else {
+                    w = D1(ph.a2 * quintic_w(0.0));
+                }
+                const D1 row[3] = {w * f.mrho, wx * f.mrho, wy * f.mrho};
+                for (int q = 0; q < 3; ++q) {
+                    M[q][0] += row[q];
+                    M[q][1] += xlk * row[q];
+                    M[q][2] += ylk * row[q];
+                    bb[q] += f.p * row[q];
+                }
+                mean += f.p;
+                ++nl;
+            });
+            D1 pk(0.0), gx(0.0), gy(0.0);
+            if (nl > 0 && !(M[0][0].v > 0.0)) {
+                pk = mean / D1((double)nl);
+            } else if (nl > 0) {
+                const double det = M[0][0].v * (M[1][1].v * M[2][2].v - M[1][2].v * M[2][1].v) -
+                                   M[0][1].v * (M[1][0].v * M[2][2].v - M[1][2].v * M[2][0].v) +
+                                   M[0][2].v * (M[1][0].v * M[2][1].v - M[1][1].v * M[2][0].v);
+                pk = bb[0] / M[0][0];
+                if (!(fabs(det) <= 1e-9 * fabs(M[0][0].v * M[1][1].v * M[2][2].v))) {
+                    D1 sol[3];
+                    if (solve3_dual(M, bb, sol)) { pk = sol[0]; gx = sol[1]; gy = sol[2]; }
+                }
+            }
+            const D1 po = pk - ((Xi - xk) * gx + (Yi - yk) * gy);
+            tg(t, d, T_P, c, s) = po.d;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------- pass B
+__global__ void t_pass_b(Dev d, TDev t)
+{
+    const int c = blockIdx.y;
+    const Phys &ph = d.ph;
+    const int n = d.cnt->n_alive;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int tag = d.stag[k] & 0x7f;
+        const bool fl = (tag == FLUID || tag == INLET);
+        const bool solid = (tag == WALL && ph.wall_drag[0]) || (tag == SLIPWALL && ph.wall_drag[1]);
+        if (!fl && !solid) continue;
+        const int i = d.order[k];
+        const double2 xy = d.XY[k];
+        const D1 Xi = dual(t, d, xy.x, T_X, c, i), Yi = dual(t, d, xy.y, T_Y, c, i);
+        const FluidD fi = fluid_dual(d, t, c, k);
+        const double mi = d.Ms[k];
+        const int N = d.snnb[k];
+        const int cc = d.cellk[k];
+        D1 ax(0.0), ay(0.0), apd(0.0), gxs(0.0), gys(0.0), sdp(0.0);
+        t_walk(d, xy.x, xy.y, cc % d.g.nx, cc / d.g.nx, [&](int j) {
+            const FluidD fj = fluid_dual(d, t, c, j);
+            const D1 dp = fj.p - fi.p;
+            sdp += dp;
+            if (solid && (d.stag[j] & 0x7f) != FLUID) return;
+            const int sj = d.order[j];
+            const double2 xj = d.XY[j];
+            double ex, ey;
+            const double r2v = exact_r2(d.g, xy.x, xy.y, xj.x, xj.y, ex, ey);
+            const D1 dx(ex, Xi.d - tg(t, d, T_X, c, sj)), dy(ey, Yi.d - tg(t, d, T_Y, c, sj));
+            const D1 r2 = dx * dx + dy * dy;
+            D1 F(0.0);
+            if (r2v > 0.0) {
+                const D1 r = dsqrt(r2);
+                D1 wq, dwq;
+                quintic_dual(r * D1(ph.inv_h), wq, dwq);
+                F = D1(ph.a2h) * dwq / r;
+            }
+            const D1 gx = F * dx, gy = F * dy, gdotr = F * r2;
+            const D1 cij = fi.V * fi.V + fj.V * fj.V;
+            const D1 inv_rs = D1(1.0) / (fi.rho + fj.rho);
+            const D1 e_ = fi.rho * dp * inv_rs;
+            const D1 hf = fi.rho * fj.rho * inv_rs * gdotr / (r2 + D1(ph.eh2));
+            const D1 vis = D1(2.0 * ph.nu) * hf;
+            const D1 uij = fi.u - fj.u, vij = fi.v - fj.v;
+            const D1 cgx = cij * gx, cgy = cij * gy;
+            gxs += cgx;
+            gys += cgy;
+            if (solid) {
+                ax += cij * (vis * uij) - e_ * cgx;
+                ay += cij * (vis * vij) - e_ * cgy;
+                return;
+            }
+            const D1 Ai = fi.rho * (fi.dut * gx + fi.dvt * gy);
+            const D1 Aj = fj.rho * (fj.dut * gx + fj.dvt * gy);
+            ax += cij * (D1(0.5) * (fi.u * Ai + fj.u * Aj) + vis * uij) - e_ * cgx;
+            ay += cij * (D1(0.5) * (fi.v * Ai + fj.v * Aj) + vis * vij) - e_ * cgy;
+            apd += fi.rho * D1(ph.c2) * fj.mrho * (uij * gx + vij * gy) -
+                   cij * D1(1.0 / mi) * D1(2.0 * ph.nu_e) * hf * dp;
+        });
+        const D1 corr = (ph.use_pavg && !solid) ? sdp / D1((double)N) : -fi.p;
+        if (solid) {
+            tg(t, d, T_FX, c, i) = (ax + corr * gxs).d;
+            tg(t, d, T_FY, c, i) = (ay + corr * gys).d;
+        } else {
+            tg(t, d, T_AU, c, i) = (ax + corr * gxs).d / mi;
+            tg(t, d, T_AV, c, i) = (ay + corr * gys).d / mi;
+            tg(t, d, T_AP, c, i) = apd.d;
+            tg(t, d, T_ABU, c, i) = -ph.pb / mi * gxs.d;
+            tg(t, d, T_ABV, c, i) = -ph.pb / mi * gys.d;
+        }
+    }
+}
+
+// --------------------------------------------------------------- hybrid outlet update
+// Runs after the tangent pass B of the end-of-step evaluation (the rates of that evaluation
+// see the outlet values of the step), reading the neighbours' previous J2p / advection
+// tangents from a snapshot.
+__global__ void t_snapshot(Dev d, TDev t)
+{
+    const int c = blockIdx.y;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.cap; s += gridDim.x * blockDim.x) {
+        tg(t, d, T_J2P_OLD, c, s) = tg(t, d, T_J2P, c, s);
+        tg(t, d, T_ADVP_OLD, c, s) = tg(t, d, T_ADVP, c, s);
+    }
+}
+
+__global__ void t_outlet(Dev d, TDev t)
+{
+    const int c = blockIdx.y;
+    const Geo &g = d.g;
+    const Phys &ph = d.ph;
+    const int nb = d.cnt->n_bnd;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        const int k = d.bnd[b];
+        if ((d.stag[k] & 0x7f) != OUTLET) continue;
+        const int s = d.order[k];
+        const double2 xy = d.XY[k];
+        const int cc = d.cellk[k];
+        D1 sw(0.0), sj(0.0), sjm(0.0), sjp(0.0), sadv(0.0);
+        int nf = 0, mr = 0;
+        const D1 Xo = dual(t, d, xy.x, T_X, c, s), Yo = dual(t, d, xy.y, T_Y, c, s);
+        t_walk(d, xy.x, xy.y, cc % g.nx, cc / g.nx, [&](int j) {
+            const uint8_t tj = d.stag[j];
+            const int sjl = d.order[j];
+            if ((tj & 0x7f) == FLUID) {
+                const double2 xj = d.XY[j];
+                double ex, ey;
+                exact_r2(g, xy.x, xy.y, xj.x, xj.y, ex, ey);
+                const D1 dx(ex, Xo.d - tg(t, d, T_X, c, sjl)), dy(ey, Yo.d - tg(t, d, T_Y, c, sjl));
+                const D1 r = dsqrt(dx * dx + dy * dy);
+                D1 w, dw;
+                quintic_dual(r * D1(ph.inv_h), w, dw);
+                const D1 W = D1(ph.a2) * w;
+                const D1 J2j = dual(t, d, d.AUX[j].x, T_J2, c, sjl);
+                sw += W; sj += W * J2j; sjm += J2j; ++nf;
+            } else if (tj == (OUTLET | TAG_REDP)) {
+                const double2 x2 = d.AUX[j];
+                sjp += dual(t, d, x2.x, T_J2P_OLD, c, sjl);
+                sadv += dual(t, d, x2.y, T_ADVP_OLD, c, sjl);
+                ++mr;
+            }
+        });
+        const bool red = nf > 0;
+        D1 J2(0.0);
+        if (red) J2 = sw.v > 0.0 ? sj / sw : sjm / D1((double)nf);
+        else if (mr > 0) J2 = sjp / D1((double)mr);
+        const D1 ub = dual(t, d, d.ubar[s], T_UBAR, c, s);
+        const D1 un = ub + J2 * D1(ph.inv_2rc);
+        const D1 adv = red ? un : (mr > 0 ? sadv / D1((double)mr) : ub);
+        tg(t, d, T_U, c, s) = un.d;
+        tg(t, d, T_V, c, s) = tg(t, d, T_VBAR, c, s);
+        tg(t, d, T_P, c, s) = tg(t, d, T_PBAR, c, s) + 0.5 * J2.d;
+        tg(t, d, T_UT, c, s) = un.d;
+        tg(t, d, T_VT, c, s) = tg(t, d, T_VBAR, c, s);
+        tg(t, d, T_J2P, c, s) = J2.d;
+        tg(t, d, T_ADVP, c, s) = adv.d;
+    }
+}
+
+// ------------------------------------------------------------------------------ stage
+template <bool CORR>
+__global__ void t_stage(Dev d, TDev t, double tau)
+{
+    const int c = blockIdx.y;
+    const Phys &ph = d.ph;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.cap; s += gridDim.x * blockDim.x) {
+        const uint8_t tag = d.tag[s];
+        if (tag == FLUID) {
+            if (!CORR) {
+                tg(t, d, T_X0, c, s) = tg(t, d, T_X, c, s);
+                tg(t, d, T_Y0, c, s) = tg(t, d, T_Y, c, s);
+                tg(t, d, T_U0, c, s) = tg(t, d, T_U, c, s);
+                tg(t, d, T_V0, c, s) = tg(t, d, T_V, c, s);
+                tg(t, d, T_P0, c, s) = tg(t, d, T_P, c, s);
+            }
+            const double un = tg(t, d, T_U0, c, s) + tau * tg(t, d, T_AU, c, s);
+            const double vn = tg(t, d, T_V0, c, s) + tau * tg(t, d, T_AV, c, s);
+            const double utn = un + tau * tg(t, d, T_ABU, c, s);
+            const double vtn = vn + tau * tg(t, d, T_ABV, c, s);
+            const double pn = tg(t, d, T_P0, c, s) + tau * tg(t, d, T_AP, c, s);
+            tg(t, d, T_U, c, s) = un;
+            tg(t, d, T_V, c, s) = vn;
+            tg(t, d, T_UT, c, s) = utn;
+            tg(t, d, T_VT, c, s) = vtn;
+            tg(t, d, T_X, c, s) = tg(t, d, T_X0, c, s) + tau * utn;
+            tg(t, d, T_Y, c, s) = tg(t, d, T_Y0, c, s) + tau * vtn;
+            tg(t, d, T_P, c, s) = pn;
+            if (CORR && ph.has_outlet && ph.outlet_kind == OUT_HYBRID) {
+                // the value kernel sampled the ring iff the gate passed on the new pressure;
+                // its write position has then moved on by one
+                const double pv = d.p[s];
+                if (pv * pv * ph.inv_2rc <= ph.I_thr) {
+                    const int kk = (d.rpos[s] + ph.n_avg - 1) % ph.n_avg;
+                    tg(t, d, T_RING + 3 * kk + 0, c, s) = un;
+                    tg(t, d, T_RING + 3 * kk + 1, c, s) = vn;
+                    tg(t, d, T_RING + 3 * kk + 2, c, s) = pn;
+                }
+                double su = 0, sv = 0, sp = 0;
+                for (int q = 0; q < ph.n_avg; ++q) {
+                    su += tg(t, d, T_RING + 3 * q + 0, c, s);
+                    sv += tg(t, d, T_RING + 3 * q + 1, c, s);
+                    sp += tg(t, d, T_RING + 3 * q + 2, c, s);
+                }
+                const double ub = su * ph.inv_navg, vb = sv * ph.inv_navg, pb = sp * ph.inv_navg;
+                tg(t, d, T_UBAR, c, s) = ub;
+                tg(t, d, T_VBAR, c, s) = vb;
+                tg(t, d, T_PBAR, c, s) = pb;
+                tg(t, d, T_J2, c, s) = ph.rho0 * ph.cs * (un - ub) + (pn - pb);
+            }
+        } else if (tag == INLET) {
+            if (!CORR) tg(t, d, T_X0, c, s) = tg(t, d, T_X, c, s);
+            const double du = c < ph.n_modes ? mode_shape(ph, c, d.y[s]) : 0.0;
+            tg(t, d, T_U, c, s) = du;
+            tg(t, d, T_V, c, s) = 0.0;
+            tg(t, d, T_UT, c, s) = du;
+            tg(t, d, T_VT, c, s) = 0.0;
+            tg(t, d, T_X, c, s) = tg(t, d, T_X0, c, s) + tau * du;
+        } else if (tag == OUTLET) {
+            if (!CORR) tg(t, d, T_X0, c, s) = tg(t, d, T_X, c, s);
+            tg(t, d, T_X, c, s) = tg(t, d, T_X0, c, s) + tau * tg(t, d, T_ADVP, c, s);
+        }
+    }
+}
+
+// -------------------------------------------------------------------------- recycling
+// Before the value kernel: the same transitions (decided on the values) applied to the
+// tangents: fluid -> outlet keeps its time averages (hybrid) or freezes its values; inlet ->
+// fluid fills its ring with its values.
+__global__ void t_recycle_pre(Dev d, TDev t)
+{
+    const int c = blockIdx.y;
+    const Phys &ph = d.ph;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.cap; s += gridDim.x * blockDim.x) {
+        const uint8_t tag = d.tag[s];
+        if (tag == FLUID && ph.has_outlet && d.x[s] >= ph.x_out) {
+            if (ph.outlet_kind == OUT_HYBRID) {
+                tg(t, d, T_U, c, s) = tg(t, d, T_UBAR, c, s);
+                tg(t, d, T_V, c, s) = tg(t, d, T_VBAR, c, s);
+                tg(t, d, T_P, c, s) = tg(t, d, T_PBAR, c, s);
+            } else {
+                tg(t, d, T_UBAR, c, s) = tg(t, d, T_U, c, s);
+                tg(t, d, T_VBAR, c, s) = tg(t, d, T_V, c, s);
+                tg(t, d, T_PBAR, c, s) = tg(t, d, T_P, c, s);
+            }
+            tg(t, d, T_UT, c, s) = tg(t, d, T_UBAR, c, s);
+            tg(t, d, T_VT, c, s) = tg(t, d, T_VBAR, c, s);
+            tg(t, d, T_J2P, c, s) = 0.0;
+            tg(t, d, T_ADVP, c, s) = tg(t, d, T_UBAR, c, s);
+        } else if (tag == INLET && ph.has_inlet && d.x[s] >= ph.x_in) {
+            const double du = tg(t, d, T_U, c, s), dv = tg(t, d, T_V, c, s), dp = tg(t, d, T_P, c, s);
+            for (int q = 0; q < ph.n_avg; ++q) {
+                tg(t, d, T_RING + 3 * q + 0, c, s) = du;
+                tg(t, d, T_RING + 3 * q + 1, c, s) = dv;
+                tg(t, d, T_RING + 3 * q + 2, c, s) = dp;
+            }
+            tg(t, d, T_UBAR, c, s) = du;
+            tg(t, d, T_VBAR, c, s) = dv;
+            tg(t, d, T_PBAR, c, s) = dp;
+            tg(t, d, T_J2, c, s) = 0.0;
+        }
+    }
+}
+
+// After the value kernel: the new inlet particles (parent p -> slot s, recorded by
+// k_end_step) take x - L_in and p of the parent and the inlet profile's mode shapes; every
+// other tangent of the slot starts at zero.  Then the drag tangents of the step.
+__global__ void __launch_bounds__(1024) t_recycle_post(Dev d, TDev t)
+{
+    __shared__ double sh[2][1024];
+    const int c = blockIdx.y;
+    const Phys &ph = d.ph;
+    const Counters *C = d.cnt;
+    const int ns = C->last_spawn;
+    for (int r = threadIdx.x; r < ns; r += blockDim.x) {
+        const int2 m = d.spawn_map[r];
+        const int ps = m.x, s = m.y;
+        for (int f = 0; f < T_NF; ++f) tg(t, d, f, c, s) = 0.0;
+        tg(t, d, T_X, c, s) = tg(t, d, T_X, c, ps);
+        tg(t, d, T_Y, c, s) = tg(t, d, T_Y, c, ps);
+        tg(t, d, T_P, c, s) = tg(t, d, T_P, c, ps);
+        const double du = c < ph.n_modes ? mode_shape(ph, c, d.y[s]) : 0.0;
+        tg(t, d, T_U, c, s) = du;
+        tg(t, d, T_UT, c, s) = du;
+    }
+    double fx = 0.0, fy = 0.0;
+    for (int i = threadIdx.x; i < C->n_drag; i += blockDim.x) {
+        const int s = d.drag_slots[i];
+        fx += tg(t, d, T_FX, c, s);
+        fy += tg(t, d, T_FY, c, s);
+    }
+    sh[0][threadIdx.x] = fx;
+    sh[1][threadIdx.x] = fy;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int slot = (C->step - 1 + d.max_history) % d.max_history;
+        t.hist[((size_t)slot * 2 + 0) * T_DIR + c] = sh[0][0];
+        t.hist[((size_t)slot * 2 + 1) * T_DIR + c] = sh[1][0];
+    }
+}
+
+// Set-up: every tangent zero but the inlet particles' velocity (the mode shapes).
+__global__ void t_init(Dev d, TDev t)
+{
+    const int c = blockIdx.y;
+    const Phys &ph = d.ph;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.cap; s += gridDim.x * blockDim.x) {
+        for (int f = 0; f < T_NF; ++f) tg(t, d, f, c, s) = 0.0;
+        if (d.tag[s] == INLET) {
+            const double du = c < ph.n_modes ? mode_shape(ph, c, d.y[s]) : 0.0;
+            tg(t, d, T_U, c, s) = du;
+            tg(t, d, T_UT, c, s) = du;
+        }
+    }
+}
+
+TDev tdev_of(const Dev &d, void *ws)
+{
+    TDev t;
+    double *p = (double *)ws;
+    for (int f = 0; f < T_NF; ++f) {
+        t.f[f] = p;
+        p += (size_t)T_DIR * d.cap;
+    }
+    t.hist = p;
+    t.ndir = T_DIR;
+    return t;
+}
+
+dim3 tgrid(int n)
+{
+    int b = (n + 127) / 128;
+    b = b < 1 ? 1 : (b > 4096 ? 4096 : b);
+    return dim3((unsigned)b, T_DIR);
+}
+
+}  // namespace
+
+size_t tangent_bytes(const Dev &d)
+{
+    return sizeof(double) * ((size_t)T_NF * T_DIR * d.cap + (size_t)d.max_history * 2 * T_DIR);
+}
+
+int launch_tangent(const Dev &d, void *ws, cudaStream_t s, int what, double tau)
+{
+    const TDev t = tdev_of(d, ws);
+    switch (what) {
+    case TG_INIT: t_init<<<tgrid(d.cap), 128, 0, s>>>(d, t); return 1;
+    case TG_PASS_A: t_pass_a<<<tgrid(d.cap), 128, 0, s>>>(d, t); return 1;
+    case TG_BOUNDARY: t_walls_inlet<<<tgrid(d.cap / 8 + 1), 128, 0, s>>>(d, t); return 1;
+    case TG_PASS_B: t_pass_b<<<tgrid(d.cap), 128, 0, s>>>(d, t); return 1;
+    case TG_OUTLET:
+        t_snapshot<<<tgrid(d.cap), 128, 0, s>>>(d, t);
+        t_outlet<<<tgrid(d.cap / 8 + 1), 128, 0, s>>>(d, t);
+        return 2;
+    case TG_STAGE_PRED: t_stage<false><<<tgrid(d.cap), 128, 0, s>>>(d, t, tau); return 1;
+    case TG_STAGE_CORR: t_stage<true><<<tgrid(d.cap), 128, 0, s>>>(d, t, tau); return 1;
+    case TG_RECYCLE_PRE: t_recycle_pre<<<tgrid(d.cap), 128, 0, s>>>(d, t); return 1;
+    case TG_RECYCLE_POST: t_recycle_post<<<dim3(1, T_DIR), 1024, 0, s>>>(d, t); return 1;
+    default: return 0;
+    }
+}
+
+}  // namespace edac
