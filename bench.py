@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--batch-channels", type=int, default=64,
                     help="uneven channels of the batched measurement (0: skip it)")
     ap.add_argument("--batch-steps", type=int, default=200)
-    ap.add_argument("--tangent-steps", type=int, default=100,
+    ap.add_argument("--tangent-steps", type=int, default=400,
                     help="steps of the gradient workload (0: skip it)")
     return ap.parse_args()
 

@@ -27,15 +27,16 @@ __device__ __forceinline__ D1 operator-(D1 a) { return D1(-a.v, -a.d); }
 __device__ __forceinline__ D1 operator*(D1 a, D1 b) { return D1(a.v * b.v, a.d * b.v + a.v * b.d); }
 __device__ __forceinline__ D1 operator/(D1 a, D1 b)
 {
-    const double q = a.v / b.v;
-    return D1(q, (a.d - q * b.d) / b.v);
+    const double r = 1.0 / b.v;
+    const double q = a.v * r;
+    return D1(q, (a.d - q * b.d) * r);
 }
 __device__ __forceinline__ D1 &operator+=(D1 &a, D1 b) { a = a + b; return a; }
 __device__ __forceinline__ D1 &operator-=(D1 &a, D1 b) { a = a - b; return a; }
 __device__ __forceinline__ D1 dsqrt(D1 a)
 {
     const double s = sqrt(a.v);
-    return D1(s, s > 0.0 ? 0.5 * a.d / s : 0.0);
+    return D1(s, s > 0.0 ? (0.5 * a.d) * (1.0 / s) : 0.0);
 }
 
 // quintic spline w(q), w'(q) with their derivatives along q (w'' for the derivative of w')
@@ -75,17 +76,20 @@ __device__ __forceinline__ double mode_shape(const Phys &ph, int c, double y)
     return sin((double)(c + 1) * 3.141592653589793 * (y - ph.in_y0) / ph.in_H);
 }
 
-// Walk the fluid-or-all neighbours of sorted particle k / of a point, exact fp64 test
+// Walk the neighbours of the point (qx, qy) in cell (cx, cy): the membership test of the
+// value kernels (fp32 pre-test on cell-relative coordinates, the fp64 test in the band), so
+// the tangent kernels visit exactly the neighbours the value kernels did.
 template <class F>
 __device__ __forceinline__ void t_walk(const Dev &d, double qx, double qy, int cx, int cy, F &&f)
 {
     const Geo &g = d.g;
-    for_block(d, cx, cy, [&](int, int, int j0, int j1) {
+    const float rx = (float)(qx - (g.x_min + (double)cx * g.sx));
+    const float ry = (float)(qy - (g.y_min + (double)cy * g.sy));
+    for_block(d, cx, cy, [&](int ox, int oy, int j0, int j1) {
+        const float rxo = rx - (float)ox * g.sxf, ryo = ry - (float)oy * g.syf;
         for (int j = j0; j < j1; ++j) {
-            const double2 xy = d.XY[j];
-            double dx, dy;
-            const double r2 = exact_r2(g, qx, qy, xy.x, xy.y, dx, dy);
-            if (r2 < g.rc2) f(j);
+            float dxf, dyf, r2f;
+            if (is_member(d, rxo, ryo, __ldg(d.P + j), j, qx, qy, dxf, dyf, r2f)) f(j);
         }
     });
 }
