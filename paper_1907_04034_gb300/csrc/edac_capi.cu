@@ -944,7 +944,7 @@ edac_status edac_read_tangent_history(edac_ctx *ctx, int max_steps, double *h_df
     CK(cudaMemcpyAsync(&h, ctx->d.cnt, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     const int H = ctx->d.max_history;
     std::vector<double> hist((size_t)H * 2 * T_DIR);
-    const double *dev_hist = (const double *)ctx->tws + (size_t)T_NF * T_DIR * ctx->d.cap;
+    const double *dev_hist = tangent_hist(ctx->d, ctx->tws);
     CK(cudaMemcpyAsync(hist.data(), dev_hist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));

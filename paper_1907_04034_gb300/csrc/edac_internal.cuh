@@ -315,6 +315,7 @@ enum : int {
 enum : int { TG_INIT, TG_PASS_A, TG_BOUNDARY, TG_PASS_B, TG_OUTLET, TG_STAGE_PRED, TG_STAGE_CORR,
              TG_RECYCLE_PRE, TG_RECYCLE_POST };
 size_t tangent_bytes(const Dev &d);
+const double *tangent_hist(const Dev &d, const void *ws);
 int launch_tangent(const Dev &d, void *ws, cudaStream_t s, int what, double tau);
 int launch_pass_a(const Dev &d, cudaStream_t s, int mixed);
 int launch_boundary(const Dev &d, cudaStream_t s, int mixed, int end_of_step);

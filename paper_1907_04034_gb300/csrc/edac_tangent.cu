@@ -5,10 +5,12 @@
 // recycling events those values produce held fixed).
 //
 // Each tangent kernel follows the value kernel it differentiates (same formulas, same
-// neighbour walk, same branch decisions, taken on the values) in dual numbers D1 = value +
-// one derivative; blockIdx.y is the direction (mode) k.  Tangents are slot-indexed,
-// [field][direction][capacity] fp64, in a workspace of their own.  The value kernels run
-// unchanged; the tangent kernels are interleaved after them (see edac_step_tangent).
+// neighbour walk, same branch decisions, taken on the values) in dual numbers = value + one
+// derivative; blockIdx.y is the direction (mode) k.  The pair passes, which dominate, use
+// fp32 duals (F1) on the fp32 pipe; the boundary parts (walls, the mirrored inlet's 3x3
+// solve, the outlet) fp64 duals (D1).  Tangents are slot-indexed, [field][direction]
+// [capacity] fp32, in a workspace of their own.  The value kernels run unchanged; the tangent
+// kernels are interleaved after them (see edac_step_tangent).
 #include "edac_internal.cuh"
 
 namespace edac {
@@ -55,19 +57,22 @@ __device__ __forceinline__ void quintic_dual(D1 q, D1 &w, D1 &dw)
 
 // ------------------------------------------------------------------ tangent storage
 struct TDev {
-    double *f[T_NF];  // [direction][capacity] per field
+    float *f[T_NF];   // [direction][capacity] per field (fp32: derivatives carry ~1e-7
+                      // relative rounding, far below the accuracy asked of the gradient)
     double *hist;     // [max_history][2][T_DIR]: d(F_x), d(F_y)
+    float4 *vf;       // [capacity] fp32 copies (p, V, rho, m/rho) by sorted index
+    float4 *vg;       // [capacity] fp32 copies (u, v, u~ - u, v~ - v) by sorted index
     int ndir;         // directions in use (modes)
 };
 
-__device__ __forceinline__ double &tg(const TDev &t, const Dev &d, int f, int c, int s)
+__device__ __forceinline__ float &tg(const TDev &t, const Dev &d, int f, int c, int s)
 {
     return t.f[f][(size_t)c * d.cap + s];
 }
 
 __device__ __forceinline__ D1 dual(const TDev &t, const Dev &d, double v, int f, int c, int s)
 {
-    return D1(v, t.f[f][(size_t)c * d.cap + s]);
+    return D1(v, (double)t.f[f][(size_t)c * d.cap + s]);
 }
 
 // sin(k pi (y - y0)/H): the derivative of the inlet velocity with respect to mode k
@@ -92,37 +97,6 @@ __device__ __forceinline__ void t_walk(const Dev &d, double qx, double qy, int c
             if (is_member(d, rxo, ryo, __ldg(d.P + j), j, qx, qy, dxf, dyf, r2f)) f(j);
         }
     });
-}
-
-// ---------------------------------------------------------------------------- pass A
-// S_i = sum_j W_ij, rho_i = sum_j m_j W_ij, V_i = 1/S_i (self included).
-__global__ void t_pass_a(Dev d, TDev t)
-{
-    const int c = blockIdx.y;
-    const int n = d.cnt->n_alive;
-    const Phys &ph = d.ph;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int i = d.order[k];
-        const double2 xi = d.XY[k];
-        const int cc = d.cellk[k];
-        D1 S(0.0), R(0.0);
-        t_walk(d, xi.x, xi.y, cc % d.g.nx, cc / d.g.nx, [&](int j) {
-            const int sj = d.order[j];
-            const double2 xj = d.XY[j];
-            double ex, ey;
-            exact_r2(d.g, xi.x, xi.y, xj.x, xj.y, ex, ey);  // minimum-image separation
-            const D1 dx(ex, tg(t, d, T_X, c, i) - tg(t, d, T_X, c, sj));
-            const D1 dy(ey, tg(t, d, T_Y, c, i) - tg(t, d, T_Y, c, sj));
-            const D1 r = dsqrt(dx * dx + dy * dy);
-            D1 w, dw;
-            quintic_dual(r * D1(ph.inv_h), w, dw);
-            const D1 W = D1(ph.a2) * w;
-            S += W;
-            R += D1(d.Ms[j]) * W;
-        });
-        tg(t, d, T_RHO, c, i) = R.d;
-        tg(t, d, T_VOL, c, i) = -S.d / (S.v * S.v);
-    }
 }
 
 // Fluid fields of sorted neighbour j as duals.
@@ -274,79 +248,6 @@ __global__ void t_walls_inlet(Dev d, TDev t)
             }
             const D1 po = pk - ((Xi - xk) * gx + (Yi - yk) * gy);
             tg(t, d, T_P, c, s) = po.d;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------- pass B
-__global__ void t_pass_b(Dev d, TDev t)
-{
-    const int c = blockIdx.y;
-    const Phys &ph = d.ph;
-    const int n = d.cnt->n_alive;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int tag = d.stag[k] & 0x7f;
-        const bool fl = (tag == FLUID || tag == INLET);
-        const bool solid = (tag == WALL && ph.wall_drag[0]) || (tag == SLIPWALL && ph.wall_drag[1]);
-        if (!fl && !solid) continue;
-        const int i = d.order[k];
-        const double2 xy = d.XY[k];
-        const D1 Xi = dual(t, d, xy.x, T_X, c, i), Yi = dual(t, d, xy.y, T_Y, c, i);
-        const FluidD fi = fluid_dual(d, t, c, k);
-        const double mi = d.Ms[k];
-        const int N = d.snnb[k];
-        const int cc = d.cellk[k];
-        D1 ax(0.0), ay(0.0), apd(0.0), gxs(0.0), gys(0.0), sdp(0.0);
-        t_walk(d, xy.x, xy.y, cc % d.g.nx, cc / d.g.nx, [&](int j) {
-            const FluidD fj = fluid_dual(d, t, c, j);
-            const D1 dp = fj.p - fi.p;
-            sdp += dp;
-            if (solid && (d.stag[j] & 0x7f) != FLUID) return;
-            const int sj = d.order[j];
-            const double2 xj = d.XY[j];
-            double ex, ey;
-            const double r2v = exact_r2(d.g, xy.x, xy.y, xj.x, xj.y, ex, ey);
-            const D1 dx(ex, Xi.d - tg(t, d, T_X, c, sj)), dy(ey, Yi.d - tg(t, d, T_Y, c, sj));
-            const D1 r2 = dx * dx + dy * dy;
-            D1 F(0.0);
-            if (r2v > 0.0) {
-                const D1 r = dsqrt(r2);
-                D1 wq, dwq;
-                quintic_dual(r * D1(ph.inv_h), wq, dwq);
-                F = D1(ph.a2h) * dwq / r;
-            }
-            const D1 gx = F * dx, gy = F * dy, gdotr = F * r2;
-            const D1 cij = fi.V * fi.V + fj.V * fj.V;
-            const D1 inv_rs = D1(1.0) / (fi.rho + fj.rho);
-            const D1 e_ = fi.rho * dp * inv_rs;
-            const D1 hf = fi.rho * fj.rho * inv_rs * gdotr / (r2 + D1(ph.eh2));
-            const D1 vis = D1(2.0 * ph.nu) * hf;
-            const D1 uij = fi.u - fj.u, vij = fi.v - fj.v;
-            const D1 cgx = cij * gx, cgy = cij * gy;
-            gxs += cgx;
-            gys += cgy;
-            if (solid) {
-                ax += cij * (vis * uij) - e_ * cgx;
-                ay += cij * (vis * vij) - e_ * cgy;
-                return;
-            }
-            const D1 Ai = fi.rho * (fi.dut * gx + fi.dvt * gy);
-            const D1 Aj = fj.rho * (fj.dut * gx + fj.dvt * gy);
-            ax += cij * (D1(0.5) * (fi.u * Ai + fj.u * Aj) + vis * uij) - e_ * cgx;
-            ay += cij * (D1(0.5) * (fi.v * Ai + fj.v * Aj) + vis * vij) - e_ * cgy;
-            apd += fi.rho * D1(ph.c2) * fj.mrho * (uij * gx + vij * gy) -
-                   cij * D1(1.0 / mi) * D1(2.0 * ph.nu_e) * hf * dp;
-        });
-        const D1 corr = (ph.use_pavg && !solid) ? sdp / D1((double)N) : -fi.p;
-        if (solid) {
-            tg(t, d, T_FX, c, i) = (ax + corr * gxs).d;
-            tg(t, d, T_FY, c, i) = (ay + corr * gys).d;
-        } else {
-            tg(t, d, T_AU, c, i) = (ax + corr * gxs).d / mi;
-            tg(t, d, T_AV, c, i) = (ay + corr * gys).d / mi;
-            tg(t, d, T_AP, c, i) = apd.d;
-            tg(t, d, T_ABU, c, i) = -ph.pb / mi * gxs.d;
-            tg(t, d, T_ABV, c, i) = -ph.pb / mi * gys.d;
         }
     }
 }
@@ -580,15 +481,203 @@ __global__ void t_init(Dev d, TDev t)
     }
 }
 
+// ------------------------------------------------- fp32 pair tangents (passes A and B)
+// The pair passes dominate the tangent step; their derivative arithmetic runs in fp32 duals
+// on the fp32 pipe (GB300's fp64 pipe is 1/76 of it).  Values come from fp32 copies of the
+// fp64 fields (t_prep), separations from the cell-relative fp32 coordinates of the membership
+// test, and the differences that cancel (p_j - p_i, u_i - u_j, v_i - v_j) from the fp64
+// values, rounded once.
+struct F1 {
+    float v, d;
+    __device__ F1() : v(0.0f), d(0.0f) {}
+    __device__ F1(float a) : v(a), d(0.0f) {}
+    __device__ F1(float a, float b) : v(a), d(b) {}
+};
+__device__ __forceinline__ F1 operator+(F1 a, F1 b) { return F1(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ F1 operator-(F1 a, F1 b) { return F1(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ F1 operator-(F1 a) { return F1(-a.v, -a.d); }
+__device__ __forceinline__ F1 operator*(F1 a, F1 b) { return F1(a.v * b.v, fmaf(a.d, b.v, a.v * b.d)); }
+__device__ __forceinline__ F1 operator/(F1 a, F1 b)
+{
+    const float r = 1.0f / b.v;
+    const float q = a.v * r;
+    return F1(q, (a.d - q * b.d) * r);
+}
+__device__ __forceinline__ F1 &operator+=(F1 &a, F1 b) { a = a + b; return a; }
+
+__device__ __forceinline__ void quintic_dual_f(F1 q, F1 &w, F1 &dw)
+{
+    const float t3 = q.v < 3.0f ? 3.0f - q.v : 0.0f;
+    const float t2 = q.v < 2.0f ? 2.0f - q.v : 0.0f;
+    const float t1 = q.v < 1.0f ? 1.0f - q.v : 0.0f;
+    const float a = t3 * t3, b = t2 * t2, c = t1 * t1;
+    const float wv = t3 * a * a - 6.0f * (t2 * b * b) + 15.0f * (t1 * c * c);
+    const float w1 = -5.0f * (a * a - 6.0f * b * b + 15.0f * c * c);
+    const float w2 = 20.0f * (t3 * a - 6.0f * (t2 * b) + 15.0f * (t1 * c));
+    w = F1(wv, w1 * q.d);
+    dw = F1(w1, w2 * q.d);
+}
+
+// fp32 copies of the fields the pair tangents read, by sorted index (after the value boundary
+// kernel, so that wall and inlet pressures are the ones pass B uses)
+__global__ void t_prep(Dev d, TDev t)
+{
+    const int n = d.cnt->n_alive;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const double2 pv = d.PV[k], rm = d.RM[k], uv = d.UV[k], duv = d.DUV[k];
+        t.vf[k] = make_float4((float)pv.x, (float)pv.y, (float)rm.x, (float)rm.y);
+        t.vg[k] = make_float4((float)uv.x, (float)uv.y, (float)duv.x, (float)duv.y);
+    }
+}
+
+// Neighbours of sorted particle k with the membership test of the value kernels; f(j, dx, dy,
+// r2) with the fp32 separation r_k - r_j.
+template <class F>
+__device__ __forceinline__ void t_walk_f(const Dev &d, int k, double qx, double qy, F &&f)
+{
+    const Geo &g = d.g;
+    const int cc = d.cellk[k];
+    const float4 pk = d.P[k];
+    for_block(d, cc % g.nx, cc / g.nx, [&](int ox, int oy, int j0, int j1) {
+        const float rxo = pk.x - (float)ox * g.sxf, ryo = pk.y - (float)oy * g.syf;
+        for (int j = j0; j < j1; ++j) {
+            float dxf, dyf, r2f;
+            if (is_member(d, rxo, ryo, __ldg(d.P + j), j, qx, qy, dxf, dyf, r2f)) f(j, dxf, dyf, r2f);
+        }
+    });
+}
+
+__global__ void t_pass_a_f(Dev d, TDev t)
+{
+    const int c = blockIdx.y;
+    const int n = d.cnt->n_alive;
+    const Phys &ph = d.ph;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int i = d.order[k];
+        const double2 xi = d.XY[k];
+        const float tx = tg(t, d, T_X, c, i), ty = tg(t, d, T_Y, c, i);
+        float dS = 0.0f, dR = 0.0f;
+        t_walk_f(d, k, xi.x, xi.y, [&](int j, float dx, float dy, float r2) {
+            if (!(r2 > 0.0f)) return;  // self: W(0), no derivative
+            const int sj = d.order[j];
+            const float ddx = tx - tg(t, d, T_X, c, sj), ddy = ty - tg(t, d, T_Y, c, sj);
+            const float r = sqrtf(r2);
+            const float dr = fmaf(dx, ddx, dy * ddy) / r;
+            const float dwq = quintic_dw(r * ph.inv_hf);
+            const float dW = ph.a2hf * dwq * dr;
+            dS += dW;
+            dR = fmaf(__ldg(d.P + j).z, dW, dR);
+        });
+        const double V = d.PV[k].y;
+        tg(t, d, T_RHO, c, i) = dR;
+        tg(t, d, T_VOL, c, i) = (float)(-(double)dS * V * V);
+    }
+}
+
+struct FluidF {
+    F1 p, u, v, rho, V, mrho, dut, dvt;
+};
+__device__ __forceinline__ FluidF fluid_f(const Dev &d, const TDev &t, int c, int j)
+{
+    const int s = d.order[j];
+    const float4 a = t.vf[j], b = t.vg[j];
+    FluidF f;
+    f.p = F1(a.x, tg(t, d, T_P, c, s));
+    f.V = F1(a.y, tg(t, d, T_VOL, c, s));
+    f.rho = F1(a.z, tg(t, d, T_RHO, c, s));
+    f.mrho = F1(a.w, -a.w * f.rho.d / a.z);  // d(m/rho) = -(m/rho) drho / rho
+    const float tu = tg(t, d, T_U, c, s), tv = tg(t, d, T_V, c, s);
+    f.u = F1(b.x, tu);
+    f.v = F1(b.y, tv);
+    f.dut = F1(b.z, tg(t, d, T_UT, c, s) - tu);
+    f.dvt = F1(b.w, tg(t, d, T_VT, c, s) - tv);
+    return f;
+}
+
+__global__ void t_pass_b_f(Dev d, TDev t)
+{
+    const int c = blockIdx.y;
+    const Phys &ph = d.ph;
+    const int n = d.cnt->n_alive;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int tag = d.stag[k] & 0x7f;
+        const bool fl = (tag == FLUID || tag == INLET);
+        const bool solid = (tag == WALL && ph.wall_drag[0]) || (tag == SLIPWALL && ph.wall_drag[1]);
+        if (!fl && !solid) continue;
+        const int i = d.order[k];
+        const double2 xy = d.XY[k];
+        const double2 pvi = d.PV[k], uvi = d.UV[k];
+        const float tx = tg(t, d, T_X, c, i), ty = tg(t, d, T_Y, c, i);
+        const FluidF fi = fluid_f(d, t, c, k);
+        const float mi_inv = 1.0f / (float)d.Ms[k];
+        const int N = d.snnb[k];
+        F1 ax, ay, apd, gxs, gys, sdp;
+        t_walk_f(d, k, xy.x, xy.y, [&](int j, float dxf, float dyf, float r2f) {
+            const FluidF fj = fluid_f(d, t, c, j);
+            const double2 pvj = d.PV[j];
+            const F1 dp((float)(pvj.x - pvi.x), fj.p.d - fi.p.d);
+            sdp += dp;
+            if (solid && (d.stag[j] & 0x7f) != FLUID) return;
+            const int sj = d.order[j];
+            const F1 dx(dxf, tx - tg(t, d, T_X, c, sj)), dy(dyf, ty - tg(t, d, T_Y, c, sj));
+            const F1 r2 = F1(r2f, 2.0f * fmaf(dxf, dx.d, dyf * dy.d));
+            F1 F(0.0f);
+            if (r2f > 0.0f) {
+                const float r = sqrtf(r2f);
+                const F1 rr(r, r2.d * 0.5f / r);
+                F1 wq, dwq;
+                quintic_dual_f(rr * F1(ph.inv_hf), wq, dwq);
+                F = F1(ph.a2hf) * dwq / rr;
+            }
+            const F1 gx = F * dx, gy = F * dy, gdotr = F * r2;
+            const F1 cij = fi.V * fi.V + fj.V * fj.V;
+            const F1 inv_rs = F1(1.0f) / (fi.rho + fj.rho);
+            const F1 e_ = fi.rho * dp * inv_rs;
+            const F1 hf = fi.rho * fj.rho * inv_rs * gdotr / (r2 + F1(ph.eh2f));
+            const F1 vis = F1(2.0f * ph.nuf) * hf;
+            const double2 uvj = d.UV[j];
+            const F1 uij((float)(uvi.x - uvj.x), fi.u.d - fj.u.d);
+            const F1 vij((float)(uvi.y - uvj.y), fi.v.d - fj.v.d);
+            const F1 cgx = cij * gx, cgy = cij * gy;
+            gxs += cgx;
+            gys += cgy;
+            if (solid) {
+                ax += cij * (vis * uij) - e_ * cgx;
+                ay += cij * (vis * vij) - e_ * cgy;
+                return;
+            }
+            const F1 Ai = fi.rho * (fi.dut * gx + fi.dvt * gy);
+            const F1 Aj = fj.rho * (fj.dut * gx + fj.dvt * gy);
+            ax += cij * (F1(0.5f) * (fi.u * Ai + fj.u * Aj) + vis * uij) - e_ * cgx;
+            ay += cij * (F1(0.5f) * (fi.v * Ai + fj.v * Aj) + vis * vij) - e_ * cgy;
+            apd += fi.rho * F1(ph.c2f) * fj.mrho * (uij * gx + vij * gy) -
+                   cij * F1(mi_inv * 2.0f * ph.nuef) * hf * dp;
+        });
+        const F1 corr = (ph.use_pavg && !solid) ? sdp / F1((float)N) : -F1((float)pvi.x, fi.p.d);
+        if (solid) {
+            tg(t, d, T_FX, c, i) = (ax + corr * gxs).d;
+            tg(t, d, T_FY, c, i) = (ay + corr * gys).d;
+        } else {
+            tg(t, d, T_AU, c, i) = (ax + corr * gxs).d * mi_inv;
+            tg(t, d, T_AV, c, i) = (ay + corr * gys).d * mi_inv;
+            tg(t, d, T_AP, c, i) = apd.d;
+            tg(t, d, T_ABU, c, i) = -ph.pbf * mi_inv * gxs.d;
+            tg(t, d, T_ABV, c, i) = -ph.pbf * mi_inv * gys.d;
+        }
+    }
+}
+
 TDev tdev_of(const Dev &d, void *ws)
 {
     TDev t;
-    double *p = (double *)ws;
+    float *p = (float *)ws;
     for (int f = 0; f < T_NF; ++f) {
         t.f[f] = p;
         p += (size_t)T_DIR * d.cap;
     }
-    t.hist = p;
+    t.hist = (double *)p;  // T_DIR * cap floats per field: a multiple of 8 bytes
+    t.vf = (float4 *)(((uintptr_t)(t.hist + (size_t)d.max_history * 2 * T_DIR) + 15) & ~(uintptr_t)15);
+    t.vg = t.vf + d.cap;
     t.ndir = T_DIR;
     return t;
 }
@@ -604,7 +693,13 @@ dim3 tgrid(int n)
 
 size_t tangent_bytes(const Dev &d)
 {
-    return sizeof(double) * ((size_t)T_NF * T_DIR * d.cap + (size_t)d.max_history * 2 * T_DIR);
+    return sizeof(float) * (size_t)T_NF * T_DIR * d.cap + sizeof(double) * (size_t)d.max_history * 2 * T_DIR +
+           16 + 2 * sizeof(float4) * (size_t)d.cap;
+}
+
+const double *tangent_hist(const Dev &d, const void *ws)
+{
+    return tdev_of(d, const_cast<void *>(ws)).hist;
 }
 
 int launch_tangent(const Dev &d, void *ws, cudaStream_t s, int what, double tau)
@@ -612,9 +707,12 @@ int launch_tangent(const Dev &d, void *ws, cudaStream_t s, int what, double tau)
     const TDev t = tdev_of(d, ws);
     switch (what) {
     case TG_INIT: t_init<<<tgrid(d.cap), 128, 0, s>>>(d, t); return 1;
-    case TG_PASS_A: t_pass_a<<<tgrid(d.cap), 128, 0, s>>>(d, t); return 1;
+    case TG_PASS_A: t_pass_a_f<<<tgrid(d.cap), 128, 0, s>>>(d, t); return 1;
     case TG_BOUNDARY: t_walls_inlet<<<tgrid(d.cap / 8 + 1), 128, 0, s>>>(d, t); return 1;
-    case TG_PASS_B: t_pass_b<<<tgrid(d.cap), 128, 0, s>>>(d, t); return 1;
+    case TG_PASS_B:
+        t_prep<<<tgrid(d.cap).x, 128, 0, s>>>(d, t);
+        t_pass_b_f<<<tgrid(d.cap), 128, 0, s>>>(d, t);
+        return 2;
     case TG_OUTLET:
         t_snapshot<<<tgrid(d.cap), 128, 0, s>>>(d, t);
         t_outlet<<<tgrid(d.cap / 8 + 1), 128, 0, s>>>(d, t);
