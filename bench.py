@@ -255,7 +255,8 @@ def run_tangent(steps, dev):
     gf, same = gradient.central_differences(c, a, steps, eps=1e-6, modes=[0], device=str(dev))
     return {"workload": f"cylinder Re=200, dx=D/25 ({c.n} particles), 8 inlet modes "
                         f"a_k ~ N(0, 0.02) seed 0, mean c_d over {steps} steps",
-            "method": "tangent-linear model of the fp64 step (forward mode, 8 directions)",
+            "method": "tangent-linear model of the fp64 step (forward mode, 8 directions; "
+                      "fp32 pair tangents, fp64 boundary tangents)",
             "loss": L, "dL_da": [float(v) for v in g],
             "tangent_s": tm["tangent_s"], "forward_s": fwd_ms / 1e3,
             "tangent_over_forward": tm["tangent_s"] / (fwd_ms / 1e3),
