@@ -513,41 +513,63 @@ __device__ __forceinline__ void global_neighbors(const Dev &d, int k, const floa
     fold();
 }
 
-// Phase 1 of pass A: walk the candidate order of particle ti (CandRows) and return the
-// 128-bit mask of its neighbours (itself included); only for cr.tot <= 128.  The loop over the
-// candidates is fp32 only: it sets a tentative bit (r2 below the upper band edge) and a band bit
-// (r2 above the lower edge); the fp64 test then settles the few band candidates, so the fp64
-// work stays out of the candidate loop (a predicated fp64 test would issue for every candidate).
-__device__ __forceinline__ uint4 tile_mask(const Dev &d, const float2 *spos, const int *sgj,
-                                           const CandRows &cr, int ti, double qx, double qy)
+// Phase 1 of pass A: walk the candidate order of particle ti (the three cell rows of its 3 x 3
+// block, CandRows) and return the 128-bit mask of its neighbours (itself included); only for
+// cr.tot <= 128.  The loop walks each row's shared-memory range directly, sets a tentative
+// bit (r2 below the upper band edge) and a band bit (r2 above the lower edge) at the running
+// candidate index, and files the 32-bit words as they fill; the fp64 test then settles the
+// few band candidates after the loop, so the fp64 work stays out of the candidate loop (a
+// predicated fp64 test would issue for every candidate).
+__device__ __forceinline__ uint4 tile_mask(const Dev &d, const TileHdr &th, const float2 *spos,
+                                           const int *sgj, const CandRows &cr, int ti, int vi,
+                                           double qx, double qy)
 {
     const float2 pi = spos[ti];
     const float hi2 = d.g.rc2_hi, lo2 = d.g.rc2_lo;
-    unsigned w[4];
+    unsigned w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u, b0 = 0u, b1 = 0u, b2 = 0u, b3 = 0u;
+    unsigned cur = 0u, bcur = 0u, bit = 1u;
+    int q = 0;
+    auto file = [&]() {  // the filled word goes to word q
+        w0 = q == 0 ? cur : w0; w1 = q == 1 ? cur : w1; w2 = q == 2 ? cur : w2; w3 = q == 3 ? cur : w3;
+        b0 = q == 0 ? bcur : b0; b1 = q == 1 ? bcur : b1; b2 = q == 2 ? bcur : b2; b3 = q == 3 ? bcur : b3;
+        ++q;
+        cur = bcur = 0u;
+        bit = 1u;
+    };
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        unsigned cur = 0u, band = 0u;
-        const int cend = min(32 * (q + 1), cr.tot);
-#pragma unroll 4
-        for (int c = 32 * q; c < cend; ++c) {
-            const float2 pj = spos[cr.smem_of(c)];
+    for (int r = 0; r < 3; ++r) {
+        const int lo = th.cstart[r][vi - 1], hi = th.cstart[r][vi + 2];
+#pragma unroll 2
+        for (int t = lo; t < hi; ++t) {
+            const float2 pj = spos[t];
             const float2 dd = __fadd2_rn(pi, f2(-pj.x, -pj.y));
             const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
-            cur |= (unsigned)(r2 < hi2) << (c & 31);
-            band |= (unsigned)(r2 > lo2) << (c & 31);
+            cur |= r2 < hi2 ? bit : 0u;
+            bcur |= r2 > lo2 ? bit : 0u;
+            bit <<= 1;
+            if (bit == 0u) file();
         }
-        band &= cur;
-#pragma unroll 1
-        while (band) {
-            const int b = __ffs(band) - 1;
-            band &= band - 1u;
-            const double2 xy = d.XY[sgj[cr.smem_of(32 * q + b)]];
-            double ex, ey;
-            if (!(exact_r2(d.g, qx, qy, xy.x, xy.y, ex, ey) < d.g.rc2)) cur &= ~(1u << b);
-        }
-        w[q] = cur;
     }
-    return make_uint4(w[0], w[1], w[2], w[3]);
+    if (bit != 1u) file();
+    uint4 m = make_uint4(w0, w1, w2, w3);
+    const uint4 bb = make_uint4(b0 & w0, b1 & w1, b2 & w2, b3 & w3);
+    if (bb.x | bb.y | bb.z | bb.w) {
+        unsigned bw[4] = {bb.x, bb.y, bb.z, bb.w};
+        unsigned mw[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+#pragma unroll 1
+            while (bw[k]) {
+                const int b = __ffs(bw[k]) - 1;
+                bw[k] &= bw[k] - 1u;
+                const double2 xy = d.XY[sgj[cr.smem_of(32 * k + b)]];
+                double ex, ey;
+                if (!(exact_r2(d.g, qx, qy, xy.x, xy.y, ex, ey) < d.g.rc2)) mw[k] &= ~(1u << b);
+            }
+        }
+        m = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+    }
+    return m;
 }
 
 // Run body(t) over the set bits of a candidate mask (shared indices t), calling fold() each
@@ -604,7 +626,7 @@ __global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled(Dev d)
             if (cr.tot <= 128) {
                 // phase 1: the neighbour mask over the candidate order (also pass B's input);
                 // phase 2: the pair terms over its set bits
-                const uint4 m = tile_mask(d, spos, sgj, cr, ti, xy.x, xy.y);
+                const uint4 m = tile_mask(d, th, spos, sgj, cr, ti, vi, xy.x, xy.y);
                 d.nbm[k] = m;
                 for_mask(cr, m, body, [&]() { f.fold(); });
             } else {
