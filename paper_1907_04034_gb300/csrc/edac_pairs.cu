@@ -690,8 +690,16 @@ __device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th,
             f.add(__fadd2_rn(pi, f2(-pj.x, -pj.y)), sq[tj], sb[tj], stg[tj]);
         };
         if (cr.tot <= 128) {
-            // the neighbours pass A found, as set bits of the candidate order
-            for_mask(cr, d.nbm[k], body, [&]() { f.fold(); });
+            // the neighbours pass A found, as set bits of the candidate order, less the
+            // particle itself (its pair terms are exact zeros: gW = 0, p_j - p_i = 0)
+            uint4 m = d.nbm[k];
+            const int cs = cr.l0 + (ti - cr.lo1), sw = cs >> 5;
+            const unsigned keep = ~(1u << (cs & 31));
+            m.x &= sw == 0 ? keep : ~0u;
+            m.y &= sw == 1 ? keep : ~0u;
+            m.z &= sw == 2 ? keep : ~0u;
+            m.w &= sw == 3 ? keep : ~0u;
+            for_mask(cr, m, body, [&]() { f.fold(); });
         } else {
 #pragma unroll 1
             for (int c = 0; c < cr.tot; ++c) {
