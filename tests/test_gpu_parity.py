@@ -408,7 +408,7 @@ def test_cylinder_re200_forces_match_table_clcd(outlet):
     """Long-run physics (Sec. 4.6): the paper's cylinder (15D x 15D, dx = D/30, Re = 200) with
     each outlet of Table clcd, run for 75 convective times on the mixed path; over the last 30
     the mean drag coefficient, the lift amplitude and the Strouhal number are compared with the
-    paper's row: c_d within 3 times the paper's band (this build's c_d sits 0.07-0.10 below
+    paper's row: c_d within 3 times the paper's band (the c_d here sits 0.07-0.10 below
     the paper's for every outlet, inside the literature range the paper quotes), the lift
     amplitude within 15%, St within 6%."""
     from paper_1907_04034_gb300 import validate
