@@ -216,6 +216,8 @@ size_t layout(Dev &d, const Geo &g, int cap, int max_history, int mixed, char *b
     DARR(ubar, double, C); DARR(vbar, double, C); DARR(pbar, double, C); DARR(J2, double, C);
     DARR(J2p, double, C); DARR(advp, double, C);
     DARR(redp, uint8_t, C);
+    DARR(org_x, double, (size_t)g.nx);
+    DARR(org_y, double, (size_t)g.ny);
     DARR(cell_count, int, (size_t)g.ncells);
     DARR(cell_start, int, (size_t)g.ncells + 1);
     DARR(slot_cell, int, C);
@@ -530,6 +532,7 @@ edac_status edac_set_particles(edac_ctx *ctx, int n, const double *h_x, const do
     Dev &d = ctx->d;
     cudaStream_t s = ctx->stream;
     CK(cudaMemsetAsync(ctx->ws, 0, ctx->ws_bytes, s));
+    ctx->launches += launch_origins(ctx->d, s);
     std::vector<uint8_t> tag(cap, TAG_DEAD);
     for (int i = 0; i < n; ++i) tag[i] = h_tag[i];
     std::vector<int> free_stack(cap - n);

@@ -30,6 +30,12 @@ __device__ __forceinline__ int warp_append(int *counter, bool want)
 }
 
 // ------------------------------------------------------------------------- cell build
+// Finite test on the exponent bits (integer pipe; the fp64 pipe is the scarce one here).
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+
 __global__ void k_cell_count(Dev d)
 {
     const Geo &g = d.g;
@@ -39,7 +45,12 @@ __global__ void k_cell_count(Dev d)
             continue;
         }
         const double xs = d.x[s], ys = d.y[s];
-        if (!(xs >= g.x_min && xs < g.x_max && ys >= g.y_min && ys < g.y_max)) {
+        // the domain test on the unclamped cell index (integer compares; the fp64 pipe is the
+        // scarce one), non-finite positions by their exponent bits
+        const int cxr = __double2int_rd((xs - g.x_min) * g.inv_sx);
+        const int cyr = __double2int_rd((ys - g.y_min) * g.inv_sy);
+        if (!(finite_bits(xs) & finite_bits(ys) & (cxr >= 0) & (cxr < g.nx) & (cyr >= 0) &
+              (cyr < g.ny))) {
             set_err(d, ERR_DOMAIN);
             if (atomicCAS(&d.cnt->err_rec, 0, 1) == 0) {
                 d.cnt->err_tag = d.tag[s];
@@ -48,8 +59,8 @@ __global__ void k_cell_count(Dev d)
                 d.cnt->err_y = ys;
             }
         }
-        const int cx = cell_coord(xs, g.x_min, g.inv_sx, g.nx);
-        const int cy = cell_coord(ys, g.y_min, g.inv_sy, g.ny);
+        const int cx = cxr < 0 ? 0 : (cxr >= g.nx ? g.nx - 1 : cxr);
+        const int cy = cyr < 0 ? 0 : (cyr >= g.ny ? g.ny - 1 : cyr);
         const int c = cy * g.nx + cx;
         d.slot_cell[s] = c;
         d.within[s] = atomicAdd(d.cell_count + c, 1);
@@ -157,8 +168,8 @@ __device__ __forceinline__ void gather_one(const Dev &d, int s, int k, int c)
     d.cellk[k] = c;
     const int cx = c % g.nx, cy = c / g.nx;
     const double xs = d.x[s], ys = d.y[s];
-    const float rx = (float)(xs - (g.x_min + (double)cx * g.sx));
-    const float ry = (float)(ys - (g.y_min + (double)cy * g.sy));
+    const float rx = (float)(xs - __ldg(d.org_x + cx));
+    const float ry = (float)(ys - __ldg(d.org_y + cy));
     const double ms = d.m[s];
     d.P[k] = make_float4(rx, ry, (float)ms, 0.0f);
     d.XY[k] = make_double2(xs, ys);
@@ -241,11 +252,6 @@ __device__ __forceinline__ void ring_sample(const Dev &d, int s, double un, doub
     pbv = (double)sp * ph.inv_navg;
 }
 
-// Finite test on the exponent bits (integer pipe; the fp64 pipe is the scarce one here).
-__device__ __forceinline__ bool finite_bits(double x)
-{
-    return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
-}
 
 template <bool CORR, int MIXED>
 __global__ void k_stage(Dev d, double tau)
@@ -611,4 +617,23 @@ int launch_probe(const Dev &d, cudaStream_t s, const ProbePts &q)
     return 2;
 }
 
+}  // namespace edac
+
+namespace edac {
+namespace {
+__global__ void k_origins(Dev d)
+{
+    const Geo &g = d.g;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nx + g.ny; i += gridDim.x * blockDim.x) {
+        if (i < g.nx) d.org_x[i] = g.x_min + (double)i * g.sx;
+        else d.org_y[i - g.nx] = g.y_min + (double)(i - g.nx) * g.sy;
+    }
+}
+}  // namespace
+
+int launch_origins(const Dev &d, cudaStream_t s)
+{
+    k_origins<<<(d.g.nx + d.g.ny + 255) / 256, 256, 0, s>>>(d);
+    return 1;
+}
 }  // namespace edac

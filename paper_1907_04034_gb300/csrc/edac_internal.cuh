@@ -99,6 +99,7 @@ struct Dev {
     double *ubar, *vbar, *pbar, *J2, *J2p, *advp;
     uint8_t *redp;
     // cell list
+    double *org_x, *org_y;  // [nx], [ny]: x_min + cx sx, y_min + cy sy (cell origins)
     int *cell_count;   // [ncells]
     int *cell_start;   // [ncells + 1]
     int *slot_cell;    // [cap]
@@ -205,7 +206,7 @@ __device__ __forceinline__ double exact_r2(const Geo &g, double xi, double yi, d
 
 __device__ __forceinline__ int cell_coord(double v, double lo, double inv_s, int n)
 {
-    int c = (int)floor((v - lo) * inv_s);
+    const int c = __double2int_rd((v - lo) * inv_s);  // floor, in one conversion
     return c < 0 ? 0 : (c >= n ? n - 1 : c);
 }
 
@@ -301,6 +302,8 @@ __device__ __forceinline__ void inlet_uv(const Phys &ph, double y, double t, dou
 // ------------------------------------------------------------------- host-side launchers
 // Every launcher issues its kernels on `s` and returns the number of launches issued.
 int launch_rebuild(const Dev &d, cudaStream_t s, int mixed);
+// cell-origin tables of the gather (after the workspace is cleared)
+int launch_origins(const Dev &d, cudaStream_t s);
 // probe values (p, u, v, fluid count) into d.probe_out
 int launch_probe(const Dev &d, cudaStream_t s, const ProbePts &q);
 
