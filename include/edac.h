@@ -237,9 +237,11 @@ edac_status edac_launch_count(edac_ctx *ctx, int64_t *count);
 /* ---------------------------------------------------------------------------
  * Allocation-free summation density.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory at the time they need
- * the result -- code running inside CUDA stream capture (an allocation there is
- * not allowed), code whose framework has handed all device memory to its own
- * pool allocator, and real-time code that forbids allocation on its hot path.
+ * the result -- code whose framework has handed all device memory to its own
+ * pool allocator (a raw allocation would fail or fragment that pool), plug-ins
+ * hosted by an application that owns the device memory and gives them none of
+ * their own, and real-time code that forbids allocation on its hot path
+ * (cudaMalloc and cudaFree can block and synchronise the device).
  * Neither this call nor the library allocates anything for it: the cell-list
  * scratch is a fixed static device array of the library (about 3.7 MB, held on
  * every GPU that loads the library until the process exits).

@@ -3,10 +3,11 @@
 // memory the library or the caller allocates.
 //
 // It exists for callers that cannot allocate device memory when they need the result: a
-// caller inside CUDA stream capture (an allocation there is not allowed), a caller whose
-// framework hands all device memory to its own pool allocator (a raw allocation would
-// fail or fragment it), and real-time callers that forbid allocation latency on the hot
-// path.  The caller still owns and passes the input and output arrays.
+// caller whose framework hands all device memory to its own pool allocator (a raw
+// allocation would fail or fragment it), a plug-in hosted by an application that owns the
+// device memory and gives it none, and real-time callers that forbid allocation on the hot
+// path (cudaMalloc and cudaFree can block and synchronise the device).  The caller still
+// owns and passes the input and output arrays.
 //
 // Scratch: one static __device__ array (EDAC_STATIC_MAX_PARTICLES particles and
 // EDAC_STATIC_MAX_CELLS cells, 3.7 MB) that every GPU which loads the library holds until

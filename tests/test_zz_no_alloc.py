@@ -1,6 +1,7 @@
 """The allocation-free entry point edac_density_static, for callers that cannot allocate
-device memory when they need the result (inside CUDA stream capture, under a framework's
-own pool allocator, or on an allocation-free real-time path).  Its scratch is the library's
+device memory when they need the result (under a framework's own pool allocator, as a
+plug-in whose host application owns the device memory, or on an allocation-free real-time
+path).  Its scratch is the library's
 static device array; this file is collected last so that a failure here comes after every
 other test has run.  Checked against the context path (edac_set_particles, whose initial
 evaluation gives rho, V and N) on two calls in a row, within the fp64 path's tolerance."""
