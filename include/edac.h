@@ -281,11 +281,13 @@ edac_status edac_fma_peak(int kind, void *cuda_stream, double *tflops);
 /* ---------------------------------------------------------------------------
  * Tiling of the mixed path's pair passes (no effect on the fp64 path): a tile
  * is a row segment of tile_cells cells (1..EDAC_TILE_MAX_CELLS) whose block has
- * `threads` threads (64 or 128).  The default, 8 cells and 128 threads, suits
- * large systems; small ones fill the GPU better with smaller tiles.  Results
- * differ only in the rounding of the fp32 sums (the candidate order changes).
- * EDAC_E_INVALID outside those values.  Drops the captured step graph. */
-#define EDAC_TILE_MAX_CELLS 8
+ * `threads` threads (a multiple of 32 from 64 to EDAC_TILE_MAX_THREADS).  The
+ * default, 11 cells and 160 threads, suits large systems; small ones fill the
+ * GPU better with smaller tiles.  Results differ only in the rounding of the
+ * fp32 sums (the candidate order changes).  EDAC_E_INVALID outside those
+ * values.  Drops the captured step graph. */
+#define EDAC_TILE_MAX_CELLS 16
+#define EDAC_TILE_MAX_THREADS 256
 edac_status edac_set_tiling(edac_ctx *ctx, int tile_cells, int threads);
 
 /* Autotuner of that tiling: times `trials` evaluations (edac_evaluate, which

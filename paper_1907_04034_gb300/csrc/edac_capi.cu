@@ -387,8 +387,8 @@ edac_status edac_create(const edac_params *params, void *d_workspace, size_t byt
     c->d.cap = params->capacity;
     c->d.mixed = c->mixed;
     c->d.max_history = params->max_history;
-    c->d.tile_tx = 8;
-    c->d.tile_tpb = 128;
+    c->d.tile_tx = 11;
+    c->d.tile_tpb = 160;
     layout(c->d, g, params->capacity, params->max_history, c->mixed, c->ws);
     *out = c;
     return EDAC_OK;
@@ -968,8 +968,9 @@ edac_status edac_read_tangent_history(edac_ctx *ctx, int max_steps, double *h_df
 edac_status edac_set_tiling(edac_ctx *ctx, int tile_cells, int threads)
 {
     if (!ctx) return EDAC_E_INVALID;
-    if (tile_cells < 1 || tile_cells > EDAC_TILE_MAX_CELLS || (threads != 64 && threads != 128))
-        return fail(ctx, EDAC_E_INVALID, "tiling: 1 <= tile_cells <= 8, threads 64 or 128");
+    if (tile_cells < 1 || tile_cells > EDAC_TILE_MAX_CELLS || threads < 64 ||
+        threads > EDAC_TILE_MAX_THREADS || threads % 32 != 0)
+        return fail(ctx, EDAC_E_INVALID, "tiling: 1 <= tile_cells <= 16, threads a multiple of 32 in [64, 256]");
     ctx->d.tile_tx = tile_cells;
     ctx->d.tile_tpb = threads;
     drop_graph(ctx);
@@ -983,7 +984,8 @@ edac_status edac_autotune(edac_ctx *ctx, int trials, int *tile_cells, int *threa
     if (ctx->failed) return fail(ctx, EDAC_E_STATE, "context in error");
     if (any_profiling(ctx)) return fail(ctx, EDAC_E_STATE, "autotune with kernel profiling on");
     // candidate tilings of the mixed pair passes; the fp64 path has none to choose
-    static const int cand[][2] = {{8, 128}, {6, 128}, {4, 64}, {6, 64}, {3, 64}, {2, 64}};
+    static const int cand[][2] = {{11, 160}, {16, 256}, {8, 128}, {6, 128},
+                                  {4, 64},   {6, 64},   {3, 64},  {2, 64}};
     const int ncand = ctx->mixed ? (int)(sizeof(cand) / sizeof(cand[0])) : 1;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));

@@ -12,6 +12,7 @@
 // MIXED = 1 evaluates the pair terms in fp32 on cell-relative coordinates with blocked
 // two-sum compensated accumulation; MIXED = 0 evaluates them in fp64 on the canonical fp64
 // separations.  The boundary kernel gives each boundary particle one warp.
+#include "edac.h"
 #include "edac_internal.cuh"
 
 namespace edac {
@@ -359,10 +360,12 @@ struct MixB {
 // row (pass A) or per 32 candidates (pass B).  A tile whose halo exceeds CT_HMAX particles
 // is processed from global memory instead (same membership test, same pair arithmetic), and
 // a particle with more than 128 candidates repeats the test in pass B.
-constexpr int CT_TX = 8;          // most cells of a tile (default: ~104 particles at 13 a cell)
+constexpr int CT_TX = 16;         // most cells of a tile (default 11: ~143 particles at 13 a cell)
 constexpr int CT_NV = CT_TX + 2;  // cells per staged row (halo included)
-constexpr int CT_TPB = 128;       // most threads of a tile block
-constexpr int CT_HMAX = 480;
+constexpr int CT_TPB = 256;       // most threads of a tile block
+constexpr int CT_HMAX = 768;      // staged particles (11 cells: ~3 x 13 x 13 = 507)
+static_assert(CT_TX == EDAC_TILE_MAX_CELLS && CT_TPB == EDAC_TILE_MAX_THREADS,
+              "tiling limits of header and kernels");
 
 struct TileHdr {
     int cstart[3][CT_NV + 1];  // shared index of each staged cell's first particle

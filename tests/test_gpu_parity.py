@@ -471,12 +471,16 @@ def test_batch_steps_equal_members_stepped_alone(prec):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("tiling", [(2, 64), (4, 64), (6, 128), (3, 64)])
-@pytest.mark.parametrize("name", ["random_open", "cylinder_coarse", "channel"])
+@pytest.mark.parametrize("tiling", [(2, 64), (4, 64), (6, 128), (3, 64), (8, 128), (16, 256),
+                                    (16, 96)])
+@pytest.mark.parametrize("name", ["random_open", "cylinder_coarse", "channel", "random_dense"])
 def test_tilings_match_oracle(tiling, name):
     """Every tiling of the mixed pair passes stays within the mixed tolerance of the oracle,
-    with the neighbour counts exact."""
-    c = _small_cases()[name]()
+    with the neighbour counts exact.  16 cells on 96 threads takes two particles per thread;
+    random_dense (~120 particles a cell) stages more particles than shared memory holds, so
+    its tiles take the global-memory path and its particles the repeated membership test."""
+    c = (cases.random_box(n=2500, seed=13, periodic_y=0) if name == "random_dense"
+         else _small_cases()[name]())
     ref = oracle.OracleSim(c)
     s = binding.Solver(c, precision="mixed")
     s.set_tiling(*tiling)
@@ -492,13 +496,14 @@ def test_autotune_leaves_the_state_unchanged():
     s.step(10)
     before = s.state(("x", "y", "u", "v", "p", "rho"))
     tx, tpb, ms = s.autotune(trials=2)
-    assert 1 <= tx <= 8 and tpb in (64, 128) and ms > 0.0
+    assert 1 <= tx <= 16 and 64 <= tpb <= 256 and tpb % 32 == 0 and ms > 0.0
     after = s.state(("x", "y", "u", "v", "p", "rho"))
     for k in ("x", "y", "u", "v"):
         np.testing.assert_array_equal(before[k], after[k], err_msg=k)
     # density, and the pressures projected on inlet and walls from it, are recomputed under
-    # the chosen tiling: equal up to the order of the fp32 sums
-    assert _rel_err(after["rho"], before["rho"], 1.0) < 1e-6
+    # the chosen tiling: equal up to the order of the fp32 sums (fp32 kernel terms, ~100 of
+    # them, folded into the compensated sums at other points)
+    assert _rel_err(after["rho"], before["rho"], 1.0) < 1e-5
     assert _rel_err(after["p"], before["p"], 0.5) < 1e-5
     s.step(5)  # the chosen tiling runs
     assert s.count() > 0
