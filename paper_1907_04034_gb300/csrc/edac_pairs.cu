@@ -214,8 +214,9 @@ __global__ void __launch_bounds__(TPB) k_pass_b64(Dev d)
 // ------------------------------------------------------------------ mixed-path pair bodies
 // fp32 arithmetic on the (x, y) pairs uses Blackwell's paired instructions (FADD2, FMUL2,
 // FFMA2); reciprocals and the inverse square root use the single-instruction approximations
-// (relative error ~2^-23).  Sums are accumulated per neighbour-cell row in fp32 and folded
-// into two-sum compensated (hi, lo) accumulators once per row.
+// (relative error ~2^-23).  Sums are accumulated over a few neighbours in fp32 and folded
+// into two-sum compensated (hi, lo) accumulators (see for_mask; once per cell row in the
+// other walks).
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float y;
@@ -316,9 +317,9 @@ struct MixB {
         const float2 g = __fmul2_rn(f2s(F), dd);
         const float gdotr = F * r2;
         const float cij = fmaf(q.y, q.y, Vi2);
-        const float irs = rcp_approx(rhoi + q.z);
-        const float e = rhoi * dp * irs;                        // pbar_ij - p_i
-        const float hf = rhoi * q.z * irs * gdotr * rcp_approx(r2 + eh2);
+        const float wi = rhoi * rcp_approx(rhoi + q.z);        // rho_i / (rho_i + rho_j)
+        const float e = wi * dp;                                // pbar_ij - p_i
+        const float hf = wi * q.z * gdotr * rcp_approx(r2 + eh2);
         const float2 uij = __fadd2_rn(ui, f2(-b.x, -b.y));
         const float2 cg = __fmul2_rn(f2s(cij), g);
         gg = __fadd2_rn(gg, cg);
@@ -356,8 +357,8 @@ struct MixB {
 // the particle's neighbours (itself included) as 16-bit shared-memory indices (phase 1),
 // evaluates its pair terms from shared memory (phase 2), and records the neighbours as a
 // 128-bit mask over the particle's candidate order; pass B iterates the set bits of that
-// mask instead of repeating the membership test.  Compensated sums are folded once per cell
-// row (pass A) or per 32 candidates (pass B).  A tile whose halo exceeds CT_HMAX particles
+// mask instead of repeating the membership test.  Compensated sums are folded once per 32
+// candidates (pass A), every 16 neighbours (pass B) or once per cell row (the other walks).  A tile whose halo exceeds CT_HMAX particles
 // is processed from global memory instead (same membership test, same pair arithmetic), and
 // a particle with more than 128 candidates repeats the test in pass B.
 constexpr int CT_TX = 16;         // most cells of a tile (default 11: ~143 particles at 13 a cell)
@@ -518,11 +519,14 @@ __device__ __forceinline__ void global_neighbors(const Dev &d, int k, const floa
 
 // Phase 1 of pass A: walk the candidate order of particle ti (the three cell rows of its 3 x 3
 // block, CandRows) and return the 128-bit mask of its neighbours (itself included); only for
-// cr.tot <= 128.  The loop walks each row's shared-memory range directly, sets a tentative
-// bit (r2 below the upper band edge) and a band bit (r2 above the lower edge) at the running
-// candidate index, and files the 32-bit words as they fill; the fp64 test then settles the
-// few band candidates after the loop, so the fp64 work stays out of the candidate loop (a
-// predicated fp64 test would issue for every candidate).
+// cr.tot <= 128.  The loop walks each row's shared-memory range directly in runs that end
+// where a 32-candidate word fills, shifting into the word being filled a tentative bit (r2
+// below the upper band edge: the sign of r2 - hi2) and a band bit (r2 above the lower edge:
+// the sign of lo2 - r2), one funnel shift each; a filled word is bit-reversed into candidate
+// order and filed.  The fp64 test then settles the few band candidates after the loop, so
+// the fp64 work stays out of the candidate loop (a predicated fp64 test would issue for
+// every candidate).  The signs are exact: r2 - hi2 is negative exactly when r2 < hi2 (a
+// difference of unequal floats is never zero), and lo2 - r2 likewise.
 __device__ __forceinline__ uint4 tile_mask(const Dev &d, const TileHdr &th, const float2 *spos,
                                            const int *sgj, const CandRows &cr, int ti, int vi,
                                            double qx, double qy)
@@ -530,30 +534,35 @@ __device__ __forceinline__ uint4 tile_mask(const Dev &d, const TileHdr &th, cons
     const float2 pi = spos[ti];
     const float hi2 = d.g.rc2_hi, lo2 = d.g.rc2_lo;
     unsigned w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u, b0 = 0u, b1 = 0u, b2 = 0u, b3 = 0u;
-    unsigned cur = 0u, bcur = 0u, bit = 1u;
-    int q = 0;
-    auto file = [&]() {  // the filled word goes to word q
-        w0 = q == 0 ? cur : w0; w1 = q == 1 ? cur : w1; w2 = q == 2 ? cur : w2; w3 = q == 3 ? cur : w3;
-        b0 = q == 0 ? bcur : b0; b1 = q == 1 ? bcur : b1; b2 = q == 2 ? bcur : b2; b3 = q == 3 ? bcur : b3;
+    unsigned cur = 0u, bcur = 0u;  // the word being filled, newest candidate in bit 0
+    int nfill = 0, q = 0;
+    auto file = [&]() {  // candidate k of the word (k = 0 oldest) goes to bit k of word q
+        const unsigned c = __brev(cur) >> (32 - nfill), bc = __brev(bcur) >> (32 - nfill);
+        w0 = q == 0 ? c : w0; w1 = q == 1 ? c : w1; w2 = q == 2 ? c : w2; w3 = q == 3 ? c : w3;
+        b0 = q == 0 ? bc : b0; b1 = q == 1 ? bc : b1; b2 = q == 2 ? bc : b2; b3 = q == 3 ? bc : b3;
         ++q;
         cur = bcur = 0u;
-        bit = 1u;
+        nfill = 0;
     };
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        const int lo = th.cstart[r][vi - 1], hi = th.cstart[r][vi + 2];
-#pragma unroll 2
-        for (int t = lo; t < hi; ++t) {
-            const float2 pj = spos[t];
-            const float2 dd = __fadd2_rn(pi, f2(-pj.x, -pj.y));
-            const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
-            cur |= r2 < hi2 ? bit : 0u;
-            bcur |= r2 > lo2 ? bit : 0u;
-            bit <<= 1;
-            if (bit == 0u) file();
+        int t = th.cstart[r][vi - 1];
+        const int hi = th.cstart[r][vi + 2];
+        while (t < hi) {
+            const int e = t + min(hi - t, 32 - nfill);
+            nfill += e - t;
+#pragma unroll 4
+            for (; t < e; ++t) {
+                const float2 pj = spos[t];
+                const float2 dd = __fadd2_rn(pi, f2(-pj.x, -pj.y));
+                const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
+                cur = __funnelshift_l(__float_as_uint(r2 - hi2), cur, 1);
+                bcur = __funnelshift_l(__float_as_uint(lo2 - r2), bcur, 1);
+            }
+            if (nfill == 32) file();
         }
     }
-    if (bit != 1u) file();
+    if (nfill > 0) file();
     uint4 m = make_uint4(w0, w1, w2, w3);
     const uint4 bb = make_uint4(b0 & w0, b1 & w1, b2 & w2, b3 & w3);
     if (bb.x | bb.y | bb.z | bb.w) {
@@ -575,9 +584,12 @@ __device__ __forceinline__ uint4 tile_mask(const Dev &d, const TileHdr &th, cons
     return m;
 }
 
-// Run body(t) over the set bits of a candidate mask (shared indices t), calling fold() each
-// time a 32-candidate word is exhausted.
-template <class Body, class Fold>
+// Run body(t) over the set bits of a candidate mask (shared indices t), calling fold() at the
+// end and either each time a lane's 32-candidate word runs out (EVERY = 0) or after every
+// EVERY terms.  The second form folds at the same iterations in every lane of a warp, so an
+// expensive fold (pass B's) runs once per warp instead of once for every lane whose word ran
+// out at another iteration; a cheap one (pass A's) costs less than the per-term count test.
+template <int EVERY, class Body, class Fold>
 __device__ __forceinline__ void for_mask(const CandRows &cr, uint4 m, Body &&body, Fold &&fold)
 {
     unsigned w0 = m.x, w1 = m.y, w2 = m.z, w3 = m.w;
@@ -588,11 +600,12 @@ __device__ __forceinline__ void for_mask(const CandRows &cr, uint4 m, Body &&bod
         while (w0 == 0u) {
             w0 = w1; w1 = w2; w2 = w3; w3 = 0u;
             base += 32;
-            fold();
+            if (EVERY == 0) fold();
         }
         const int b = __ffs(w0) - 1;
         w0 &= w0 - 1u;
         body(cr.smem_of(base + b));
+        if (EVERY > 0 && it % EVERY == EVERY - 1) fold();
     }
     fold();
 }
@@ -631,7 +644,7 @@ __global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled(Dev d)
                 // phase 2: the pair terms over its set bits
                 const uint4 m = tile_mask(d, th, spos, sgj, cr, ti, vi, xy.x, xy.y);
                 d.nbm[k] = m;
-                for_mask(cr, m, body, [&]() { f.fold(); });
+                for_mask<0>(cr, m, body, [&]() { f.fold(); });
             } else {
 #pragma unroll 1
                 for (int c = 0; c < cr.tot; ++c) {
@@ -702,7 +715,7 @@ __device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th,
             m.y &= sw == 1 ? keep : ~0u;
             m.z &= sw == 2 ? keep : ~0u;
             m.w &= sw == 3 ? keep : ~0u;
-            for_mask(cr, m, body, [&]() { f.fold(); });
+            for_mask<16>(cr, m, body, [&]() { f.fold(); });
         } else {
 #pragma unroll 1
             for (int c = 0; c < cr.tot; ++c) {
