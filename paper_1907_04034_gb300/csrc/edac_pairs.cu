@@ -806,6 +806,39 @@ __device__ __forceinline__ void warp_sum(T (&a)[NA])
     }
 }
 
+// Reduce-scatter of NA <= 16 fp64 values (zero-padded to 16) over the warp: in each round a
+// lane sends half of its values to lane ^ o and adds the half it receives, the last round
+// (o = 1) being a plain exchange.  On return lane L holds the warp total of value L >> 1.
+// The totals equal warp_sum's bit for bit (the same pairs are added in the same tree, and
+// fp addition is commutative), at 16 additions per lane instead of 5 NA: on GB300 the fp64
+// pipe runs at 1/64 of the fp32 rate, which makes the fp64 butterfly of the mirror's sums its
+// largest cost.
+template <int N>
+__device__ __forceinline__ void rs_round(double (&v)[16], int o, bool up)
+{
+    constexpr int M = N / 2;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        const double send = up ? v[j] : v[j + M];
+        const double keep = up ? v[j + M] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+}
+
+template <int NA>
+__device__ __forceinline__ double warp_reduce_scatter16(const double (&a)[NA], int lane)
+{
+    static_assert(NA <= 16, "at most 16 values");
+    double v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = i < NA ? a[i] : 0.0;
+    rs_round<16>(v, 16, lane & 16);
+    rs_round<8>(v, 8, lane & 8);
+    rs_round<4>(v, 4, lane & 4);
+    rs_round<2>(v, 2, lane & 2);
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 // Lane-strided walk of the neighbours of a query point: f(j, dx, dy, r2) with the pair
 // geometry in T (fp32 cell-relative for the mixed path, canonical fp64 otherwise).
 template <int MIXED, class F>
@@ -1000,11 +1033,15 @@ __device__ bool solve3(const double (&M)[3][3], const double (&b)[3], double (&x
 // system (|det| <= 1e-9 |M00 M11 M22|): the Shepard value sum f W V / sum W V; all weights
 // zero (every fluid neighbour at the support edge): the plain mean of f.  fp64 on both paths:
 // with disordered particles the system can be ill-conditioned and fp32 moment sums would
-// lose the solution.  Whole warp; lane 0 receives fo.
+// lose the solution.
+//
+// mirror_sums: this lane's share of the sums a[mirror_na(NF)] (whole warp; the lanes split the
+// fluid neighbours); mirror_solve: f_o from the warp totals of those sums (one lane).
+__host__ __device__ constexpr int mirror_na(int nf) { return 9 + 3 * nf + 1 + nf; }
+
 template <int MIXED, int NF>
-__device__ __forceinline__ void mirror_extrapolate(const Dev &d, int lane, int *wbuf, double xo,
-                                                   double yo, double xk, double yk,
-                                                   double (&fo)[NF])
+__device__ __forceinline__ void mirror_sums(const Dev &d, int lane, int *wbuf, double xk, double yk,
+                                            double (&a)[mirror_na(NF)])
 {
     const Geo &g = d.g;
     const Phys &ph = d.ph;
@@ -1013,8 +1050,7 @@ __device__ __forceinline__ void mirror_extrapolate(const Dev &d, int lane, int *
     const float rx = (float)(xk - (g.x_min + (double)cx * g.sx));
     const float ry = (float)(yk - (g.y_min + (double)cy * g.sy));
     // [M (9) | right-hand sides (3 per field) | count | plain sums (1 per field)]
-    constexpr int NA = 9 + 3 * NF + 1 + NF;
-    double a[NA];
+    constexpr int NA = mirror_na(NF);
 #pragma unroll
     for (int i = 0; i < NA; ++i) a[i] = 0.0;
     lane_fluid_compact(d, lane, wbuf, xk, yk, cx, cy, rx, ry, [&](int l) {
@@ -1076,8 +1112,12 @@ __device__ __forceinline__ void mirror_extrapolate(const Dev &d, int lane, int *
 #pragma unroll
         for (int f = 0; f < NF; ++f) a[10 + 3 * NF + f] += fv[f];
     });
-    warp_sum(a);
-    if (lane != 0) return;
+}
+
+template <int NF>
+__device__ __forceinline__ void mirror_solve(const double (&a)[mirror_na(NF)], double xo, double yo,
+                                             double xk, double yk, double (&fo)[NF])
+{
     double M[3][3];
     for (int q = 0; q < 3; ++q)
         for (int c = 0; c < 3; ++c) M[q][c] = a[3 * q + c];
@@ -1103,17 +1143,47 @@ __device__ __forceinline__ void mirror_extrapolate(const Dev &d, int lane, int *
     }
 }
 
+
+// The whole extrapolation on one warp: lane 0 receives fo.
+template <int MIXED, int NF>
+__device__ __forceinline__ void mirror_extrapolate(const Dev &d, int lane, int *wbuf, double xo,
+                                                   double yo, double xk, double yk,
+                                                   double (&fo)[NF])
+{
+    double a[mirror_na(NF)];
+    mirror_sums<MIXED, NF>(d, lane, wbuf, xk, yk, a);
+    warp_sum(a);
+    if (lane == 0) mirror_solve<NF>(a, xo, yo, xk, yk, fo);
+}
+
+// A warp takes the boundary particles in chunks of BND_CHUNK.  Walls and outlet particles are
+// finished one by one (lane 0); an inlet particle's mirror sums are reduce-scattered into a
+// per-warp stash, and the chunk's inlet particles are solved together at its end, lane i for
+// the chunk's particle i, so that the fp64 3x3 solve runs once per warp-instruction for up
+// to BND_CHUNK particles instead of once per particle.  Nothing in the kernel reads the
+// inlet's values, so finishing them at the chunk end changes no result.
+constexpr int BND_CHUNK = 8;
+constexpr int BND_STASH = 17;  // stash row stride (doubles): odd, against bank conflicts
+
 template <int MIXED>
 __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
 {
     typedef typename std::conditional<MIXED, float, double>::type T;
+    constexpr int NAI = mirror_na(1);
+    static_assert(NAI <= 16 && NAI <= BND_STASH, "inlet mirror sums");
     __shared__ int wbuf[8][CMP_CAP];  // per-warp list of the mirror's fluid neighbours
+    __shared__ double stash[8][BND_CHUNK][BND_STASH];  // per-warp inlet mirror sums
     const Phys &ph = d.ph;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = d.cnt->n_bnd;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const T a2 = (T)ph.a2, a2h = (T)ph.a2h, inv_h = (T)ph.inv_h;
-    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nwarps) {
+    for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * BND_CHUNK; base < nb;
+         base += nwarps * BND_CHUNK) {
+    const int nchunk = min(BND_CHUNK, nb - base);
+    bool inlet_mine = false;  // lane i: chunk particle i is an inlet particle to solve
+    for (int i = 0; i < nchunk; ++i) {
+        const int b = base + i;
         const int k = d.bnd[b];
         const int t = d.stag[k] & 0x7f;
         const int s = d.order[k];
@@ -1164,21 +1234,13 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                 d.p[s] = pw; d.u[s] = ug; d.v[s] = vg; d.ut[s] = ug; d.vt[s] = vg;
             }
         } else if (t == INLET && ph.has_inlet) {
-            // Mirrored inlet pressure (Sec. 3.2) about k = (2 x_in - x_o, y_o)
-            double fo[1];
-            mirror_extrapolate<MIXED, 1>(d, lane, wbuf[threadIdx.x >> 5], xy.x, xy.y,
-                                         2.0 * ph.x_in - xy.x, xy.y, fo);
-            if (lane == 0) {
-                const double po = fo[0];
-                if (MIXED) {
-                    float4 q = d.Qf[k];
-                    q.x = (float)po;
-                    d.Qf[k] = q;
-                } else {
-                    d.PV[k].x = po;
-                }
-                d.p[s] = po;
-            }
+            // Mirrored inlet pressure (Sec. 3.2) about k = (2 x_in - x_o, y_o): the sums now,
+            // the solve at the end of the chunk
+            double a[NAI];
+            mirror_sums<MIXED, 1>(d, lane, wbuf[w], 2.0 * ph.x_in - xy.x, xy.y, a);
+            const double v = warp_reduce_scatter16(a, lane);
+            if (!(lane & 1) && (lane >> 1) < NAI) stash[w][i][lane >> 1] = v;
+            inlet_mine = inlet_mine || lane == i;
         } else if (t == OUTLET && end_of_step && ph.has_outlet &&
                    (ph.outlet_kind == OUT_HYBRID || ph.outlet_kind == OUT_CHARACTERISTIC ||
                     ph.outlet_kind == OUT_MOD_DONOTHING)) {
@@ -1253,6 +1315,27 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                 }
             }
         }
+    }
+    __syncwarp();
+    if (inlet_mine) {
+        const int k = d.bnd[base + lane];
+        const int s = d.order[k];
+        const double2 xy = d.XY[k];
+        double a[NAI], fo[1];
+#pragma unroll
+        for (int q = 0; q < NAI; ++q) a[q] = stash[w][lane][q];
+        mirror_solve<1>(a, xy.x, xy.y, 2.0 * ph.x_in - xy.x, xy.y, fo);
+        const double po = fo[0];
+        if (MIXED) {
+            float4 q = d.Qf[k];
+            q.x = (float)po;
+            d.Qf[k] = q;
+        } else {
+            d.PV[k].x = po;
+        }
+        d.p[s] = po;
+    }
+    __syncwarp();  // the stash is refilled by the next chunk
     }
 }
 
@@ -1330,10 +1413,12 @@ int launch_pass_a(const Dev &d, cudaStream_t s, int mixed)
 
 int launch_boundary(const Dev &d, cudaStream_t s, int mixed, int end_of_step)
 {
-    // one warp per boundary particle (grid-stride); boundary particles are O(sqrt(N))
+    // one warp per chunk of BND_CHUNK boundary particles (grid-stride over the chunks; boundary
+    // particles are O(sqrt(N))); at most three resident blocks per SM
+    const int bblocks = min(grid_for(d.cap, 64 * BND_CHUNK), 152 * 3);
+    if (mixed) k_boundary<1><<<bblocks, 256, 0, s>>>(d, end_of_step);
+    else k_boundary<0><<<bblocks, 256, 0, s>>>(d, end_of_step);
     const int blocks = min(grid_for(d.cap, 64), 152 * 16);
-    if (mixed) k_boundary<1><<<blocks, 256, 0, s>>>(d, end_of_step);
-    else k_boundary<0><<<blocks, 256, 0, s>>>(d, end_of_step);
     if (end_of_step && d.ph.has_outlet && d.ph.outlet_kind == OUT_MIRROR) {
         if (mixed) k_outlet_mirror<1><<<blocks, 256, 0, s>>>(d);
         else k_outlet_mirror<0><<<blocks, 256, 0, s>>>(d);
