@@ -279,6 +279,24 @@ edac_status edac_density_static(const edac_params *params, int n, const double *
 edac_status edac_fma_peak(int kind, void *cuda_stream, double *tflops);
 
 /* ---------------------------------------------------------------------------
+ * Self-check of the library's fp32 <-> fp64 conversions.  The paper has no
+ * counterpart: on GB300 the hardware conversions between fp32 and fp64 issue
+ * to the fp64 pipe (1/64 of the fp32 rate), so the kernels convert on the
+ * integer pipe instead (IEEE 754 widening, and narrowing with round to
+ * nearest, ties to even); this compares those conversions with the hardware's
+ * on the device.  all_floats != 0: every one of the 2^32 float bit patterns
+ * is widened; n_doubles: that many sampled double bit patterns are narrowed
+ * (uniform bit patterns, values whose dropped bits sit at or next to a
+ * rounding tie, values near the float range's overflow and underflow edges).
+ * Writes the mismatch counts (0 when the conversions agree; NaNs compare
+ * equal whatever their payload).  Runs on cuda_stream (NULL: default stream)
+ * and synchronises it; allocates nothing (the counters are static device
+ * variables, so overlapping calls race).  EDAC_E_INVALID for NULL outputs,
+ * EDAC_E_CUDA if a copy or launch fails. */
+edac_status edac_conversion_check(void *cuda_stream, int all_floats, uint64_t n_doubles,
+                                  uint64_t *float_mismatches, uint64_t *double_mismatches);
+
+/* ---------------------------------------------------------------------------
  * Tiling of the mixed path's pair passes (no effect on the fp64 path): a tile
  * is a row segment of tile_cells cells (1..EDAC_TILE_MAX_CELLS) whose block has
  * `threads` threads (a multiple of 32 from 64 to EDAC_TILE_MAX_THREADS).  The

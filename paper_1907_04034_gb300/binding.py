@@ -25,7 +25,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libedac.so")
 SOURCES = ("edac_capi.cu", "edac_cells.cu", "edac_pairs.cu", "edac_static.cu", "edac_peaks.cu",
-           "edac_tangent.cu")
+           "edac_tangent.cu", "edac_selfcheck.cu")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 EDAC_FP64, EDAC_MIXED = 0, 1
@@ -41,7 +41,8 @@ EXPORTS = ("edac_workspace_bytes", "edac_create", "edac_set_inlet", "edac_set_ou
            "edac_set_wall", "edac_set_particles", "edac_step", "edac_evaluate", "edac_get_count",
            "edac_read_state", "edac_read_history", "edac_neighbor_scratch_bytes",
            "edac_read_neighbors", "edac_profile", "edac_read_profile", "edac_launch_count",
-           "edac_density_static", "edac_fma_peak", "edac_set_tiling", "edac_autotune",
+           "edac_density_static", "edac_fma_peak", "edac_conversion_check", "edac_set_tiling",
+           "edac_autotune",
            "edac_batch_create", "edac_batch_step", "edac_batch_launch_count", "edac_batch_destroy",
            "edac_set_inlet_transient", "edac_set_outlet_reference", "edac_probe",
            "edac_tangent_workspace_bytes", "edac_tangent_enable", "edac_step_tangent",
@@ -147,6 +148,8 @@ def load(path: Optional[str] = None):
         L.edac_launch_count.argtypes = [_P, C.POINTER(i64)]
         L.edac_density_static.argtypes = [C.POINTER(Params), i32] + [_P] * 6
         L.edac_fma_peak.argtypes = [i32, _P, _DP]
+        L.edac_conversion_check.argtypes = [_P, i32, C.c_uint64, C.POINTER(C.c_uint64),
+                                            C.POINTER(C.c_uint64)]
         L.edac_set_tiling.argtypes = [_P, i32, i32]
         L.edac_autotune.argtypes = [_P, i32, C.POINTER(i32), C.POINTER(i32), _DP]
         L.edac_batch_create.argtypes = [C.POINTER(_P), i32, _P, C.POINTER(_P)]
@@ -240,6 +243,24 @@ def fma_peak(kind: int, device: str = "cuda:0", stream=None) -> float:
     if rc != 0:
         raise EdacError(rc, "edac_fma_peak")
     return float(out.value)
+
+
+def conversion_check(all_floats: bool = True, n_doubles: int = 1 << 28,
+                     device: str = "cuda:0") -> tuple:
+    """(float, double) mismatch counts of the library's integer-pipe conversions against the
+    hardware ones (edac_conversion_check)."""
+    import torch
+
+    lib = load()
+    dev = torch.device(device)
+    st = torch.cuda.current_stream(dev)
+    a, b = C.c_uint64(0), C.c_uint64(0)
+    with torch.cuda.device(dev):
+        rc = lib.edac_conversion_check(C.c_void_p(st.cuda_stream), int(bool(all_floats)),
+                                       int(n_doubles), C.byref(a), C.byref(b))
+    if rc != 0:
+        raise EdacError(rc, "edac_conversion_check")
+    return int(a.value), int(b.value)
 
 
 class Solver:

@@ -168,10 +168,10 @@ __device__ __forceinline__ void gather_one(const Dev &d, int s, int k, int c)
     d.cellk[k] = c;
     const int cx = c % g.nx, cy = c / g.nx;
     const double xs = d.x[s], ys = d.y[s];
-    const float rx = (float)(xs - __ldg(d.org_x + cx));
-    const float ry = (float)(ys - __ldg(d.org_y + cy));
+    const float rx = d2f(xs - __ldg(d.org_x + cx));
+    const float ry = d2f(ys - __ldg(d.org_y + cy));
     const double ms = d.m[s];
-    d.P[k] = make_float4(rx, ry, (float)ms, 0.0f);
+    d.P[k] = make_float4(rx, ry, d2f(ms), 0.0f);
     d.XY[k] = make_double2(xs, ys);
     const uint8_t t = d.tag[s];
     d.stag[k] = (uint8_t)(t | ((t == OUTLET && d.redp[s]) ? TAG_REDP : 0));
@@ -179,8 +179,8 @@ __device__ __forceinline__ void gather_one(const Dev &d, int s, int k, int c)
     const double us = d.u[s], vs = d.v[s];
     const double dus = d.ut[s] - us, dvs = d.vt[s] - vs;
     if (MIXED) {
-        d.Bf[k] = make_float4((float)us, (float)vs, (float)dus, (float)dvs);
-        d.Qf[k] = make_float4((float)d.p[s], 0.0f, 0.0f, 0.0f);
+        d.Bf[k] = make_float4(d2f(us), d2f(vs), d2f(dus), d2f(dvs));
+        d.Qf[k] = make_float4(d2f(d.p[s]), 0.0f, 0.0f, 0.0f);
     } else {
         d.UV[k] = make_double2(us, vs);
         d.DUV[k] = make_double2(dus, dvs);
@@ -240,16 +240,16 @@ __device__ __forceinline__ void ring_sample(const Dev &d, int s, double un, doub
     // below it
     if (pn * pn * ph.inv_2rc <= ph.I_thr) {
         const int k = d.rpos[s];
-        rg[3 * k + 0] = (R)un; rg[3 * k + 1] = (R)vn; rg[3 * k + 2] = (R)pn;
+        rg[3 * k + 0] = narrow<R>(un); rg[3 * k + 1] = narrow<R>(vn); rg[3 * k + 2] = narrow<R>(pn);
         d.rpos[s] = (uint8_t)(k + 1 == ph.n_avg ? 0 : k + 1);
     }
     R su = 0, sv = 0, sp = 0;
     for (int k = 0; k < ph.n_avg; ++k) {
         su += rg[3 * k + 0]; sv += rg[3 * k + 1]; sp += rg[3 * k + 2];
     }
-    ub = (double)su * ph.inv_navg;
-    vb = (double)sv * ph.inv_navg;
-    pbv = (double)sp * ph.inv_navg;
+    ub = widen(su) * ph.inv_navg;
+    vb = widen(sv) * ph.inv_navg;
+    pbv = widen(sp) * ph.inv_navg;
 }
 
 

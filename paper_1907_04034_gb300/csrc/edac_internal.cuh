@@ -147,6 +147,51 @@ struct ProbePts {
 };
 
 // -------------------------------------------------------------------------------------------
+// fp32 <-> fp64 conversions on the integer pipe.  On GB300 the hardware conversions between
+// fp32 and fp64 issue to the fp64 pipe (about 0.6 T conversions/s, the DFMA rate), which makes
+// them the largest fp64 cost of the gather, the stage, the pair-pass epilogues and the
+// mirror sums.  These are the IEEE 754 conversions written out on the bit fields: widening a
+// normal float moves the sign, re-biases the exponent (127 -> 1023) and appends 29 zero
+// mantissa bits; narrowing a double whose result is a normal float (or overflows to
+// infinity by rounding) keeps the top 23 of the 52 mantissa bits and rounds the 29 dropped
+// bits to nearest, ties to even (a carry out of the mantissa steps the exponent, as the
+// format intends).  Zeros are handled on the fast path; subnormals, infinities and NaNs (none
+// of which the solver's fields hold) take the hardware conversion.  The results equal the
+// hardware conversion bit for bit (edac_conversion_check: every float, and sampled doubles).
+// -------------------------------------------------------------------------------------------
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned mag = b & 0x7fffffffu;
+    if ((mag >> 23) - 1u < 254u) {  // normal: exponent field 1..254
+        const unsigned hi = (b & 0x80000000u) | ((mag >> 3) + 0x38000000u);
+        return __hiloint2double((int)hi, (int)(b << 29));
+    }
+    if (mag == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    return (double)f;
+}
+
+__device__ __forceinline__ float d2f(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned mag = hi & 0x7fffffffu;
+    if ((mag >> 20) - 897u < 254u) {  // float exponent 1..254 before rounding
+        const unsigned base = __funnelshift_l(lo, mag - 0x38000000u, 3);  // exponent | top 23 bits
+        const unsigned inc = ((lo & 0x1fffffffu) + (base & 1u) + 0x0fffffffu) >> 29;  // RNE
+        return __uint_as_float((hi & 0x80000000u) | (base + inc));
+    }
+    if ((mag | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+    return __double2float_rn(x);
+}
+
+// the same for code templated on the storage type R (float or double)
+__device__ __forceinline__ double widen(float x) { return f2d(x); }
+__device__ __forceinline__ double widen(double x) { return x; }
+template <class R> __device__ __forceinline__ R narrow(double x);
+template <> __device__ __forceinline__ float narrow<float>(double x) { return d2f(x); }
+template <> __device__ __forceinline__ double narrow<double>(double x) { return x; }
+
+// -------------------------------------------------------------------------------------------
 // Quintic spline (Eq. quintic-spline) in the branch-free form: with t_k = max(0, k - q),
 //   w(q) = t3^5 - 6 t2^5 + 15 t1^5,   dw/dq = -5 (t3^4 - 6 t2^4 + 15 t1^4),
 // which equals the paper's piecewise definition on every branch (t_k vanishes where the

@@ -673,8 +673,8 @@ __global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled(Dev d)
         d.Qf[k] = make_float4(q.x, V, R, pk.z / R);
         d.snnb[k] = f.n;
         const int s = d.order[k];
-        d.rho[s] = (double)R;
-        d.vol[s] = (double)V;
+        d.rho[s] = f2d(R);
+        d.vol[s] = f2d(V);
         d.nnb[s] = f.n;
     }
 }
@@ -750,16 +750,16 @@ __device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th,
     const float corr = (ph.use_pavg && !SOLID) ? f.sdp / (float)N : -q.x;
     const int s = d.order[k];
     if (SOLID) {
-        d.fx[s] = (double)fmaf(corr, G0, sx);
-        d.fy[s] = (double)fmaf(corr, G1, sy);
+        d.fx[s] = f2d(fmaf(corr, G0, sx));
+        d.fy[s] = f2d(fmaf(corr, G1, sy));
     } else {
         const float mi_inv = 1.0f / pk.z;
-        d.au[s] = (double)fmaf(fmaf(corr, G0, sx), mi_inv, ph.gxf);
-        d.av[s] = (double)fmaf(fmaf(corr, G1, sy), mi_inv, ph.gyf);
-        d.ap[s] = (double)(f.ap_hl.x + f.ap_hl.y);
+        d.au[s] = f2d(fmaf(fmaf(corr, G0, sx), mi_inv, ph.gxf));
+        d.av[s] = f2d(fmaf(fmaf(corr, G1, sy), mi_inv, ph.gyf));
+        d.ap[s] = f2d(f.ap_hl.x + f.ap_hl.y);
         const float pbm = -ph.pbf * mi_inv;
-        d.abu[s] = (double)(pbm * G0);
-        d.abv[s] = (double)(pbm * G1);
+        d.abu[s] = f2d(pbm * G0);
+        d.abv[s] = f2d(pbm * G1);
     }
 }
 
@@ -1047,8 +1047,8 @@ __device__ __forceinline__ void mirror_sums(const Dev &d, int lane, int *wbuf, d
     const Phys &ph = d.ph;
     const int cx = cell_coord(xk, g.x_min, g.inv_sx, g.nx);
     const int cy = cell_coord(yk, g.y_min, g.inv_sy, g.ny);
-    const float rx = (float)(xk - (g.x_min + (double)cx * g.sx));
-    const float ry = (float)(yk - (g.y_min + (double)cy * g.sy));
+    const float rx = d2f(xk - (g.x_min + (double)cx * g.sx));
+    const float ry = d2f(yk - (g.y_min + (double)cy * g.sy));
     // [M (9) | right-hand sides (3 per field) | count | plain sums (1 per field)]
     constexpr int NA = mirror_na(NF);
 #pragma unroll
@@ -1063,8 +1063,8 @@ __device__ __forceinline__ void mirror_sums(const Dev &d, int lane, int *wbuf, d
             // each, on the fp32 pipe); the moment sums, where the cancellation is, stay fp64
             const float4 q = d.Qf[l];
             const float4 b = d.Bf[l];
-            fv[0] = (double)q.x; fv[1] = (double)b.x; fv[2] = (double)b.y;
-            const float Vl = q.w, r2f = (float)r2;
+            fv[0] = f2d(q.x); fv[1] = f2d(b.x); fv[2] = f2d(b.y);
+            const float Vl = q.w, r2f = d2f(r2);
             float w, wx = 0.0f, wy = 0.0f;
             if (r2f > 1e-30f) {
                 const float ir = rsqrt_approx(r2f);
@@ -1072,14 +1072,14 @@ __device__ __forceinline__ void mirror_sums(const Dev &d, int lane, int *wbuf, d
                 quintic_w_dw(r2f * ir * ph.inv_hf, wq, dwq);
                 w = ph.a2f * wq;
                 const float dwr = ph.a2hf * dwq * ir;
-                wx = dwr * (float)xlk;
-                wy = dwr * (float)ylk;
+                wx = dwr * d2f(xlk);
+                wy = dwr * d2f(ylk);
             } else {
                 w = ph.a2f * quintic_w(0.0f);
             }
-            row[0] = (double)(w * Vl);
-            row[1] = (double)(wx * Vl);
-            row[2] = (double)(wy * Vl);
+            row[0] = f2d(w * Vl);
+            row[1] = f2d(wx * Vl);
+            row[2] = f2d(wy * Vl);
         } else {
             // fp64 path: IEEE square root and division (the oracle's arithmetic)
             double Vl;
@@ -1177,7 +1177,7 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = d.cnt->n_bnd;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const T a2 = (T)ph.a2, a2h = (T)ph.a2h, inv_h = (T)ph.inv_h;
+    const T a2 = narrow<T>(ph.a2), a2h = narrow<T>(ph.a2h), inv_h = narrow<T>(ph.inv_h);
     for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * BND_CHUNK; base < nb;
          base += nwarps * BND_CHUNK) {
     const int nchunk = min(BND_CHUNK, nb - base);
@@ -1217,9 +1217,9 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                     pw = (wz ? a[5] : a[1]) * isw;
                     const T uf = (wz ? a[6] : a[2]) * isw, vf = (wz ? a[7] : a[3]) * isw;
                     if (ph.wall_slip[wi]) { ug = uf; vg = -vf; }
-                    else { ug = (T)(2.0 * ph.wall_u[wi]) - uf; vg = (T)(2.0 * ph.wall_v[wi]) - vf; }
+                    else { ug = narrow<T>(2.0 * ph.wall_u[wi]) - uf; vg = narrow<T>(2.0 * ph.wall_v[wi]) - vf; }
                 } else {
-                    pw = (T)0; ug = (T)ph.wall_u[wi]; vg = (T)ph.wall_v[wi];
+                    pw = (T)0; ug = narrow<T>(ph.wall_u[wi]); vg = narrow<T>(ph.wall_v[wi]);
                 }
                 if (MIXED) {
                     float4 q = d.Qf[k];
@@ -1231,7 +1231,8 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                     d.UV[k] = make_double2(ug, vg);
                     d.DUV[k] = make_double2(0.0, 0.0);
                 }
-                d.p[s] = pw; d.u[s] = ug; d.v[s] = vg; d.ut[s] = ug; d.vt[s] = vg;
+                const double pwd = widen(pw), ugd = widen(ug), vgd = widen(vg);
+                d.p[s] = pwd; d.u[s] = ugd; d.v[s] = vgd; d.ut[s] = ugd; d.vt[s] = vgd;
             }
         } else if (t == INLET && ph.has_inlet) {
             // Mirrored inlet pressure (Sec. 3.2) about k = (2 x_in - x_o, y_o): the sums now,
@@ -1273,7 +1274,7 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                         fluid_fields<MIXED>(d, j, p, u, v, mr);
                         fj = u;
                     } else {
-                        fj = (T)d.AUX[j].x;  // J2 of the fluid particle
+                        fj = narrow<T>(d.AUX[j].x);  // J2 of the fluid particle
                     }
                     a[0] += w;
                     a[1] += w * fj;
@@ -1281,8 +1282,8 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                     a[6] += fj;
                 } else if (tj == (OUTLET | TAG_REDP)) {
                     const double2 x2 = d.AUX[j];
-                    a[3] += (T)x2.x;
-                    a[4] += (T)x2.y;
+                    a[3] += narrow<T>(x2.x);
+                    a[4] += narrow<T>(x2.y);
                     a[5] += (T)1;
                 }
             });
@@ -1292,24 +1293,24 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
                 const T mr = a[5];
                 // Shepard average; all weights zero (fluid at the support edge): plain mean
                 const T shep = red ? (a[0] > (T)0 ? a[1] / a[0] : a[6] / a[2]) : (T)0;
-                const double blue_adv = mr > (T)0 ? (double)(a[4] / mr) : 0.0;
+                const double blue_adv = mr > (T)0 ? widen(a[4] / mr) : 0.0;
                 if (kind == OUT_MOD_DONOTHING) {
                     d.J2p[s] = 0.0;
-                    d.advp[s] = red ? (double)shep : (mr > (T)0 ? blue_adv : d.ubar[s]);
+                    d.advp[s] = red ? widen(shep) : (mr > (T)0 ? blue_adv : d.ubar[s]);
                     d.redp[s] = red ? 1 : 0;
                 } else {
                     const bool ch = kind == OUT_CHARACTERISTIC;
                     const T J2 = red ? shep : (mr > (T)0 ? a[3] / mr : (T)0);
                     const double ub = ch ? ph.moc_u_ref : d.ubar[s];
                     const double pb = ch ? ph.moc_p_ref : d.pbar[s];
-                    const double un = ub + (double)(J2 * (MIXED ? (T)ph.inv_2rcf : (T)ph.inv_2rc));
+                    const double un = ub + widen(J2 * (MIXED ? (T)ph.inv_2rcf : narrow<T>(ph.inv_2rc)));
                     const double adv = red ? un : (mr > (T)0 ? blue_adv : (ch ? un : ub));
                     d.u[s] = un;
                     d.v[s] = d.vbar[s];
-                    d.p[s] = pb + (double)((T)0.5 * J2);
+                    d.p[s] = pb + widen((T)0.5 * J2);
                     d.ut[s] = un;
                     d.vt[s] = d.vbar[s];
-                    d.J2p[s] = (double)J2;
+                    d.J2p[s] = widen(J2);
                     d.advp[s] = adv;
                     d.redp[s] = red ? 1 : 0;
                 }
@@ -1328,7 +1329,7 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
         const double po = fo[0];
         if (MIXED) {
             float4 q = d.Qf[k];
-            q.x = (float)po;
+            q.x = d2f(po);
             d.Qf[k] = q;
         } else {
             d.PV[k].x = po;

@@ -88,6 +88,12 @@ def test_fma_peak_rejects_bad_arguments_before_any_gpu_call(lib):
     assert lib.edac_fma_peak(binding.EDAC_PEAK_FP32, None, None) == 1
 
 
+def test_conversion_check_rejects_null_outputs_before_any_gpu_call(lib):
+    out = C.c_uint64(0)  # status 1 = EDAC_E_INVALID
+    assert lib.edac_conversion_check(None, 1, 16, None, C.byref(out)) == 1
+    assert lib.edac_conversion_check(None, 1, 16, C.byref(out), None) == 1
+
+
 def test_binding_declares_the_argument_types_of_every_entry(lib):
     # ctypes converts floats and pointers only for declared signatures
     for name in binding.EXPORTS:

@@ -353,6 +353,16 @@ def test_bad_uploads_are_rejected_on_the_host():
 
 
 @pytest.mark.gpu
+def test_integer_pipe_conversions_equal_the_hardware_ones():
+    """The kernels' fp32 <-> fp64 conversions (integer-pipe IEEE 754 widening and
+    round-to-nearest-even narrowing) give the hardware conversion's bits: every float bit
+    pattern widened, 3 x 2^28 sampled doubles narrowed (uniform bit patterns, ties and their
+    neighbours, the overflow and underflow edges)."""
+    bad_f, bad_d = binding.conversion_check(all_floats=True, n_doubles=3 << 28)
+    assert bad_f == 0 and bad_d == 0, (bad_f, bad_d)
+
+
+@pytest.mark.gpu
 def test_fma_peaks_are_measured_and_plausible():
     """edac_fma_peak: the FP32 rate lies between a quarter and 2.2x of 128 lanes x 2 flops x
     SMs x 2.1 GHz, and the FP64 rate is positive and below the FP32 rate."""
