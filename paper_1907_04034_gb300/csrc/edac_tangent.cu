@@ -72,7 +72,7 @@ __device__ __forceinline__ float &tg(const TDev &t, const Dev &d, int f, int c, 
 
 __device__ __forceinline__ D1 dual(const TDev &t, const Dev &d, double v, int f, int c, int s)
 {
-    return D1(v, (double)t.f[f][(size_t)c * d.cap + s]);
+    return D1(v, f2d(t.f[f][(size_t)c * d.cap + s]));
 }
 
 // sin(k pi (y - y0)/H): the derivative of the inlet velocity with respect to mode k
@@ -88,8 +88,8 @@ template <class F>
 __device__ __forceinline__ void t_walk(const Dev &d, double qx, double qy, int cx, int cy, F &&f)
 {
     const Geo &g = d.g;
-    const float rx = (float)(qx - (g.x_min + (double)cx * g.sx));
-    const float ry = (float)(qy - (g.y_min + (double)cy * g.sy));
+    const float rx = d2f(qx - (g.x_min + (double)cx * g.sx));
+    const float ry = d2f(qy - (g.y_min + (double)cy * g.sy));
     for_block(d, cx, cy, [&](int ox, int oy, int j0, int j1) {
         const float rxo = rx - (float)ox * g.sxf, ryo = ry - (float)oy * g.syf;
         for (int j = j0; j < j1; ++j) {
@@ -114,8 +114,8 @@ __device__ __forceinline__ FluidD fluid_dual(const Dev &d, const TDev &t, int c,
     f.mrho = D1(d.Ms[j]) / f.rho;
     f.u = dual(t, d, uv.x, T_U, c, s);
     f.v = dual(t, d, uv.y, T_V, c, s);
-    f.dut = D1(duv.x, tg(t, d, T_UT, c, s) - tg(t, d, T_U, c, s));
-    f.dvt = D1(duv.y, tg(t, d, T_VT, c, s) - tg(t, d, T_V, c, s));
+    f.dut = D1(duv.x, f2d(tg(t, d, T_UT, c, s) - tg(t, d, T_U, c, s)));
+    f.dvt = D1(duv.y, f2d(tg(t, d, T_VT, c, s) - tg(t, d, T_V, c, s)));
     return f;
 }
 
@@ -190,11 +190,11 @@ __global__ void t_walls_inlet(Dev d, TDev t)
                 if (ph.wall_slip[wi]) { ug = uf; vg = -vf; }
                 else { ug = D1(2.0 * ph.wall_u[wi]) - uf; vg = D1(2.0 * ph.wall_v[wi]) - vf; }
             }
-            tg(t, d, T_P, c, s) = pw.d;
-            tg(t, d, T_U, c, s) = ug.d;
-            tg(t, d, T_V, c, s) = vg.d;
-            tg(t, d, T_UT, c, s) = ug.d;
-            tg(t, d, T_VT, c, s) = vg.d;
+            tg(t, d, T_P, c, s) = d2f(pw.d);
+            tg(t, d, T_U, c, s) = d2f(ug.d);
+            tg(t, d, T_V, c, s) = d2f(vg.d);
+            tg(t, d, T_UT, c, s) = d2f(ug.d);
+            tg(t, d, T_VT, c, s) = d2f(vg.d);
         } else if (tag == INLET && ph.has_inlet) {
             // mirrored inlet pressure (Eqs. matform, taylor2) about k = (2 x_in - x_o, y_o)
             const D1 xk = D1(2.0 * ph.x_in) - Xi, yk = Yi;
@@ -208,7 +208,7 @@ __global__ void t_walls_inlet(Dev d, TDev t)
                 const double2 xl = d.XY[l];
                 double ex, ey;
                 exact_r2(g, xl.x, xl.y, xk.v, yk.v, ex, ey);
-                const D1 xlk(ex, tg(t, d, T_X, c, sl) - xk.d), ylk(ey, tg(t, d, T_Y, c, sl) - yk.d);
+                const D1 xlk(ex, f2d(tg(t, d, T_X, c, sl)) - xk.d), ylk(ey, f2d(tg(t, d, T_Y, c, sl)) - yk.d);
                 const FluidD f = fluid_dual(d, t, c, l);
                 const D1 r2 = xlk * xlk + ylk * ylk;
                 D1 w, wx(0.0), wy(0.0);
@@ -247,7 +247,7 @@ __global__ void t_walls_inlet(Dev d, TDev t)
                 }
             }
             const D1 po = pk - ((Xi - xk) * gx + (Yi - yk) * gy);
-            tg(t, d, T_P, c, s) = po.d;
+            tg(t, d, T_P, c, s) = d2f(po.d);
         }
     }
 }
@@ -308,13 +308,13 @@ __global__ void t_outlet(Dev d, TDev t)
         const D1 ub = dual(t, d, d.ubar[s], T_UBAR, c, s);
         const D1 un = ub + J2 * D1(ph.inv_2rc);
         const D1 adv = red ? un : (mr > 0 ? sadv / D1((double)mr) : ub);
-        tg(t, d, T_U, c, s) = un.d;
+        tg(t, d, T_U, c, s) = d2f(un.d);
         tg(t, d, T_V, c, s) = tg(t, d, T_VBAR, c, s);
         tg(t, d, T_P, c, s) = tg(t, d, T_PBAR, c, s) + 0.5 * J2.d;
-        tg(t, d, T_UT, c, s) = un.d;
+        tg(t, d, T_UT, c, s) = d2f(un.d);
         tg(t, d, T_VT, c, s) = tg(t, d, T_VBAR, c, s);
-        tg(t, d, T_J2P, c, s) = J2.d;
-        tg(t, d, T_ADVP, c, s) = adv.d;
+        tg(t, d, T_J2P, c, s) = d2f(J2.d);
+        tg(t, d, T_ADVP, c, s) = d2f(adv.d);
     }
 }
 
@@ -334,51 +334,51 @@ __global__ void t_stage(Dev d, TDev t, double tau)
                 tg(t, d, T_V0, c, s) = tg(t, d, T_V, c, s);
                 tg(t, d, T_P0, c, s) = tg(t, d, T_P, c, s);
             }
-            const double un = tg(t, d, T_U0, c, s) + tau * tg(t, d, T_AU, c, s);
-            const double vn = tg(t, d, T_V0, c, s) + tau * tg(t, d, T_AV, c, s);
-            const double utn = un + tau * tg(t, d, T_ABU, c, s);
-            const double vtn = vn + tau * tg(t, d, T_ABV, c, s);
-            const double pn = tg(t, d, T_P0, c, s) + tau * tg(t, d, T_AP, c, s);
-            tg(t, d, T_U, c, s) = un;
-            tg(t, d, T_V, c, s) = vn;
-            tg(t, d, T_UT, c, s) = utn;
-            tg(t, d, T_VT, c, s) = vtn;
-            tg(t, d, T_X, c, s) = tg(t, d, T_X0, c, s) + tau * utn;
-            tg(t, d, T_Y, c, s) = tg(t, d, T_Y0, c, s) + tau * vtn;
-            tg(t, d, T_P, c, s) = pn;
+            const double un = f2d(tg(t, d, T_U0, c, s)) + tau * f2d(tg(t, d, T_AU, c, s));
+            const double vn = f2d(tg(t, d, T_V0, c, s)) + tau * f2d(tg(t, d, T_AV, c, s));
+            const double utn = un + tau * f2d(tg(t, d, T_ABU, c, s));
+            const double vtn = vn + tau * f2d(tg(t, d, T_ABV, c, s));
+            const double pn = f2d(tg(t, d, T_P0, c, s)) + tau * f2d(tg(t, d, T_AP, c, s));
+            tg(t, d, T_U, c, s) = d2f(un);
+            tg(t, d, T_V, c, s) = d2f(vn);
+            tg(t, d, T_UT, c, s) = d2f(utn);
+            tg(t, d, T_VT, c, s) = d2f(vtn);
+            tg(t, d, T_X, c, s) = d2f(f2d(tg(t, d, T_X0, c, s)) + tau * utn);
+            tg(t, d, T_Y, c, s) = d2f(f2d(tg(t, d, T_Y0, c, s)) + tau * vtn);
+            tg(t, d, T_P, c, s) = d2f(pn);
             if (CORR && ph.has_outlet && ph.outlet_kind == OUT_HYBRID) {
                 // the value kernel sampled the ring iff the gate passed on the new pressure;
                 // its write position has then moved on by one
                 const double pv = d.p[s];
                 if (pv * pv * ph.inv_2rc <= ph.I_thr) {
                     const int kk = (d.rpos[s] + ph.n_avg - 1) % ph.n_avg;
-                    tg(t, d, T_RING + 3 * kk + 0, c, s) = un;
-                    tg(t, d, T_RING + 3 * kk + 1, c, s) = vn;
-                    tg(t, d, T_RING + 3 * kk + 2, c, s) = pn;
+                    tg(t, d, T_RING + 3 * kk + 0, c, s) = d2f(un);
+                    tg(t, d, T_RING + 3 * kk + 1, c, s) = d2f(vn);
+                    tg(t, d, T_RING + 3 * kk + 2, c, s) = d2f(pn);
                 }
                 double su = 0, sv = 0, sp = 0;
                 for (int q = 0; q < ph.n_avg; ++q) {
-                    su += tg(t, d, T_RING + 3 * q + 0, c, s);
-                    sv += tg(t, d, T_RING + 3 * q + 1, c, s);
-                    sp += tg(t, d, T_RING + 3 * q + 2, c, s);
+                    su += f2d(tg(t, d, T_RING + 3 * q + 0, c, s));
+                    sv += f2d(tg(t, d, T_RING + 3 * q + 1, c, s));
+                    sp += f2d(tg(t, d, T_RING + 3 * q + 2, c, s));
                 }
                 const double ub = su * ph.inv_navg, vb = sv * ph.inv_navg, pb = sp * ph.inv_navg;
-                tg(t, d, T_UBAR, c, s) = ub;
-                tg(t, d, T_VBAR, c, s) = vb;
-                tg(t, d, T_PBAR, c, s) = pb;
-                tg(t, d, T_J2, c, s) = ph.rho0 * ph.cs * (un - ub) + (pn - pb);
+                tg(t, d, T_UBAR, c, s) = d2f(ub);
+                tg(t, d, T_VBAR, c, s) = d2f(vb);
+                tg(t, d, T_PBAR, c, s) = d2f(pb);
+                tg(t, d, T_J2, c, s) = d2f(ph.rho0 * ph.cs * (un - ub) + (pn - pb));
             }
         } else if (tag == INLET) {
             if (!CORR) tg(t, d, T_X0, c, s) = tg(t, d, T_X, c, s);
             const double du = c < ph.n_modes ? mode_shape(ph, c, d.y[s]) : 0.0;
-            tg(t, d, T_U, c, s) = du;
-            tg(t, d, T_V, c, s) = 0.0;
-            tg(t, d, T_UT, c, s) = du;
-            tg(t, d, T_VT, c, s) = 0.0;
-            tg(t, d, T_X, c, s) = tg(t, d, T_X0, c, s) + tau * du;
+            tg(t, d, T_U, c, s) = d2f(du);
+            tg(t, d, T_V, c, s) = 0.0f;
+            tg(t, d, T_UT, c, s) = d2f(du);
+            tg(t, d, T_VT, c, s) = 0.0f;
+            tg(t, d, T_X, c, s) = d2f(f2d(tg(t, d, T_X0, c, s)) + tau * du);
         } else if (tag == OUTLET) {
             if (!CORR) tg(t, d, T_X0, c, s) = tg(t, d, T_X, c, s);
-            tg(t, d, T_X, c, s) = tg(t, d, T_X0, c, s) + tau * tg(t, d, T_ADVP, c, s);
+            tg(t, d, T_X, c, s) = d2f(f2d(tg(t, d, T_X0, c, s)) + tau * f2d(tg(t, d, T_ADVP, c, s)));
         }
     }
 }
@@ -525,8 +525,8 @@ __global__ void t_prep(Dev d, TDev t)
     const int n = d.cnt->n_alive;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const double2 pv = d.PV[k], rm = d.RM[k], uv = d.UV[k], duv = d.DUV[k];
-        t.vf[k] = make_float4((float)pv.x, (float)pv.y, (float)rm.x, (float)rm.y);
-        t.vg[k] = make_float4((float)uv.x, (float)uv.y, (float)duv.x, (float)duv.y);
+        t.vf[k] = make_float4(d2f(pv.x), d2f(pv.y), d2f(rm.x), d2f(rm.y));
+        t.vg[k] = make_float4(d2f(uv.x), d2f(uv.y), d2f(duv.x), d2f(duv.y));
     }
 }
 
@@ -570,7 +570,7 @@ __global__ void t_pass_a_f(Dev d, TDev t)
         });
         const double V = d.PV[k].y;
         tg(t, d, T_RHO, c, i) = dR;
-        tg(t, d, T_VOL, c, i) = (float)(-(double)dS * V * V);
+        tg(t, d, T_VOL, c, i) = d2f(-f2d(dS) * V * V);
     }
 }
 
@@ -609,13 +609,13 @@ __global__ void t_pass_b_f(Dev d, TDev t)
         const double2 pvi = d.PV[k], uvi = d.UV[k];
         const float tx = tg(t, d, T_X, c, i), ty = tg(t, d, T_Y, c, i);
         const FluidF fi = fluid_f(d, t, c, k);
-        const float mi_inv = 1.0f / (float)d.Ms[k];
+        const float mi_inv = 1.0f / d2f(d.Ms[k]);
         const int N = d.snnb[k];
         F1 ax, ay, apd, gxs, gys, sdp;
         t_walk_f(d, k, xy.x, xy.y, [&](int j, float dxf, float dyf, float r2f) {
             const FluidF fj = fluid_f(d, t, c, j);
             const double2 pvj = d.PV[j];
-            const F1 dp((float)(pvj.x - pvi.x), fj.p.d - fi.p.d);
+            const F1 dp(d2f(pvj.x - pvi.x), fj.p.d - fi.p.d);
             sdp += dp;
             if (solid && (d.stag[j] & 0x7f) != FLUID) return;
             const int sj = d.order[j];
@@ -636,8 +636,8 @@ __global__ void t_pass_b_f(Dev d, TDev t)
             const F1 hf = fi.rho * fj.rho * inv_rs * gdotr / (r2 + F1(ph.eh2f));
             const F1 vis = F1(2.0f * ph.nuf) * hf;
             const double2 uvj = d.UV[j];
-            const F1 uij((float)(uvi.x - uvj.x), fi.u.d - fj.u.d);
-            const F1 vij((float)(uvi.y - uvj.y), fi.v.d - fj.v.d);
+            const F1 uij(d2f(uvi.x - uvj.x), fi.u.d - fj.u.d);
+            const F1 vij(d2f(uvi.y - uvj.y), fi.v.d - fj.v.d);
             const F1 cgx = cij * gx, cgy = cij * gy;
             gxs += cgx;
             gys += cgy;
@@ -653,7 +653,7 @@ __global__ void t_pass_b_f(Dev d, TDev t)
             apd += fi.rho * F1(ph.c2f) * fj.mrho * (uij * gx + vij * gy) -
                    cij * F1(mi_inv * 2.0f * ph.nuef) * hf * dp;
         });
-        const F1 corr = (ph.use_pavg && !solid) ? sdp / F1((float)N) : -F1((float)pvi.x, fi.p.d);
+        const F1 corr = (ph.use_pavg && !solid) ? sdp / F1((float)N) : -F1(d2f(pvi.x), fi.p.d);
         if (solid) {
             tg(t, d, T_FX, c, i) = (ax + corr * gxs).d;
             tg(t, d, T_FY, c, i) = (ay + corr * gys).d;
