@@ -72,8 +72,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if all(os.path.getmtime(p) <= t for p in deps):
             return LIB
     nvcc = _nvcc()
-    flags = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
-             "-I" + CSRC]
+    flags = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-pthread",
+             "-I" + INCLUDE, "-I" + CSRC]
     objs = []
 
     def comp(src):
@@ -89,7 +89,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(comp, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, ARCH, "-shared", "-o", tmp] + objs
+    cmd = [nvcc, ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stderr}")

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "edac.h"
@@ -512,7 +513,6 @@ edac_status edac_set_particles(edac_ctx *ctx, int n, const double *h_x, const do
     if (n > 0 && (!h_x || !h_y || !h_u || !h_v || !h_p || !h_m || !h_tag || !h_id))
         return fail(ctx, EDAC_E_INVALID, "NULL input array");
     const Geo &g = ctx->d.g;
-    std::vector<uint64_t> ids(h_id, h_id + n);
     for (int i = 0; i < n; ++i) {
         if (h_tag[i] > EDAC_SLIPWALL) return fail(ctx, EDAC_E_INVALID, "tag out of range");
         if (!(is_fin(h_x[i]) && is_fin(h_y[i]) && is_fin(h_u[i]) && is_fin(h_v[i]) &&
@@ -526,9 +526,20 @@ edac_status edac_set_particles(edac_ctx *ctx, int n, const double *h_x, const do
         if (h_tag[i] == EDAC_OUTLET && !ctx->d.ph.has_outlet)
             return fail(ctx, EDAC_E_INVALID, "outlet particles without edac_set_outlet");
     }
-    std::sort(ids.begin(), ids.end());
-    if (std::adjacent_find(ids.begin(), ids.end()) != ids.end())
-        return fail(ctx, EDAC_E_INVALID, "duplicate particle ids");
+    // duplicate ids: a strictly increasing sequence (the usual input, and what edac_read_state
+    // returns) has none; anything else is sorted and scanned
+    bool increasing = true;
+    uint64_t max_id = n ? h_id[0] : 0;
+    for (int i = 1; i < n; ++i) {
+        increasing = increasing && h_id[i - 1] < h_id[i];
+        max_id = h_id[i] > max_id ? h_id[i] : max_id;
+    }
+    if (!increasing) {
+        std::vector<uint64_t> ids(h_id, h_id + n);
+        std::sort(ids.begin(), ids.end());
+        if (std::adjacent_find(ids.begin(), ids.end()) != ids.end())
+            return fail(ctx, EDAC_E_INVALID, "duplicate particle ids");
+    }
     Dev &d = ctx->d;
     cudaStream_t s = ctx->stream;
     CK(cudaMemsetAsync(ctx->ws, 0, ctx->ws_bytes, s));
@@ -548,7 +559,7 @@ edac_status edac_set_particles(edac_ctx *ctx, int n, const double *h_x, const do
     hc.n_alive = n;
     hc.free_top = cap - n;
     hc.n_drag = (int)drag.size();
-    hc.next_id = n ? (unsigned long long)ids.back() + 1ull : 0ull;
+    hc.next_id = n ? (unsigned long long)max_id + 1ull : 0ull;
     if (n > 0) {
         CK(cudaMemcpyAsync(d.x, h_x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(d.y, h_y, sizeof(double) * n, cudaMemcpyHostToDevice, s));
@@ -690,20 +701,53 @@ edac_status edac_read_state(edac_ctx *ctx, int cap, uint64_t *h_id, uint8_t *h_t
         }
     }
     CK(cudaStreamSynchronize(s));
-    std::vector<int> live;
-    live.reserve(C);
-    for (int i = 0; i < C; ++i)
-        if (tag[i] != TAG_DEAD) live.push_back(i);
-    std::sort(live.begin(), live.end(), [&](int a, int b) { return id[a] < id[b]; });
+    // live slots in ascending id order.  Slots keep their ids and a recycled slot takes a new,
+    // larger id, so the slot order is mostly id order: the slots that continue the increasing
+    // run are kept in place, the others (recycled slots) are sorted apart and merged in.
+    std::vector<int> run, side;
+    run.reserve(C);
+    unsigned long long last = 0;
+    bool any = false;
+    for (int i = 0; i < C; ++i) {
+        if (tag[i] == TAG_DEAD) continue;
+        if (!any || id[i] > last) {
+            run.push_back(i);
+            last = id[i];
+            any = true;
+        } else {
+            side.push_back(i);
+        }
+    }
+    auto by_id = [&](int a, int b) { return id[a] < id[b]; };
+    std::sort(side.begin(), side.end(), by_id);
+    std::vector<int> live(run.size() + side.size());
+    std::merge(run.begin(), run.end(), side.begin(), side.end(), live.begin(), by_id);
     const int nl = (int)live.size();
     *n = nl;
     if (nl > cap) return fail(ctx, EDAC_E_INVALID, "output arrays too short");
-    for (int r = 0; r < nl; ++r) {
-        const int i = live[r];
-        if (h_id) h_id[r] = id[i];
-        if (h_tag) h_tag[r] = tag[i];
-        for (int f = 0; f < nfields; ++f) h_out[f][r] = cols[f][i];
+    // the permuted copies, one host thread per output column
+    std::vector<std::thread> th;
+    auto column = [&](int f) {
+        if (f == nfields) {
+            for (int r = 0; r < nl; ++r) {
+                if (h_id) h_id[r] = id[live[r]];
+                if (h_tag) h_tag[r] = tag[live[r]];
+            }
+        } else {
+            const double *src = cols[f].data();
+            double *dst = h_out[f];
+            for (int r = 0; r < nl; ++r) dst[r] = src[live[r]];
+        }
+    };
+    for (int f = 1; f <= nfields; ++f) {
+        try {
+            th.emplace_back(column, f);
+        } catch (...) {  // no thread to be had: this thread does the column
+            column(f);
+        }
     }
+    column(0);  // field 0, or the ids and tags when no field is asked for
+    for (auto &t : th) t.join();
     return EDAC_OK;
 }
 
