@@ -41,7 +41,7 @@ FLOPS_PER_PAIR_B = 90
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the pair kernels from
 # one ncu capture of the current kernels on the 247k-particle cylinder, scaled by particle count
 # to the 1.51M workload (bytes grow with the particles: one read of the cell-ordered arrays).
-TRAFFIC = {}  # per-launch DRAM bytes of the dominant kernels, from an ncu capture of the current kernels
+TRAFFIC = {"pass_a": 112.7e6, "pass_b": 172.9e6}  # profiles/pair_kernels_cylinder_dx25_full.md (D/100)
 
 
 def parse():
