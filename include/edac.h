@@ -192,7 +192,10 @@ edac_status edac_get_count(edac_ctx *ctx, int *n_active);
 
 /* Synchronise and copy the live particles to host arrays in ascending id order:
  * h_id and h_tag (either may be NULL) and nfields fields (ids in field_ids,
- * EDAC_F_*) into h_out[f][0..n).  cap: length of every output array. */
+ * EDAC_F_*) into h_out[f][0..n).  cap: length of every output array.  The
+ * columns are permuted into id order on the device (kernels on the context's
+ * stream, with the integrator's per-step base-state arrays as scratch, which no
+ * result depends on between steps) and copied straight into the outputs. */
 edac_status edac_read_state(edac_ctx *ctx, int cap, uint64_t *h_id, uint8_t *h_tag,
                             int nfields, const int *field_ids, double *const *h_out, int *n);
 

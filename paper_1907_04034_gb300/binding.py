@@ -345,18 +345,18 @@ class Solver:
         """Live particles in ascending id order: id, tag and the requested fields."""
         fields = list(fields)
         cap = int(self.cparams.capacity)
-        ids = np.zeros(cap, dtype=np.uint64)
-        tags = np.zeros(cap, dtype=np.uint8)
-        outs = [np.zeros(cap, dtype=np.float64) for _ in fields]
+        ids = np.empty(cap, dtype=np.uint64)
+        tags = np.empty(cap, dtype=np.uint8)
+        outs = [np.empty(cap, dtype=np.float64) for _ in fields]
         fid = (C.c_int * max(1, len(fields)))(*[FIELD_ID[f] for f in fields])
         optr = (_DP * max(1, len(fields)))(*[_ptr(o, C.c_double) for o in outs])
         n = C.c_int(0)
         self._call("edac_read_state", cap, _ptr(ids, C.c_uint64), _ptr(tags, C.c_uint8),
                    len(fields), fid, optr, C.byref(n))
         k = n.value
-        out = {"id": ids[:k].copy(), "tag": tags[:k].copy()}
+        out = {"id": ids[:k], "tag": tags[:k]}
         for f, o in zip(fields, outs):
-            out[f] = o[:k].copy()
+            out[f] = o[:k]
         return out
 
     def history(self, max_steps: Optional[int] = None):

@@ -513,19 +513,58 @@ edac_status edac_set_particles(edac_ctx *ctx, int n, const double *h_x, const do
     if (n > 0 && (!h_x || !h_y || !h_u || !h_v || !h_p || !h_m || !h_tag || !h_id))
         return fail(ctx, EDAC_E_INVALID, "NULL input array");
     const Geo &g = ctx->d.g;
-    for (int i = 0; i < n; ++i) {
-        if (h_tag[i] > EDAC_SLIPWALL) return fail(ctx, EDAC_E_INVALID, "tag out of range");
-        if (!(is_fin(h_x[i]) && is_fin(h_y[i]) && is_fin(h_u[i]) && is_fin(h_v[i]) &&
-              is_fin(h_p[i]) && is_fin(h_m[i])))
-            return fail(ctx, EDAC_E_INVALID, "non-finite input value");
-        if (!(h_m[i] > 0)) return fail(ctx, EDAC_E_INVALID, "masses must be > 0");
-        if (!(h_x[i] >= g.x_min && h_x[i] < g.x_max && h_y[i] >= g.y_min && h_y[i] < g.y_max))
-            return fail(ctx, EDAC_E_DOMAIN, "particle outside the domain box");
-        if (h_tag[i] == EDAC_INLET && !ctx->d.ph.has_inlet)
-            return fail(ctx, EDAC_E_INVALID, "inlet particles without edac_set_inlet");
-        if (h_tag[i] == EDAC_OUTLET && !ctx->d.ph.has_outlet)
-            return fail(ctx, EDAC_E_INVALID, "outlet particles without edac_set_outlet");
+    Dev &d = ctx->d;
+    // Validation, in chunks on host threads (the inputs are ~50 bytes a particle); the first
+    // failing particle in input order decides the error, as a sequential scan would.  Each
+    // chunk also lists its particles counted in the drag (ascending).
+    const int nthreads = n < (1 << 16) ? 1 : 16;
+    const int chunk = (n + nthreads - 1) / nthreads;
+    std::vector<int> bad_at(nthreads, -1);
+    std::vector<edac_status> bad_st(nthreads, EDAC_OK);
+    std::vector<const char *> bad_msg(nthreads, nullptr);
+    std::vector<std::vector<int>> drag_part(nthreads);
+    auto validate = [&](int c) {
+        const int i0 = c * chunk, i1 = std::min(n, i0 + chunk);
+        for (int i = i0; i < i1; ++i) {
+            const char *why = nullptr;
+            edac_status st = EDAC_E_INVALID;
+            if (h_tag[i] > EDAC_SLIPWALL) why = "tag out of range";
+            else if (!(is_fin(h_x[i]) && is_fin(h_y[i]) && is_fin(h_u[i]) && is_fin(h_v[i]) &&
+                       is_fin(h_p[i]) && is_fin(h_m[i])))
+                why = "non-finite input value";
+            else if (!(h_m[i] > 0)) why = "masses must be > 0";
+            else if (!(h_x[i] >= g.x_min && h_x[i] < g.x_max && h_y[i] >= g.y_min && h_y[i] < g.y_max)) {
+                why = "particle outside the domain box";
+                st = EDAC_E_DOMAIN;
+            } else if (h_tag[i] == EDAC_INLET && !d.ph.has_inlet)
+                why = "inlet particles without edac_set_inlet";
+            else if (h_tag[i] == EDAC_OUTLET && !d.ph.has_outlet)
+                why = "outlet particles without edac_set_outlet";
+            if (why) {
+                bad_at[c] = i;
+                bad_st[c] = st;
+                bad_msg[c] = why;
+                return;
+            }
+            const int t = h_tag[i];
+            if ((t == EDAC_WALL && d.ph.wall_drag[0]) || (t == EDAC_SLIPWALL && d.ph.wall_drag[1]))
+                drag_part[c].push_back(i);
+        }
+    };
+    {
+        std::vector<std::thread> th;
+        for (int c = 1; c < nthreads; ++c) {
+            try {
+                th.emplace_back(validate, c);
+            } catch (...) {  // no thread to be had: this thread does the chunk
+                validate(c);
+            }
+        }
+        validate(0);
+        for (auto &t : th) t.join();
     }
+    for (int c = 0; c < nthreads; ++c)
+        if (bad_at[c] >= 0) return fail(ctx, bad_st[c], bad_msg[c]);
     // duplicate ids: a strictly increasing sequence (the usual input, and what edac_read_state
     // returns) has none; anything else is sorted and scanned
     bool increasing = true;
@@ -540,20 +579,11 @@ edac_status edac_set_particles(edac_ctx *ctx, int n, const double *h_x, const do
         if (std::adjacent_find(ids.begin(), ids.end()) != ids.end())
             return fail(ctx, EDAC_E_INVALID, "duplicate particle ids");
     }
-    Dev &d = ctx->d;
     cudaStream_t s = ctx->stream;
     CK(cudaMemsetAsync(ctx->ws, 0, ctx->ws_bytes, s));
     ctx->launches += launch_origins(ctx->d, s);
-    std::vector<uint8_t> tag(cap, TAG_DEAD);
-    for (int i = 0; i < n; ++i) tag[i] = h_tag[i];
-    std::vector<int> free_stack(cap - n);
-    for (int i = 0; i < cap - n; ++i) free_stack[i] = cap - 1 - i;
     std::vector<int> drag;
-    for (int i = 0; i < n; ++i) {
-        const int t = h_tag[i];
-        if ((t == EDAC_WALL && d.ph.wall_drag[0]) || (t == EDAC_SLIPWALL && d.ph.wall_drag[1]))
-            drag.push_back(i);
-    }
+    for (auto &p : drag_part) drag.insert(drag.end(), p.begin(), p.end());
     Counters hc;
     std::memset(&hc, 0, sizeof(hc));
     hc.n_alive = n;
@@ -569,10 +599,11 @@ edac_status edac_set_particles(edac_ctx *ctx, int n, const double *h_x, const do
         CK(cudaMemcpyAsync(d.m, h_m, sizeof(double) * n, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(d.id, h_id, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
     }
-    CK(cudaMemcpyAsync(d.tag, tag.data(), cap, cudaMemcpyHostToDevice, s));
-    if (cap - n > 0)
-        CK(cudaMemcpyAsync(d.free_stack, free_stack.data(), sizeof(int) * (cap - n),
-                           cudaMemcpyHostToDevice, s));
+    if (n > 0) CK(cudaMemcpyAsync(d.tag, h_tag, n, cudaMemcpyHostToDevice, s));
+    if (cap - n > 0) {
+        CK(cudaMemsetAsync(d.tag + n, TAG_DEAD, cap - n, s));
+        ctx->launches += launch_free_stack(d, s, n);
+    }
     if (!drag.empty())
         CK(cudaMemcpyAsync(d.drag_slots, drag.data(), sizeof(int) * drag.size(),
                            cudaMemcpyHostToDevice, s));
@@ -652,54 +683,43 @@ edac_status edac_read_state(edac_ctx *ctx, int cap, uint64_t *h_id, uint8_t *h_t
     const Dev &d = ctx->d;
     const int C = d.cap;
     cudaStream_t s = ctx->stream;
+    // field id -> device column and its type (0 double, 1 int, 2 byte)
+    std::vector<const void *> src(nfields);
+    std::vector<int> kind(nfields, 0);
+    for (int f = 0; f < nfields; ++f) {
+        switch (field_ids[f]) {
+            case EDAC_F_X: src[f] = d.x; break;
+            case EDAC_F_Y: src[f] = d.y; break;
+            case EDAC_F_U: src[f] = d.u; break;
+            case EDAC_F_V: src[f] = d.v; break;
+            case EDAC_F_UT: src[f] = d.ut; break;
+            case EDAC_F_VT: src[f] = d.vt; break;
+            case EDAC_F_P: src[f] = d.p; break;
+            case EDAC_F_M: src[f] = d.m; break;
+            case EDAC_F_RHO: src[f] = d.rho; break;
+            case EDAC_F_VOL: src[f] = d.vol; break;
+            case EDAC_F_AU: src[f] = d.au; break;
+            case EDAC_F_AV: src[f] = d.av; break;
+            case EDAC_F_AP: src[f] = d.ap; break;
+            case EDAC_F_ABU: src[f] = d.abu; break;
+            case EDAC_F_ABV: src[f] = d.abv; break;
+            case EDAC_F_FX: src[f] = d.fx; break;
+            case EDAC_F_FY: src[f] = d.fy; break;
+            case EDAC_F_UBAR: src[f] = d.ubar; break;
+            case EDAC_F_VBAR: src[f] = d.vbar; break;
+            case EDAC_F_PBAR: src[f] = d.pbar; break;
+            case EDAC_F_J2: src[f] = d.J2; break;
+            case EDAC_F_J2P: src[f] = d.J2p; break;
+            case EDAC_F_ADVP: src[f] = d.advp; break;
+            case EDAC_F_NNB: src[f] = d.nnb; kind[f] = 1; break;
+            case EDAC_F_REDP: src[f] = d.redp; kind[f] = 2; break;
+            default: src[f] = d.rpos; kind[f] = 2; break;  // EDAC_F_RPOS
+        }
+    }
     std::vector<uint8_t> tag(C);
     std::vector<unsigned long long> id(C);
     CK(cudaMemcpyAsync(tag.data(), d.tag, C, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(id.data(), d.id, sizeof(unsigned long long) * C, cudaMemcpyDeviceToHost, s));
-    std::vector<std::vector<double>> cols(nfields, std::vector<double>(C));
-    std::vector<int> ibuf(C);
-    std::vector<uint8_t> bbuf(C);
-    for (int f = 0; f < nfields; ++f) {
-        const double *src = nullptr;
-        switch (field_ids[f]) {
-            case EDAC_F_X: src = d.x; break;
-            case EDAC_F_Y: src = d.y; break;
-            case EDAC_F_U: src = d.u; break;
-            case EDAC_F_V: src = d.v; break;
-            case EDAC_F_UT: src = d.ut; break;
-            case EDAC_F_VT: src = d.vt; break;
-            case EDAC_F_P: src = d.p; break;
-            case EDAC_F_M: src = d.m; break;
-            case EDAC_F_RHO: src = d.rho; break;
-            case EDAC_F_VOL: src = d.vol; break;
-            case EDAC_F_AU: src = d.au; break;
-            case EDAC_F_AV: src = d.av; break;
-            case EDAC_F_AP: src = d.ap; break;
-            case EDAC_F_ABU: src = d.abu; break;
-            case EDAC_F_ABV: src = d.abv; break;
-            case EDAC_F_FX: src = d.fx; break;
-            case EDAC_F_FY: src = d.fy; break;
-            case EDAC_F_UBAR: src = d.ubar; break;
-            case EDAC_F_VBAR: src = d.vbar; break;
-            case EDAC_F_PBAR: src = d.pbar; break;
-            case EDAC_F_J2: src = d.J2; break;
-            case EDAC_F_J2P: src = d.J2p; break;
-            case EDAC_F_ADVP: src = d.advp; break;
-            default: break;
-        }
-        if (src) {
-            CK(cudaMemcpyAsync(cols[f].data(), src, sizeof(double) * C, cudaMemcpyDeviceToHost, s));
-        } else if (field_ids[f] == EDAC_F_NNB) {
-            CK(cudaMemcpyAsync(ibuf.data(), d.nnb, sizeof(int) * C, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            for (int i = 0; i < C; ++i) cols[f][i] = ibuf[i];
-        } else {
-            const uint8_t *b = field_ids[f] == EDAC_F_REDP ? d.redp : d.rpos;
-            CK(cudaMemcpyAsync(bbuf.data(), b, C, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            for (int i = 0; i < C; ++i) cols[f][i] = bbuf[i];
-        }
-    }
     CK(cudaStreamSynchronize(s));
     // live slots in ascending id order.  Slots keep their ids and a recycled slot takes a new,
     // larger id, so the slot order is mostly id order: the slots that continue the increasing
@@ -725,29 +745,27 @@ edac_status edac_read_state(edac_ctx *ctx, int cap, uint64_t *h_id, uint8_t *h_t
     const int nl = (int)live.size();
     *n = nl;
     if (nl > cap) return fail(ctx, EDAC_E_INVALID, "output arrays too short");
-    // the permuted copies, one host thread per output column
-    std::vector<std::thread> th;
-    auto column = [&](int f) {
-        if (f == nfields) {
-            for (int r = 0; r < nl; ++r) {
-                if (h_id) h_id[r] = id[live[r]];
-                if (h_tag) h_tag[r] = tag[live[r]];
-            }
-        } else {
-            const double *src = cols[f].data();
-            double *dst = h_out[f];
-            for (int r = 0; r < nl; ++r) dst[r] = src[live[r]];
-        }
-    };
-    for (int f = 1; f <= nfields; ++f) {
-        try {
-            th.emplace_back(column, f);
-        } catch (...) {  // no thread to be had: this thread does the column
-            column(f);
-        }
+    if (nl == 0) return EDAC_OK;
+    // The columns are permuted on the device and copied straight into the caller's arrays.
+    // Scratch: the predictor's base-state arrays, which are dead between steps (every step's
+    // predictor writes them before its corrector reads them): y0 holds the order, x0 each
+    // permuted column, u0 the permuted tags.
+    int *d_live = reinterpret_cast<int *>(d.y0);
+    double *d_col = d.x0;
+    CK(cudaMemcpyAsync(d_live, live.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, s));
+    for (int f = 0; f < nfields; ++f) {
+        ctx->launches += launch_permute(s, src[f], kind[f], d_live, nl, d_col);
+        CK(cudaMemcpyAsync(h_out[f], d_col, sizeof(double) * nl, cudaMemcpyDeviceToHost, s));
     }
-    column(0);  // field 0, or the ids and tags when no field is asked for
-    for (auto &t : th) t.join();
+    if (h_id || h_tag) {
+        unsigned long long *d_id = reinterpret_cast<unsigned long long *>(d.x0);
+        uint8_t *d_tag = reinterpret_cast<uint8_t *>(d.u0);
+        ctx->launches += launch_permute_id_tag(d, s, d_live, nl, d_id, d_tag);
+        if (h_id) CK(cudaMemcpyAsync(h_id, d_id, sizeof(uint64_t) * nl, cudaMemcpyDeviceToHost, s));
+        if (h_tag) CK(cudaMemcpyAsync(h_tag, d_tag, nl, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));  // live must outlive its copy
     return EDAC_OK;
 }
 

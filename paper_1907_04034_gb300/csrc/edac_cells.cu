@@ -636,4 +636,55 @@ int launch_origins(const Dev &d, cudaStream_t s)
     k_origins<<<(d.g.nx + d.g.ny + 255) / 256, 256, 0, s>>>(d);
     return 1;
 }
+
+namespace {
+// Free-slot stack after an upload of n particles into slots 0..n-1: slots cap-1 down to n.
+__global__ void k_free_stack(Dev d, int n)
+{
+    const int m = d.cap - n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        d.free_stack[i] = d.cap - 1 - i;
+}
+
+// out[r] = src[live[r]] for the read-back in id order; kind 0: src is double, 1: int,
+// 2: byte (integer and byte fields are widened to double).
+__global__ void k_permute(const void *src, int kind, const int *live, int n, double *out)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int s = live[r];
+        out[r] = kind == 0 ? static_cast<const double *>(src)[s]
+                           : (kind == 1 ? (double)static_cast<const int *>(src)[s]
+                                        : (double)static_cast<const uint8_t *>(src)[s]);
+    }
+}
+
+__global__ void k_permute_id_tag(Dev d, const int *live, int n, unsigned long long *id,
+                                 uint8_t *tag)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int s = live[r];
+        id[r] = d.id[s];
+        tag[r] = d.tag[s];
+    }
+}
+}  // namespace
+
+int launch_free_stack(const Dev &d, cudaStream_t s, int n)
+{
+    k_free_stack<<<grid_for(d.cap - n > 0 ? d.cap - n : 1), TPB, 0, s>>>(d, n);
+    return 1;
+}
+
+int launch_permute(cudaStream_t s, const void *src, int kind, const int *live, int n, double *out)
+{
+    k_permute<<<grid_for(n > 0 ? n : 1), TPB, 0, s>>>(src, kind, live, n, out);
+    return 1;
+}
+
+int launch_permute_id_tag(const Dev &d, cudaStream_t s, const int *live, int n,
+                          unsigned long long *id, uint8_t *tag)
+{
+    k_permute_id_tag<<<grid_for(n > 0 ? n : 1), TPB, 0, s>>>(d, live, n, id, tag);
+    return 1;
+}
 }  // namespace edac

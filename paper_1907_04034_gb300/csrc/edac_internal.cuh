@@ -349,6 +349,10 @@ __device__ __forceinline__ void inlet_uv(const Phys &ph, double y, double t, dou
 int launch_rebuild(const Dev &d, cudaStream_t s, int mixed);
 // cell-origin tables of the gather (after the workspace is cleared)
 int launch_origins(const Dev &d, cudaStream_t s);
+int launch_free_stack(const Dev &d, cudaStream_t s, int n);
+int launch_permute(cudaStream_t s, const void *src, int kind, const int *live, int n, double *out);
+int launch_permute_id_tag(const Dev &d, cudaStream_t s, const int *live, int n,
+                          unsigned long long *id, uint8_t *tag);
 // probe values (p, u, v, fluid count) into d.probe_out
 int launch_probe(const Dev &d, cudaStream_t s, const ProbePts &q);
 
