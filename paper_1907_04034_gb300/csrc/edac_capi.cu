@@ -284,10 +284,10 @@ struct Group {
     }
 };
 
-int issue_eval(edac_ctx *c, int end_of_step)
+int issue_eval(edac_ctx *c, int end_of_step, int counted = 0)
 {
     int n = 0;
-    { Group g(c, EDAC_K_REBUILD); n += launch_rebuild(c->d, c->stream, c->mixed); }
+    { Group g(c, EDAC_K_REBUILD); n += launch_rebuild(c->d, c->stream, c->mixed, counted); }
     { Group g(c, EDAC_K_PASS_A); n += launch_pass_a(c->d, c->stream, c->mixed); }
     { Group g(c, EDAC_K_BOUNDARY); n += launch_boundary(c->d, c->stream, c->mixed, end_of_step); }
     { Group g(c, EDAC_K_PASS_B); n += launch_pass_b(c->d, c->stream, c->mixed); }
@@ -297,10 +297,11 @@ int issue_eval(edac_ctx *c, int end_of_step)
 int issue_step(edac_ctx *c)
 {
     int n = 0;
-    { Group g(c, EDAC_K_STAGE); n += launch_stage(c->d, c->stream, c->mixed, 0); }
-    n += issue_eval(c, 0);
-    { Group g(c, EDAC_K_STAGE); n += launch_stage(c->d, c->stream, c->mixed, 1); }
-    n += issue_eval(c, 1);
+    // each stage also counts the particles into the cells of the evaluation that follows it
+    { Group g(c, EDAC_K_STAGE); n += launch_stage(c->d, c->stream, c->mixed, 0, 1); }
+    n += issue_eval(c, 0, 1);
+    { Group g(c, EDAC_K_STAGE); n += launch_stage(c->d, c->stream, c->mixed, 1, 1); }
+    n += issue_eval(c, 1, 1);
     { Group g(c, EDAC_K_RECYCLE); n += launch_recycle(c->d, c->stream); }
     return n;
 }

@@ -36,34 +36,37 @@ __device__ __forceinline__ bool finite_bits(double x)
     return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
 }
 
-__global__ void k_cell_count(Dev d)
+// The first step of the cell build for one live slot at (xs, ys): its cell and its place in
+// the cell's count.  Run by k_cell_count, or fused into the stages, which hold the new position.
+__device__ __forceinline__ void count_slot(const Dev &d, int s, double xs, double ys)
 {
     const Geo &g = d.g;
+    // the domain test on the unclamped cell index (integer compares; the fp64 pipe is the
+    // scarce one), non-finite positions by their exponent bits
+    const int cxr = __double2int_rd((xs - g.x_min) * g.inv_sx);
+    const int cyr = __double2int_rd((ys - g.y_min) * g.inv_sy);
+    if (!(finite_bits(xs) & finite_bits(ys) & (cxr >= 0) & (cxr < g.nx) & (cyr >= 0) &
+          (cyr < g.ny))) {
+        set_err(d, ERR_DOMAIN);
+        if (atomicCAS(&d.cnt->err_rec, 0, 1) == 0) {
+            d.cnt->err_tag = d.tag[s];
+            d.cnt->err_id = d.id[s];
+            d.cnt->err_x = xs;
+            d.cnt->err_y = ys;
+        }
+    }
+    const int cx = cxr < 0 ? 0 : (cxr >= g.nx ? g.nx - 1 : cxr);
+    const int cy = cyr < 0 ? 0 : (cyr >= g.ny ? g.ny - 1 : cyr);
+    const int c = cy * g.nx + cx;
+    d.slot_cell[s] = c;
+    d.within[s] = atomicAdd(d.cell_count + c, 1);
+}
+
+__global__ void k_cell_count(Dev d)
+{
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.cap; s += gridDim.x * blockDim.x) {
-        if (d.tag[s] == TAG_DEAD) {
-            d.slot_cell[s] = -1;
-            continue;
-        }
-        const double xs = d.x[s], ys = d.y[s];
-        // the domain test on the unclamped cell index (integer compares; the fp64 pipe is the
-        // scarce one), non-finite positions by their exponent bits
-        const int cxr = __double2int_rd((xs - g.x_min) * g.inv_sx);
-        const int cyr = __double2int_rd((ys - g.y_min) * g.inv_sy);
-        if (!(finite_bits(xs) & finite_bits(ys) & (cxr >= 0) & (cxr < g.nx) & (cyr >= 0) &
-              (cyr < g.ny))) {
-            set_err(d, ERR_DOMAIN);
-            if (atomicCAS(&d.cnt->err_rec, 0, 1) == 0) {
-                d.cnt->err_tag = d.tag[s];
-                d.cnt->err_id = d.id[s];
-                d.cnt->err_x = xs;
-                d.cnt->err_y = ys;
-            }
-        }
-        const int cx = cxr < 0 ? 0 : (cxr >= g.nx ? g.nx - 1 : cxr);
-        const int cy = cyr < 0 ? 0 : (cyr >= g.ny ? g.ny - 1 : cyr);
-        const int c = cy * g.nx + cx;
-        d.slot_cell[s] = c;
-        d.within[s] = atomicAdd(d.cell_count + c, 1);
+        if (d.tag[s] == TAG_DEAD) d.slot_cell[s] = -1;
+        else count_slot(d, s, d.x[s], d.y[s]);
     }
 }
 
@@ -253,7 +256,9 @@ __device__ __forceinline__ void ring_sample(const Dev &d, int s, double un, doub
 }
 
 
-template <bool CORR, int MIXED>
+// COUNT: also the first step of the next cell build (count_slot) at each slot's new position,
+// which saves k_cell_count its pass over the positions.
+template <bool CORR, int MIXED, bool COUNT>
 __global__ void k_stage(Dev d, double tau)
 {
     const Geo &g = d.g;
@@ -279,6 +284,7 @@ __global__ void k_stage(Dev d, double tau)
             const double pn = p0 + tau * d.ap[s];
             d.u[s] = un; d.v[s] = vn; d.ut[s] = utn; d.vt[s] = vtn;
             d.x[s] = xn; d.y[s] = yn; d.p[s] = pn;
+            if (COUNT) count_slot(d, s, xn, yn);
             if (!(finite_bits(xn) & finite_bits(yn) & finite_bits(un) & finite_bits(vn) &
                   finite_bits(pn) & finite_bits(utn) & finite_bits(vtn)))
                 set_err(d, ERR_NONFINITE);
@@ -298,11 +304,18 @@ __global__ void k_stage(Dev d, double tau)
             double uin, vin;  // the inlet velocity at the end of the stage
             inlet_uv(ph, d.y[s], (double)d.cnt->step * ph.dt + tau, uin, vin);
             d.u[s] = uin; d.v[s] = vin; d.ut[s] = uin; d.vt[s] = vin;
-            d.x[s] = x0 + tau * uin;
+            const double xn = x0 + tau * uin;
+            d.x[s] = xn;
+            if (COUNT) count_slot(d, s, xn, d.y[s]);
         } else if (t == OUTLET) {
             double x0;
             if (!CORR) { x0 = d.x[s]; d.x0[s] = x0; } else { x0 = d.x0[s]; }
-            d.x[s] = x0 + tau * d.advp[s];
+            const double xn = x0 + tau * d.advp[s];
+            d.x[s] = xn;
+            if (COUNT) count_slot(d, s, xn, d.y[s]);
+        } else if (COUNT) {
+            if (t == TAG_DEAD) d.slot_cell[s] = -1;
+            else count_slot(d, s, d.x[s], d.y[s]);  // walls: not moved by the stages
         }
     }
 }
@@ -508,28 +521,35 @@ int grid_for(int n)
 
 // cell_count is all zero on entry: cleared by the workspace reset at upload and by
 // k_cell_gather of the previous build.
-int launch_rebuild(const Dev &d, cudaStream_t s, int mixed)
+int launch_rebuild(const Dev &d, cudaStream_t s, int mixed, int counted)
 {
     const int nblk = (d.g.ncells + SCAN_TILE - 1) / SCAN_TILE;
-    k_cell_count<<<grid_for(d.cap), TPB, 0, s>>>(d);
+    if (!counted) k_cell_count<<<grid_for(d.cap), TPB, 0, s>>>(d);
     k_scan_reduce<<<nblk, 1024, 0, s>>>(d);
     k_scan_top<<<1, 1024, 0, s>>>(d, nblk);
     k_scan_down<<<nblk, 1024, 0, s>>>(d);
     k_cell_scatter<<<grid_for(d.cap), TPB, 0, s>>>(d);
     if (mixed) k_cell_gather<1><<<grid_for(d.cap), TPB, 0, s>>>(d);
     else k_cell_gather<0><<<grid_for(d.cap), TPB, 0, s>>>(d);
-    return 6;
+    return counted ? 5 : 6;
 }
 
-int launch_stage(const Dev &d, cudaStream_t s, int mixed, int corrector)
+template <bool CORR, bool COUNT>
+void stage_of(const Dev &d, cudaStream_t s, int mixed, double tau)
 {
     const int gb = grid_for(d.cap);
+    if (mixed) k_stage<CORR, 1, COUNT><<<gb, TPB, 0, s>>>(d, tau);
+    else k_stage<CORR, 0, COUNT><<<gb, TPB, 0, s>>>(d, tau);
+}
+
+int launch_stage(const Dev &d, cudaStream_t s, int mixed, int corrector, int count)
+{
     if (corrector) {
-        if (mixed) k_stage<true, 1><<<gb, TPB, 0, s>>>(d, d.ph.dt);
-        else k_stage<true, 0><<<gb, TPB, 0, s>>>(d, d.ph.dt);
+        if (count) stage_of<true, true>(d, s, mixed, d.ph.dt);
+        else stage_of<true, false>(d, s, mixed, d.ph.dt);
     } else {
-        if (mixed) k_stage<false, 1><<<gb, TPB, 0, s>>>(d, 0.5 * d.ph.dt);
-        else k_stage<false, 0><<<gb, TPB, 0, s>>>(d, 0.5 * d.ph.dt);
+        if (count) stage_of<false, true>(d, s, mixed, 0.5 * d.ph.dt);
+        else stage_of<false, false>(d, s, mixed, 0.5 * d.ph.dt);
     }
     return 1;
 }

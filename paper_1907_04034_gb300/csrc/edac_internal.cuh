@@ -346,7 +346,8 @@ __device__ __forceinline__ void inlet_uv(const Phys &ph, double y, double t, dou
 
 // ------------------------------------------------------------------- host-side launchers
 // Every launcher issues its kernels on `s` and returns the number of launches issued.
-int launch_rebuild(const Dev &d, cudaStream_t s, int mixed);
+// counted: the cell count was fused into the preceding stage (launch_stage with count)
+int launch_rebuild(const Dev &d, cudaStream_t s, int mixed, int counted = 0);
 // cell-origin tables of the gather (after the workspace is cleared)
 int launch_origins(const Dev &d, cudaStream_t s);
 int launch_free_stack(const Dev &d, cudaStream_t s, int n);
@@ -372,7 +373,8 @@ int launch_tangent(const Dev &d, void *ws, cudaStream_t s, int what, double tau)
 int launch_pass_a(const Dev &d, cudaStream_t s, int mixed);
 int launch_boundary(const Dev &d, cudaStream_t s, int mixed, int end_of_step);
 int launch_pass_b(const Dev &d, cudaStream_t s, int mixed);
-int launch_stage(const Dev &d, cudaStream_t s, int mixed, int corrector);
+// count: the stage also takes the first step of the next cell build
+int launch_stage(const Dev &d, cudaStream_t s, int mixed, int corrector, int count = 0);
 int launch_recycle(const Dev &d, cudaStream_t s);
 int launch_init(const Dev &d, cudaStream_t s);
 int launch_neighbor_dump(const Dev &d, cudaStream_t s, int mixed, const long long *start,
