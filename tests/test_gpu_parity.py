@@ -378,6 +378,40 @@ def test_bad_uploads_are_rejected_on_the_host():
 
 
 @pytest.mark.gpu
+def test_large_uploads_report_the_first_bad_particle():
+    """Uploads of 2^16 particles or more are validated in chunks on host threads; the error is
+    still the one of the first bad particle in input order, whichever chunk finds it, and a
+    rejected upload leaves the context's state as it was."""
+    import copy
+
+    c = cases.cylinder(dx=1.0 / 25.0)  # 98,491 particles
+    assert c.n > 1 << 16
+    s = binding.Solver(c, precision="mixed")
+    before = s.state(("x", "y", "u"))
+
+    def upload_with(edits):
+        bad = copy.deepcopy(c)
+        for field, i, v in edits:
+            getattr(bad, field)[i] = v
+        with pytest.raises(binding.EdacError) as e:
+            s.upload(bad)
+        return e.value
+
+    # outside the box (code 7) at 70000 before a non-finite value (code 1) at 90000, and back
+    e = upload_with([("x", 70000, 99.0), ("u", 90000, float("nan"))])
+    assert e.code == 7 and "outside the domain" in str(e)
+    e = upload_with([("u", 70000, float("nan")), ("x", 90000, 99.0)])
+    assert e.code == 1 and "non-finite" in str(e)
+    # in the first chunk and in the last
+    e = upload_with([("m", 5, -1.0), ("x", c.n - 1, 99.0)])
+    assert e.code == 1 and "masses" in str(e)
+    after = s.state(("x", "y", "u"))
+    for k in before:
+        np.testing.assert_array_equal(before[k], after[k], err_msg=k)
+    s.close()
+
+
+@pytest.mark.gpu
 def test_integer_pipe_conversions_equal_the_hardware_ones():
     """The kernels' fp32 <-> fp64 conversions (integer-pipe IEEE 754 widening and
     round-to-nearest-even narrowing) give the hardware conversion's bits: every float bit
