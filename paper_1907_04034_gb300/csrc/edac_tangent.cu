@@ -7,9 +7,10 @@
 // Each tangent kernel follows the value kernel it differentiates (same formulas, same
 // neighbour walk, same branch decisions, taken on the values) in dual numbers = value + one
 // derivative; blockIdx.y is the direction (mode) k.  The pair passes, which dominate, use
-// fp32 duals (F1) on the fp32 pipe; the boundary parts (walls, the mirrored inlet's 3x3
-// solve, the outlet) fp64 duals (D1).  Tangents are slot-indexed, [field][direction]
-// [capacity] fp32, in a workspace of their own.  The value kernels run unchanged; the tangent
+// fp32 duals with four derivatives (FG: one neighbour walk and one value evaluation for four
+// directions, blockIdx.y a group of four) on the fp32 pipe; the boundary parts (walls, the
+// mirrored inlet's 3x3 solve, the outlet) fp64 duals (D1).  Tangents are slot-indexed,
+// [field][direction][capacity] fp32, in a workspace of their own.  The value kernels run unchanged; the tangent
 // kernels are interleaved after them (see edac_step_tangent).
 #include "edac_internal.cuh"
 
@@ -487,48 +488,6 @@ __global__ void t_init(Dev d, TDev t)
 // fp64 fields (t_prep), separations from the cell-relative fp32 coordinates of the membership
 // test, and the differences that cancel (p_j - p_i, u_i - u_j, v_i - v_j) from the fp64
 // values, rounded once.
-struct F1 {
-    float v, d;
-    __device__ F1() : v(0.0f), d(0.0f) {}
-    __device__ F1(float a) : v(a), d(0.0f) {}
-    __device__ F1(float a, float b) : v(a), d(b) {}
-};
-__device__ __forceinline__ F1 operator+(F1 a, F1 b) { return F1(a.v + b.v, a.d + b.d); }
-__device__ __forceinline__ F1 operator-(F1 a, F1 b) { return F1(a.v - b.v, a.d - b.d); }
-__device__ __forceinline__ F1 operator-(F1 a) { return F1(-a.v, -a.d); }
-__device__ __forceinline__ F1 operator*(F1 a, F1 b) { return F1(a.v * b.v, fmaf(a.d, b.v, a.v * b.d)); }
-__device__ __forceinline__ F1 operator/(F1 a, F1 b)
-{
-    const float r = 1.0f / b.v;
-    const float q = a.v * r;
-    return F1(q, (a.d - q * b.d) * r);
-}
-__device__ __forceinline__ F1 &operator+=(F1 &a, F1 b) { a = a + b; return a; }
-
-__device__ __forceinline__ void quintic_dual_f(F1 q, F1 &w, F1 &dw)
-{
-    const float t3 = q.v < 3.0f ? 3.0f - q.v : 0.0f;
-    const float t2 = q.v < 2.0f ? 2.0f - q.v : 0.0f;
-    const float t1 = q.v < 1.0f ? 1.0f - q.v : 0.0f;
-    const float a = t3 * t3, b = t2 * t2, c = t1 * t1;
-    const float wv = t3 * a * a - 6.0f * (t2 * b * b) + 15.0f * (t1 * c * c);
-    const float w1 = -5.0f * (a * a - 6.0f * b * b + 15.0f * c * c);
-    const float w2 = 20.0f * (t3 * a - 6.0f * (t2 * b) + 15.0f * (t1 * c));
-    w = F1(wv, w1 * q.d);
-    dw = F1(w1, w2 * q.d);
-}
-
-// fp32 copies of the fields the pair tangents read, by sorted index (after the value boundary
-// kernel, so that wall and inlet pressures are the ones pass B uses)
-__global__ void t_prep(Dev d, TDev t)
-{
-    const int n = d.cnt->n_alive;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const double2 pv = d.PV[k], rm = d.RM[k], uv = d.UV[k], duv = d.DUV[k];
-        t.vf[k] = make_float4(d2f(pv.x), d2f(pv.y), d2f(rm.x), d2f(rm.y));
-        t.vg[k] = make_float4(d2f(uv.x), d2f(uv.y), d2f(duv.x), d2f(duv.y));
-    }
-}
 
 // Neighbours of sorted particle k with the membership test of the value kernels; f(j, dx, dy,
 // r2) with the fp32 separation r_k - r_j.
@@ -547,56 +506,162 @@ __device__ __forceinline__ void t_walk_f(const Dev &d, int k, double qx, double 
     });
 }
 
+// fp32 dual numbers with TG derivatives: the pair kernels carry TG directions per thread, so
+// that the neighbour walk and the values are evaluated once for all of them (the value parts
+// of every operation are shared; only the derivative parts repeat per direction).
+constexpr int TG = 4;
+static_assert(T_DIR % TG == 0, "directions per thread");
+struct FG {
+    float v, d[TG];
+    __device__ FG() : v(0.0f)
+    {
+#pragma unroll
+        for (int g = 0; g < TG; ++g) d[g] = 0.0f;
+    }
+    __device__ explicit FG(float a) : v(a)
+    {
+#pragma unroll
+        for (int g = 0; g < TG; ++g) d[g] = 0.0f;
+    }
+};
+__device__ __forceinline__ FG operator+(const FG &a, const FG &b)
+{
+    FG r;
+    r.v = a.v + b.v;
+#pragma unroll
+    for (int g = 0; g < TG; ++g) r.d[g] = a.d[g] + b.d[g];
+    return r;
+}
+__device__ __forceinline__ FG operator-(const FG &a, const FG &b)
+{
+    FG r;
+    r.v = a.v - b.v;
+#pragma unroll
+    for (int g = 0; g < TG; ++g) r.d[g] = a.d[g] - b.d[g];
+    return r;
+}
+__device__ __forceinline__ FG operator-(const FG &a)
+{
+    FG r;
+    r.v = -a.v;
+#pragma unroll
+    for (int g = 0; g < TG; ++g) r.d[g] = -a.d[g];
+    return r;
+}
+__device__ __forceinline__ FG operator*(const FG &a, const FG &b)
+{
+    FG r;
+    r.v = a.v * b.v;
+#pragma unroll
+    for (int g = 0; g < TG; ++g) r.d[g] = fmaf(a.d[g], b.v, a.v * b.d[g]);
+    return r;
+}
+__device__ __forceinline__ FG operator*(float s, const FG &a)  // a constant times a dual
+{
+    FG r;
+    r.v = s * a.v;
+#pragma unroll
+    for (int g = 0; g < TG; ++g) r.d[g] = s * a.d[g];
+    return r;
+}
+__device__ __forceinline__ FG operator/(const FG &a, const FG &b)
+{
+    const float rb = 1.0f / b.v;
+    FG r;
+    r.v = a.v * rb;
+#pragma unroll
+    for (int g = 0; g < TG; ++g) r.d[g] = (a.d[g] - r.v * b.d[g]) * rb;
+    return r;
+}
+__device__ __forceinline__ FG &operator+=(FG &a, const FG &b) { a = a + b; return a; }
+
+// fp32 copies of the fields the pair tangents read, by sorted index (after the value boundary
+// kernel, so that wall and inlet pressures are the ones pass B uses)
+__global__ void t_prep(Dev d, TDev t)
+{
+    const int n = d.cnt->n_alive;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const double2 pv = d.PV[k], rm = d.RM[k], uv = d.UV[k], duv = d.DUV[k];
+        t.vf[k] = make_float4(d2f(pv.x), d2f(pv.y), d2f(rm.x), d2f(rm.y));
+        t.vg[k] = make_float4(d2f(uv.x), d2f(uv.y), d2f(duv.x), d2f(duv.y));
+    }
+}
+
+// Directions c0 .. c0 + TG - 1 (blockIdx.y TG) of pass A's tangents: dW = W'(r) dr with
+// dr = (r_ij . dr_ij) / r, summed to d(sum W) and d(sum m W).
 __global__ void t_pass_a_f(Dev d, TDev t)
 {
-    const int c = blockIdx.y;
+    const int c0 = blockIdx.y * TG;
     const int n = d.cnt->n_alive;
     const Phys &ph = d.ph;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = d.order[k];
         const double2 xi = d.XY[k];
-        const float tx = tg(t, d, T_X, c, i), ty = tg(t, d, T_Y, c, i);
-        float dS = 0.0f, dR = 0.0f;
+        float tx[TG], ty[TG], dS[TG], dR[TG];
+#pragma unroll
+        for (int g = 0; g < TG; ++g) {
+            tx[g] = tg(t, d, T_X, c0 + g, i);
+            ty[g] = tg(t, d, T_Y, c0 + g, i);
+            dS[g] = dR[g] = 0.0f;
+        }
         t_walk_f(d, k, xi.x, xi.y, [&](int j, float dx, float dy, float r2) {
             if (!(r2 > 0.0f)) return;  // self: W(0), no derivative
             const int sj = d.order[j];
-            const float ddx = tx - tg(t, d, T_X, c, sj), ddy = ty - tg(t, d, T_Y, c, sj);
             const float r = sqrtf(r2);
-            const float dr = fmaf(dx, ddx, dy * ddy) / r;
             const float dwq = quintic_dw(r * ph.inv_hf);
-            const float dW = ph.a2hf * dwq * dr;
-            dS += dW;
-            dR = fmaf(__ldg(d.P + j).z, dW, dR);
+            const float base = ph.a2hf * dwq / r;  // dW = base (r_ij . dr_ij)
+            const float mj = __ldg(d.P + j).z;
+#pragma unroll
+            for (int g = 0; g < TG; ++g) {
+                const float ddx = tx[g] - tg(t, d, T_X, c0 + g, sj);
+                const float ddy = ty[g] - tg(t, d, T_Y, c0 + g, sj);
+                const float dW = base * fmaf(dx, ddx, dy * ddy);
+                dS[g] += dW;
+                dR[g] = fmaf(mj, dW, dR[g]);
+            }
         });
         const double V = d.PV[k].y;
-        tg(t, d, T_RHO, c, i) = dR;
-        tg(t, d, T_VOL, c, i) = d2f(-f2d(dS) * V * V);
+#pragma unroll
+        for (int g = 0; g < TG; ++g) {
+            tg(t, d, T_RHO, c0 + g, i) = dR[g];
+            tg(t, d, T_VOL, c0 + g, i) = d2f(-f2d(dS[g]) * V * V);
+        }
     }
 }
 
-struct FluidF {
-    F1 p, u, v, rho, V, mrho, dut, dvt;
+struct FluidG {
+    FG p, u, v, rho, V, mrho, dut, dvt;
 };
-__device__ __forceinline__ FluidF fluid_f(const Dev &d, const TDev &t, int c, int j)
+__device__ __forceinline__ FluidG fluid_g(const Dev &d, const TDev &t, int c0, int j)
 {
     const int s = d.order[j];
     const float4 a = t.vf[j], b = t.vg[j];
-    FluidF f;
-    f.p = F1(a.x, tg(t, d, T_P, c, s));
-    f.V = F1(a.y, tg(t, d, T_VOL, c, s));
-    f.rho = F1(a.z, tg(t, d, T_RHO, c, s));
-    f.mrho = F1(a.w, -a.w * f.rho.d / a.z);  // d(m/rho) = -(m/rho) drho / rho
-    const float tu = tg(t, d, T_U, c, s), tv = tg(t, d, T_V, c, s);
-    f.u = F1(b.x, tu);
-    f.v = F1(b.y, tv);
-    f.dut = F1(b.z, tg(t, d, T_UT, c, s) - tu);
-    f.dvt = F1(b.w, tg(t, d, T_VT, c, s) - tv);
+    FluidG f;
+    f.p.v = a.x; f.V.v = a.y; f.rho.v = a.z; f.mrho.v = a.w;
+    f.u.v = b.x; f.v.v = b.y; f.dut.v = b.z; f.dvt.v = b.w;
+    const float mr_rho = -a.w / a.z;  // d(m/rho) = -(m/rho) drho / rho
+#pragma unroll
+    for (int g = 0; g < TG; ++g) {
+        const int c = c0 + g;
+        f.p.d[g] = tg(t, d, T_P, c, s);
+        f.V.d[g] = tg(t, d, T_VOL, c, s);
+        f.rho.d[g] = tg(t, d, T_RHO, c, s);
+        f.mrho.d[g] = mr_rho * f.rho.d[g];
+        const float tu = tg(t, d, T_U, c, s), tv = tg(t, d, T_V, c, s);
+        f.u.d[g] = tu;
+        f.v.d[g] = tv;
+        f.dut.d[g] = tg(t, d, T_UT, c, s) - tu;
+        f.dvt.d[g] = tg(t, d, T_VT, c, s) - tv;
+    }
     return f;
 }
 
+// Pass B's tangents for directions c0 .. c0 + TG - 1: the value kernel's pair terms in dual
+// numbers, with the differences that cancel (p_j - p_i, u_i - u_j) taken in fp64 and rounded
+// once.
 __global__ void t_pass_b_f(Dev d, TDev t)
 {
-    const int c = blockIdx.y;
+    const int c0 = blockIdx.y * TG;
     const Phys &ph = d.ph;
     const int n = d.cnt->n_alive;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
@@ -607,38 +672,69 @@ __global__ void t_pass_b_f(Dev d, TDev t)
         const int i = d.order[k];
         const double2 xy = d.XY[k];
         const double2 pvi = d.PV[k], uvi = d.UV[k];
-        const float tx = tg(t, d, T_X, c, i), ty = tg(t, d, T_Y, c, i);
-        const FluidF fi = fluid_f(d, t, c, k);
+        float tx[TG], ty[TG];
+#pragma unroll
+        for (int g = 0; g < TG; ++g) {
+            tx[g] = tg(t, d, T_X, c0 + g, i);
+            ty[g] = tg(t, d, T_Y, c0 + g, i);
+        }
+        const FluidG fi = fluid_g(d, t, c0, k);
         const float mi_inv = 1.0f / d2f(d.Ms[k]);
         const int N = d.snnb[k];
-        F1 ax, ay, apd, gxs, gys, sdp;
+        FG ax, ay, apd, gxs, gys, sdp;
         t_walk_f(d, k, xy.x, xy.y, [&](int j, float dxf, float dyf, float r2f) {
-            const FluidF fj = fluid_f(d, t, c, j);
+            const FluidG fj = fluid_g(d, t, c0, j);
             const double2 pvj = d.PV[j];
-            const F1 dp(d2f(pvj.x - pvi.x), fj.p.d - fi.p.d);
+            FG dp = fj.p - fi.p;
+            dp.v = d2f(pvj.x - pvi.x);
             sdp += dp;
             if (solid && (d.stag[j] & 0x7f) != FLUID) return;
             const int sj = d.order[j];
-            const F1 dx(dxf, tx - tg(t, d, T_X, c, sj)), dy(dyf, ty - tg(t, d, T_Y, c, sj));
-            const F1 r2 = F1(r2f, 2.0f * fmaf(dxf, dx.d, dyf * dy.d));
-            F1 F(0.0f);
+            FG dx, dy, r2;
+            dx.v = dxf;
+            dy.v = dyf;
+            r2.v = r2f;
+#pragma unroll
+            for (int g = 0; g < TG; ++g) {
+                dx.d[g] = tx[g] - tg(t, d, T_X, c0 + g, sj);
+                dy.d[g] = ty[g] - tg(t, d, T_Y, c0 + g, sj);
+                r2.d[g] = 2.0f * fmaf(dxf, dx.d[g], dyf * dy.d[g]);
+            }
+            FG F;
             if (r2f > 0.0f) {
                 const float r = sqrtf(r2f);
-                const F1 rr(r, r2.d * 0.5f / r);
-                F1 wq, dwq;
-                quintic_dual_f(rr * F1(ph.inv_hf), wq, dwq);
-                F = F1(ph.a2hf) * dwq / rr;
+                FG rr;
+                rr.v = r;
+                const float h2r = 0.5f / r;
+#pragma unroll
+                for (int g = 0; g < TG; ++g) rr.d[g] = r2.d[g] * h2r;
+                // w'(q) and w''(q) at q = r / h: F = alpha_2/h w'(q) / r as a dual
+                const float q = r * ph.inv_hf;
+                const float t3 = q < 3.0f ? 3.0f - q : 0.0f;
+                const float t2 = q < 2.0f ? 2.0f - q : 0.0f;
+                const float t1 = q < 1.0f ? 1.0f - q : 0.0f;
+                const float a = t3 * t3, b = t2 * t2, c = t1 * t1;
+                const float w1 = -5.0f * (a * a - 6.0f * b * b + 15.0f * c * c);
+                const float w2 = 20.0f * (t3 * a - 6.0f * (t2 * b) + 15.0f * (t1 * c));
+                FG dwq;
+                dwq.v = w1;
+#pragma unroll
+                for (int g = 0; g < TG; ++g) dwq.d[g] = w2 * (rr.d[g] * ph.inv_hf);
+                F = (ph.a2hf * dwq) / rr;
             }
-            const F1 gx = F * dx, gy = F * dy, gdotr = F * r2;
-            const F1 cij = fi.V * fi.V + fj.V * fj.V;
-            const F1 inv_rs = F1(1.0f) / (fi.rho + fj.rho);
-            const F1 e_ = fi.rho * dp * inv_rs;
-            const F1 hf = fi.rho * fj.rho * inv_rs * gdotr / (r2 + F1(ph.eh2f));
-            const F1 vis = F1(2.0f * ph.nuf) * hf;
+            const FG gx = F * dx, gy = F * dy, gdotr = F * r2;
+            const FG cij = fi.V * fi.V + fj.V * fj.V;
+            const FG inv_rs = FG(1.0f) / (fi.rho + fj.rho);
+            const FG e_ = fi.rho * dp * inv_rs;
+            FG r2e = r2;
+            r2e.v += ph.eh2f;
+            const FG hf = fi.rho * fj.rho * inv_rs * gdotr / r2e;
+            const FG vis = (2.0f * ph.nuf) * hf;
             const double2 uvj = d.UV[j];
-            const F1 uij(d2f(uvi.x - uvj.x), fi.u.d - fj.u.d);
-            const F1 vij(d2f(uvi.y - uvj.y), fi.v.d - fj.v.d);
-            const F1 cgx = cij * gx, cgy = cij * gy;
+            FG uij = fi.u - fj.u, vij = fi.v - fj.v;
+            uij.v = d2f(uvi.x - uvj.x);
+            vij.v = d2f(uvi.y - uvj.y);
+            const FG cgx = cij * gx, cgy = cij * gy;
             gxs += cgx;
             gys += cgy;
             if (solid) {
@@ -646,23 +742,34 @@ __global__ void t_pass_b_f(Dev d, TDev t)
                 ay += cij * (vis * vij) - e_ * cgy;
                 return;
             }
-            const F1 Ai = fi.rho * (fi.dut * gx + fi.dvt * gy);
-            const F1 Aj = fj.rho * (fj.dut * gx + fj.dvt * gy);
-            ax += cij * (F1(0.5f) * (fi.u * Ai + fj.u * Aj) + vis * uij) - e_ * cgx;
-            ay += cij * (F1(0.5f) * (fi.v * Ai + fj.v * Aj) + vis * vij) - e_ * cgy;
-            apd += fi.rho * F1(ph.c2f) * fj.mrho * (uij * gx + vij * gy) -
-                   cij * F1(mi_inv * 2.0f * ph.nuef) * hf * dp;
+            const FG Ai = fi.rho * (fi.dut * gx + fi.dvt * gy);
+            const FG Aj = fj.rho * (fj.dut * gx + fj.dvt * gy);
+            ax += cij * (0.5f * (fi.u * Ai + fj.u * Aj) + vis * uij) - e_ * cgx;
+            ay += cij * (0.5f * (fi.v * Ai + fj.v * Aj) + vis * vij) - e_ * cgy;
+            apd += (ph.c2f * fi.rho) * fj.mrho * (uij * gx + vij * gy) -
+                   (mi_inv * 2.0f * ph.nuef) * (cij * hf * dp);
         });
-        const F1 corr = (ph.use_pavg && !solid) ? sdp / F1((float)N) : -F1(d2f(pvi.x), fi.p.d);
-        if (solid) {
-            tg(t, d, T_FX, c, i) = (ax + corr * gxs).d;
-            tg(t, d, T_FY, c, i) = (ay + corr * gys).d;
+        FG corr;
+        if (ph.use_pavg && !solid) {
+            corr = sdp / FG((float)N);
         } else {
-            tg(t, d, T_AU, c, i) = (ax + corr * gxs).d * mi_inv;
-            tg(t, d, T_AV, c, i) = (ay + corr * gys).d * mi_inv;
-            tg(t, d, T_AP, c, i) = apd.d;
-            tg(t, d, T_ABU, c, i) = -ph.pbf * mi_inv * gxs.d;
-            tg(t, d, T_ABV, c, i) = -ph.pbf * mi_inv * gys.d;
+            corr = -fi.p;
+            corr.v = -d2f(pvi.x);
+        }
+        const FG fxv = ax + corr * gxs, fyv = ay + corr * gys;
+#pragma unroll
+        for (int g = 0; g < TG; ++g) {
+            const int c = c0 + g;
+            if (solid) {
+                tg(t, d, T_FX, c, i) = fxv.d[g];
+                tg(t, d, T_FY, c, i) = fyv.d[g];
+            } else {
+                tg(t, d, T_AU, c, i) = fxv.d[g] * mi_inv;
+                tg(t, d, T_AV, c, i) = fyv.d[g] * mi_inv;
+                tg(t, d, T_AP, c, i) = apd.d[g];
+                tg(t, d, T_ABU, c, i) = -ph.pbf * mi_inv * gxs.d[g];
+                tg(t, d, T_ABV, c, i) = -ph.pbf * mi_inv * gys.d[g];
+            }
         }
     }
 }
@@ -689,6 +796,13 @@ dim3 tgrid(int n)
     return dim3((unsigned)b, T_DIR);
 }
 
+// the pair kernels: TG directions per thread
+dim3 tgrid_pair(int n)
+{
+    const dim3 g = tgrid(n);
+    return dim3(g.x, T_DIR / TG);
+}
+
 }  // namespace
 
 size_t tangent_bytes(const Dev &d)
@@ -707,11 +821,11 @@ int launch_tangent(const Dev &d, void *ws, cudaStream_t s, int what, double tau)
     const TDev t = tdev_of(d, ws);
     switch (what) {
     case TG_INIT: t_init<<<tgrid(d.cap), 128, 0, s>>>(d, t); return 1;
-    case TG_PASS_A: t_pass_a_f<<<tgrid(d.cap), 128, 0, s>>>(d, t); return 1;
+    case TG_PASS_A: t_pass_a_f<<<tgrid_pair(d.cap), 128, 0, s>>>(d, t); return 1;
     case TG_BOUNDARY: t_walls_inlet<<<tgrid(d.cap / 8 + 1), 128, 0, s>>>(d, t); return 1;
     case TG_PASS_B:
         t_prep<<<tgrid(d.cap).x, 128, 0, s>>>(d, t);
-        t_pass_b_f<<<tgrid(d.cap), 128, 0, s>>>(d, t);
+        t_pass_b_f<<<tgrid_pair(d.cap), 128, 0, s>>>(d, t);
         return 2;
     case TG_OUTLET:
         t_snapshot<<<tgrid(d.cap), 128, 0, s>>>(d, t);
