@@ -25,8 +25,6 @@ struct D1 {
     __device__ D1(double a, double b) : v(a), d(b) {}
 };
 __device__ __forceinline__ D1 operator+(D1 a, D1 b) { return D1(a.v + b.v, a.d + b.d); }
-__device__ __forceinline__ D1 operator-(D1 a, D1 b) { return D1(a.v - b.v, a.d - b.d); }
-__device__ __forceinline__ D1 operator-(D1 a) { return D1(-a.v, -a.d); }
 __device__ __forceinline__ D1 operator*(D1 a, D1 b) { return D1(a.v * b.v, a.d * b.v + a.v * b.d); }
 __device__ __forceinline__ D1 operator/(D1 a, D1 b)
 {
@@ -35,7 +33,6 @@ __device__ __forceinline__ D1 operator/(D1 a, D1 b)
     return D1(q, (a.d - q * b.d) * r);
 }
 __device__ __forceinline__ D1 &operator+=(D1 &a, D1 b) { a = a + b; return a; }
-__device__ __forceinline__ D1 &operator-=(D1 &a, D1 b) { a = a - b; return a; }
 __device__ __forceinline__ D1 dsqrt(D1 a)
 {
     const double s = sqrt(a.v);
@@ -100,28 +97,111 @@ __device__ __forceinline__ void t_walk(const Dev &d, double qx, double qy, int c
     });
 }
 
-// Fluid fields of sorted neighbour j as duals.
-struct FluidD {
-    D1 p, u, v, rho, V, mrho, dut, dvt;
+// ------------------------------------------------------------- walls and inlet mirror
+// fp64 duals with TGW derivatives: the wall and inlet tangents carry TGW directions per
+// thread, so that the neighbour walk and the fp64 values (the Shepard sums, the mirror's
+// moment sums and pivots) are evaluated once for all of them.
+constexpr int TGW = 2;
+static_assert(T_DIR % TGW == 0, "directions per thread");
+struct DG {
+    double v, d[TGW];
+    __device__ DG() : v(0.0)
+    {
+#pragma unroll
+        for (int g = 0; g < TGW; ++g) d[g] = 0.0;
+    }
+    __device__ explicit DG(double a) : v(a)
+    {
+#pragma unroll
+        for (int g = 0; g < TGW; ++g) d[g] = 0.0;
+    }
 };
-__device__ __forceinline__ FluidD fluid_dual(const Dev &d, const TDev &t, int c, int j)
+__device__ __forceinline__ DG operator+(const DG &a, const DG &b)
 {
-    const int s = d.order[j];
-    FluidD f;
-    const double2 pv = d.PV[j], rm = d.RM[j], uv = d.UV[j], duv = d.DUV[j];
-    f.p = dual(t, d, pv.x, T_P, c, s);
-    f.V = dual(t, d, pv.y, T_VOL, c, s);
-    f.rho = dual(t, d, rm.x, T_RHO, c, s);
-    f.mrho = D1(d.Ms[j]) / f.rho;
-    f.u = dual(t, d, uv.x, T_U, c, s);
-    f.v = dual(t, d, uv.y, T_V, c, s);
-    f.dut = D1(duv.x, f2d(tg(t, d, T_UT, c, s) - tg(t, d, T_U, c, s)));
-    f.dvt = D1(duv.y, f2d(tg(t, d, T_VT, c, s) - tg(t, d, T_V, c, s)));
-    return f;
+    DG r;
+    r.v = a.v + b.v;
+#pragma unroll
+    for (int g = 0; g < TGW; ++g) r.d[g] = a.d[g] + b.d[g];
+    return r;
+}
+__device__ __forceinline__ DG operator-(const DG &a, const DG &b)
+{
+    DG r;
+    r.v = a.v - b.v;
+#pragma unroll
+    for (int g = 0; g < TGW; ++g) r.d[g] = a.d[g] - b.d[g];
+    return r;
+}
+__device__ __forceinline__ DG operator-(const DG &a)
+{
+    DG r;
+    r.v = -a.v;
+#pragma unroll
+    for (int g = 0; g < TGW; ++g) r.d[g] = -a.d[g];
+    return r;
+}
+__device__ __forceinline__ DG operator*(const DG &a, const DG &b)
+{
+    DG r;
+    r.v = a.v * b.v;
+#pragma unroll
+    for (int g = 0; g < TGW; ++g) r.d[g] = a.d[g] * b.v + a.v * b.d[g];
+    return r;
+}
+__device__ __forceinline__ DG operator*(double s, const DG &a)  // a constant times a dual
+{
+    DG r;
+    r.v = s * a.v;
+#pragma unroll
+    for (int g = 0; g < TGW; ++g) r.d[g] = s * a.d[g];
+    return r;
+}
+__device__ __forceinline__ DG operator/(const DG &a, const DG &b)
+{
+    const double rb = 1.0 / b.v;
+    DG r;
+    r.v = a.v * rb;
+#pragma unroll
+    for (int g = 0; g < TGW; ++g) r.d[g] = (a.d[g] - r.v * b.d[g]) * rb;
+    return r;
+}
+__device__ __forceinline__ DG &operator+=(DG &a, const DG &b) { a = a + b; return a; }
+__device__ __forceinline__ DG &operator-=(DG &a, const DG &b) { a = a - b; return a; }
+__device__ __forceinline__ DG dsqrt(const DG &a)
+{
+    DG r;
+    r.v = sqrt(a.v);
+    const double h = r.v > 0.0 ? 1.0 / r.v : 0.0;
+#pragma unroll
+    for (int g = 0; g < TGW; ++g) r.d[g] = r.v > 0.0 ? (0.5 * a.d[g]) * h : 0.0;
+    return r;
+}
+__device__ __forceinline__ void quintic_dual(const DG &q, DG &w, DG &dw)
+{
+    const double t3 = q.v < 3.0 ? 3.0 - q.v : 0.0;
+    const double t2 = q.v < 2.0 ? 2.0 - q.v : 0.0;
+    const double t1 = q.v < 1.0 ? 1.0 - q.v : 0.0;
+    const double a = t3 * t3, b = t2 * t2, c = t1 * t1;
+    w.v = t3 * a * a - 6.0 * (t2 * b * b) + 15.0 * (t1 * c * c);
+    dw.v = -5.0 * (a * a - 6.0 * b * b + 15.0 * c * c);
+    const double w2 = 20.0 * (t3 * a - 6.0 * (t2 * b) + 15.0 * (t1 * c));
+#pragma unroll
+    for (int g = 0; g < TGW; ++g) {
+        w.d[g] = dw.v * q.d[g];
+        dw.d[g] = w2 * q.d[g];
+    }
+}
+
+__device__ __forceinline__ DG dual_g(const TDev &t, const Dev &d, double v, int f, int c0, int s)
+{
+    DG r(v);
+#pragma unroll
+    for (int g = 0; g < TGW; ++g) r.d[g] = f2d(t.f[f][(size_t)(c0 + g) * d.cap + s]);
+    return r;
 }
 
 // 3x3 solve with partial pivoting (pivots chosen on the values)
-__device__ bool solve3_dual(D1 (&M)[3][3], D1 (&b)[3], D1 (&x)[3])
+__device__ bool solve3_dual(DG (&M)[3][3], DG (&b)[3], DG (&x)[3])
 {
     int piv[3] = {0, 1, 2};
     for (int col = 0; col < 3; ++col) {
@@ -135,24 +215,23 @@ __device__ bool solve3_dual(D1 (&M)[3][3], D1 (&b)[3], D1 (&x)[3])
         if (M[pr][col].v == 0.0) return false;
         for (int r = col + 1; r < 3; ++r) {
             const int rr = piv[r];
-            const D1 f = M[rr][col] / M[pr][col];
+            const DG f = M[rr][col] / M[pr][col];
             for (int cc = col; cc < 3; ++cc) M[rr][cc] -= f * M[pr][cc];
             b[rr] -= f * b[pr];
         }
     }
     for (int col = 2; col >= 0; --col) {
         const int pr = piv[col];
-        D1 s = b[pr];
+        DG s = b[pr];
         for (int cc = col + 1; cc < 3; ++cc) s -= M[pr][cc] * x[cc];
         x[col] = s / M[pr][col];
     }
     return true;
 }
 
-// ------------------------------------------------------------- walls and inlet mirror
 __global__ void t_walls_inlet(Dev d, TDev t)
 {
-    const int c = blockIdx.y;
+    const int c0 = blockIdx.y * TGW;
     const Geo &g = d.g;
     const Phys &ph = d.ph;
     const int nb = d.cnt->n_bnd;
@@ -161,10 +240,10 @@ __global__ void t_walls_inlet(Dev d, TDev t)
         const int tag = d.stag[k] & 0x7f;
         const int s = d.order[k];
         const double2 xy = d.XY[k];
-        const D1 Xi = dual(t, d, xy.x, T_X, c, s), Yi = dual(t, d, xy.y, T_Y, c, s);
+        const DG Xi = dual_g(t, d, xy.x, T_X, c0, s), Yi = dual_g(t, d, xy.y, T_Y, c0, s);
         if (tag == WALL || tag == SLIPWALL) {
             const int cc = d.cellk[k];
-            D1 sw(0.0), sp(0.0), su(0.0), sv(0.0), mp(0.0), mu(0.0), mv(0.0);
+            DG sw, sp, su, sv, mp, mu, mv;
             int nf = 0;
             t_walk(d, xy.x, xy.y, cc % g.nx, cc / g.nx, [&](int j) {
                 if ((d.stag[j] & 0x7f) != FLUID) return;
@@ -172,36 +251,51 @@ __global__ void t_walls_inlet(Dev d, TDev t)
                 const double2 xj = d.XY[j];
                 double ex, ey;
                 exact_r2(g, xy.x, xy.y, xj.x, xj.y, ex, ey);
-                const D1 dx(ex, Xi.d - tg(t, d, T_X, c, sj)), dy(ey, Yi.d - tg(t, d, T_Y, c, sj));
-                const D1 r = dsqrt(dx * dx + dy * dy);
-                D1 w, dw;
-                quintic_dual(r * D1(ph.inv_h), w, dw);
-                const D1 W = D1(ph.a2) * w;
-                const FluidD f = fluid_dual(d, t, c, j);
-                sw += W; sp += W * f.p; su += W * f.u; sv += W * f.v;
-                mp += f.p; mu += f.u; mv += f.v;
+                DG dx(ex), dy(ey);
+#pragma unroll
+                for (int q = 0; q < TGW; ++q) {
+                    dx.d[q] = Xi.d[q] - tg(t, d, T_X, c0 + q, sj);
+                    dy.d[q] = Yi.d[q] - tg(t, d, T_Y, c0 + q, sj);
+                }
+                const DG r = dsqrt(dx * dx + dy * dy);
+                DG w, dw;
+                quintic_dual(ph.inv_h * r, w, dw);
+                const DG W = ph.a2 * w;
+                const double2 pv = d.PV[j], uv = d.UV[j];
+                const DG fp = dual_g(t, d, pv.x, T_P, c0, sj);
+                const DG fu = dual_g(t, d, uv.x, T_U, c0, sj);
+                const DG fv = dual_g(t, d, uv.y, T_V, c0, sj);
+                sw += W; sp += W * fp; su += W * fu; sv += W * fv;
+                mp += fp; mu += fu; mv += fv;
                 ++nf;
             });
             const int wi = tag == WALL ? 0 : 1;
-            D1 pw(0.0), ug(ph.wall_u[wi]), vg(ph.wall_v[wi]);
+            DG pw, ug(ph.wall_u[wi]), vg(ph.wall_v[wi]);
             if (nf > 0) {
-                D1 uf, vf;
+                DG uf, vf;
                 if (sw.v > 0.0) { pw = sp / sw; uf = su / sw; vf = sv / sw; }
-                else { pw = mp / D1((double)nf); uf = mu / D1((double)nf); vf = mv / D1((double)nf); }
+                else {
+                    const DG n_(static_cast<double>(nf));
+                    pw = mp / n_; uf = mu / n_; vf = mv / n_;
+                }
                 if (ph.wall_slip[wi]) { ug = uf; vg = -vf; }
-                else { ug = D1(2.0 * ph.wall_u[wi]) - uf; vg = D1(2.0 * ph.wall_v[wi]) - vf; }
+                else { ug = DG(2.0 * ph.wall_u[wi]) - uf; vg = DG(2.0 * ph.wall_v[wi]) - vf; }
             }
-            tg(t, d, T_P, c, s) = d2f(pw.d);
-            tg(t, d, T_U, c, s) = d2f(ug.d);
-            tg(t, d, T_V, c, s) = d2f(vg.d);
-            tg(t, d, T_UT, c, s) = d2f(ug.d);
-            tg(t, d, T_VT, c, s) = d2f(vg.d);
+#pragma unroll
+            for (int q = 0; q < TGW; ++q) {
+                const int c = c0 + q;
+                tg(t, d, T_P, c, s) = d2f(pw.d[q]);
+                tg(t, d, T_U, c, s) = d2f(ug.d[q]);
+                tg(t, d, T_V, c, s) = d2f(vg.d[q]);
+                tg(t, d, T_UT, c, s) = d2f(ug.d[q]);
+                tg(t, d, T_VT, c, s) = d2f(vg.d[q]);
+            }
         } else if (tag == INLET && ph.has_inlet) {
             // mirrored inlet pressure (Eqs. matform, taylor2) about k = (2 x_in - x_o, y_o)
-            const D1 xk = D1(2.0 * ph.x_in) - Xi, yk = Yi;
+            const DG xk = DG(2.0 * ph.x_in) - Xi, yk = Yi;
             const int cx = cell_coord(xk.v, g.x_min, g.inv_sx, g.nx);
             const int cy = cell_coord(yk.v, g.y_min, g.inv_sy, g.ny);
-            D1 M[3][3], bb[3], mean(0.0);
+            DG M[3][3], bb[3], mean;
             int nl = 0;
             t_walk(d, xk.v, yk.v, cx, cy, [&](int l) {
                 if ((d.stag[l] & 0x7f) != FLUID) return;
@@ -209,46 +303,55 @@ __global__ void t_walls_inlet(Dev d, TDev t)
                 const double2 xl = d.XY[l];
                 double ex, ey;
                 exact_r2(g, xl.x, xl.y, xk.v, yk.v, ex, ey);
-                const D1 xlk(ex, f2d(tg(t, d, T_X, c, sl)) - xk.d), ylk(ey, f2d(tg(t, d, T_Y, c, sl)) - yk.d);
-                const FluidD f = fluid_dual(d, t, c, l);
-                const D1 r2 = xlk * xlk + ylk * ylk;
-                D1 w, wx(0.0), wy(0.0);
+                DG xlk(ex), ylk(ey);
+#pragma unroll
+                for (int q = 0; q < TGW; ++q) {
+                    xlk.d[q] = f2d(tg(t, d, T_X, c0 + q, sl)) - xk.d[q];
+                    ylk.d[q] = f2d(tg(t, d, T_Y, c0 + q, sl)) - yk.d[q];
+                }
+                const double2 pv = d.PV[l], rm = d.RM[l];
+                const DG fp = dual_g(t, d, pv.x, T_P, c0, sl);
+                const DG frho = dual_g(t, d, rm.x, T_RHO, c0, sl);
+                const DG fmrho = DG(d.Ms[l]) / frho;
+                const DG r2 = xlk * xlk + ylk * ylk;
+                DG w, wx, wy;
                 if (r2.v > 1e-30) {
-                    const D1 r = dsqrt(r2);
-                    D1 wq, dwq;
-                    quintic_dual(r * D1(ph.inv_h), wq, dwq);
-                    w = D1(ph.a2) * wq;
-                    const D1 dwr = D1(ph.a2h) * dwq / r;
+                    const DG r = dsqrt(r2);
+                    DG wq, dwq;
+                    quintic_dual(ph.inv_h * r, wq, dwq);
+                    w = ph.a2 * wq;
+                    const DG dwr = (ph.a2h * dwq) / r;
                     wx = dwr * xlk;
                     wy = dwr * ylk;
                 } else {
-                    w = D1(ph.a2 * quintic_w(0.0));
+                    w = DG(ph.a2 * quintic_w(0.0));
                 }
-                const D1 row[3] = {w * f.mrho, wx * f.mrho, wy * f.mrho};
+                const DG row[3] = {w * fmrho, wx * fmrho, wy * fmrho};
                 for (int q = 0; q < 3; ++q) {
                     M[q][0] += row[q];
                     M[q][1] += xlk * row[q];
                     M[q][2] += ylk * row[q];
-                    bb[q] += f.p * row[q];
+                    bb[q] += fp * row[q];
                 }
-                mean += f.p;
+                mean += fp;
                 ++nl;
             });
-            D1 pk(0.0), gx(0.0), gy(0.0);
+            DG pk, gx, gy;
             if (nl > 0 && !(M[0][0].v > 0.0)) {
-                pk = mean / D1((double)nl);
+                pk = mean / DG(static_cast<double>(nl));
             } else if (nl > 0) {
                 const double det = M[0][0].v * (M[1][1].v * M[2][2].v - M[1][2].v * M[2][1].v) -
                                    M[0][1].v * (M[1][0].v * M[2][2].v - M[1][2].v * M[2][0].v) +
                                    M[0][2].v * (M[1][0].v * M[2][1].v - M[1][1].v * M[2][0].v);
                 pk = bb[0] / M[0][0];
                 if (!(fabs(det) <= 1e-9 * fabs(M[0][0].v * M[1][1].v * M[2][2].v))) {
-                    D1 sol[3];
+                    DG sol[3];
                     if (solve3_dual(M, bb, sol)) { pk = sol[0]; gx = sol[1]; gy = sol[2]; }
                 }
             }
-            const D1 po = pk - ((Xi - xk) * gx + (Yi - yk) * gy);
-            tg(t, d, T_P, c, s) = d2f(po.d);
+            const DG po = pk - ((Xi - xk) * gx + (Yi - yk) * gy);
+#pragma unroll
+            for (int q = 0; q < TGW; ++q) tg(t, d, T_P, c0 + q, s) = d2f(po.d[q]);
         }
     }
 }
@@ -822,7 +925,11 @@ int launch_tangent(const Dev &d, void *ws, cudaStream_t s, int what, double tau)
     switch (what) {
     case TG_INIT: t_init<<<tgrid(d.cap), 128, 0, s>>>(d, t); return 1;
     case TG_PASS_A: t_pass_a_f<<<tgrid_pair(d.cap), 128, 0, s>>>(d, t); return 1;
-    case TG_BOUNDARY: t_walls_inlet<<<tgrid(d.cap / 8 + 1), 128, 0, s>>>(d, t); return 1;
+    case TG_BOUNDARY: {
+        const dim3 gb = tgrid(d.cap / 8 + 1);
+        t_walls_inlet<<<dim3(gb.x, T_DIR / TGW), 128, 0, s>>>(d, t);
+        return 1;
+    }
     case TG_PASS_B:
         t_prep<<<tgrid(d.cap).x, 128, 0, s>>>(d, t);
         t_pass_b_f<<<tgrid_pair(d.cap), 128, 0, s>>>(d, t);
