@@ -742,3 +742,161 @@ def test_slip_wall_keeps_tangential_flow_and_no_slip_wall_brakes_it():
         assert np.abs(f["v"][f["tag"] == FLUID]).max() < 5e-3
     assert abs(out[1] - 0.5) < 5e-3, out
     assert out[0] < 0.4, out
+
+
+# ----------------------------------------- A-term, blue rule, time window, integrator order
+def test_A_term_is_the_divergence_of_rho_u_times_the_shift():
+    """The A-term of Eq. tvf-momentum, 1/2 (A_i + A_j).gW with A = rho u (x) (u~ - u), is the
+    SPH form of div(A)/rho.  With u = (U, 0), p = 0 and u~ - u = (0, gamma y) that is
+    d/dy(rho U gamma y)/rho = U gamma in x and 0 in y (interior of an open lattice).  The
+    transposed tensor rho (u~ - u) (x) u gives 0 in x, a flipped sign -U gamma; the viscous and
+    pressure terms vanish (uniform u, p = 0), so the A-term alone is measured."""
+    c = _open_lattice(n=30)
+    U, gamma = 0.8, 0.35
+    c.u[:] = U
+    o = oracle.OracleSim(c)
+    n = o.n
+    o.a["vt"][:n] = o.a["v"][:n] + gamma * o.a["y"][:n]
+    o.evaluate()
+    sel = _interior(o, c)
+    au, av = o.field("au")[sel], o.field("av")[sel]
+    np.testing.assert_allclose(au, U * gamma, rtol=2e-3)
+    assert np.abs(av).max() < 1e-10 * U * gamma
+    # with u~ = u the same state has no A-term: the rate above is the A-term's alone
+    o.a["vt"][:n] = o.a["v"][:n]
+    o.evaluate()
+    assert np.abs(o.field("au")[sel]).max() < 1e-10 * U * gamma
+
+
+def test_A_term_shift_along_the_flow():
+    """Second orientation check of A = rho u (x) (u~ - u): u = (0, V), u~ - u = (gamma x, 0) gives
+    div(A)_y / rho = d/dx(rho V gamma x)/rho = V gamma in y and 0 in x."""
+    c = _open_lattice(n=30)
+    V, gamma = -0.6, 0.45
+    c.v[:] = V
+    o = oracle.OracleSim(c)
+    n = o.n
+    o.a["ut"][:n] = o.a["u"][:n] + gamma * o.a["x"][:n]
+    o.evaluate()
+    sel = _interior(o, c)
+    np.testing.assert_allclose(o.field("av")[sel], V * gamma, rtol=2e-3)
+    assert np.abs(o.field("au")[sel]).max() < 1e-10 * abs(V * gamma)
+
+
+def test_blue_outlet_particles_take_the_previous_red_mean():
+    """Eq. average_old (Sec. 3.4): an outlet particle without fluid in reach ("blue") takes J2
+    as the mean of the previous step's J2 over the outlet particles within 3h that were red in
+    the previous step (self included), 0 if there are none, and the mean of their previous
+    advection velocities (else its frozen u average).  The stored previous-step values and red
+    flags are planted at random (blue particles among the flagged ones, so that the flag and
+    not the current class decides), one step is taken, and every blue particle's p - p_bar,
+    u - u_bar, stored J2 and advection velocity are checked against a numpy evaluation over
+    the brute-force neighbour lists."""
+    c = cases.channel(jitter=0.0, pulse_amp=0.0, n_in=4, n_out=8)
+    o = oracle.OracleSim(c)
+    n = o.n
+    rng = np.random.default_rng(21)
+    tag = o.a["tag"][:n]
+    out = tag == OUTLET
+    J2p0 = np.where(out, rng.normal(0.0, 0.02, n), 0.0)
+    adv0 = np.where(out, rng.uniform(0.8, 1.2, n), o.a["advp"][:n])
+    red0 = np.where(out, rng.integers(0, 2, n), 0).astype(np.int32)
+    o.a["J2p"][:n] = J2p0
+    o.a["advp"][:n] = adv0
+    o.a["redp"][:n] = red0
+    hist = o.step(1)
+    assert hist[0]["n_delete"] == hist[0]["n_to_outlet"] == hist[0]["n_spawn"] == 0
+    assert o.n == n
+    f = o.fields(("tag", "p", "u", "J2p", "advp", "redp", "ubar", "pbar"))
+    start, idx = o.neighbors()
+    rho_c = c.params.rho0 * c.params.cs
+    nblue = nmix = 0
+    for k in np.nonzero(f["tag"] == OUTLET)[0]:
+        nb = idx[start[k]:start[k + 1]]
+        if np.any(f["tag"][nb] == FLUID):
+            continue
+        nblue += 1
+        assert f["redp"][k] == 0
+        prev = nb[(f["tag"][nb] == OUTLET) & (red0[nb] == 1)]
+        J2 = J2p0[prev].mean() if len(prev) else 0.0
+        adv = adv0[prev].mean() if len(prev) else f["ubar"][k]
+        nmix += len(prev) > 0 and len(prev) < np.count_nonzero(f["tag"][nb] == OUTLET)
+        assert f["J2p"][k] == pytest.approx(J2, rel=1e-13, abs=1e-16)
+        assert f["p"][k] - f["pbar"][k] == pytest.approx(0.5 * J2, rel=1e-12, abs=1e-16)
+        assert f["u"][k] - f["ubar"][k] == pytest.approx(J2 / (2 * rho_c), rel=1e-9, abs=1e-16)
+        assert f["advp"][k] == pytest.approx(adv, rel=1e-13)
+    assert nblue > 50 and nmix > 50
+
+
+def test_time_average_is_a_moving_window_of_n_avg_samples():
+    """Eq. timeevg with N = n_avg = 6: after an ungated update, the average is the mean of the
+    last six samples, i.e. the ring with its oldest entry (at the write index) replaced by the
+    current value; the write index advances by one modulo 6 and J2 = rho0 c (u - u_bar) +
+    (p - p_bar) (Eq. characteristic-vars against the average).  Rings and write indices are
+    planted at random on every fluid particle."""
+    c = cases.channel()
+    o = oracle.OracleSim(c)
+    n = o.n
+    navg = c.params.n_avg
+    assert navg == 6
+    rng = np.random.default_rng(5)
+    fl = o.a["tag"][:n] == FLUID
+    ring = o.a["ring"].reshape(-1, oracle.NAVG_MAX, 3)
+    planted = rng.normal(0.0, 0.3, (n, navg, 3)) + np.array([1.0, 0.0, 0.0])
+    ring[:n, :navg][fl] = planted[fl]
+    rpos0 = rng.integers(0, navg, n).astype(np.int32)
+    o.a["rpos"][:n] = np.where(fl, rpos0, o.a["rpos"][:n])
+    o.step(1)
+    assert o.n == n
+    f = o.fields(("tag", "u", "v", "p", "ubar", "vbar", "pbar", "J2", "rpos"))
+    assert np.array_equal(f["tag"] == FLUID, fl)
+    rho_c = c.params.rho0 * c.params.cs
+    I = (0.5 * c.params.rho0 * c.params.U ** 2) ** 2 / (2 * c.params.rho0 * c.params.cs)
+    assert np.all(f["p"][fl] ** 2 / (2 * c.params.rho0 * c.params.cs) <= I)  # ungated
+    for i in np.nonzero(fl)[0]:
+        win = planted[i].copy()
+        win[rpos0[i]] = (f["u"][i], f["v"][i], f["p"][i])
+        for comp, key in enumerate(("ubar", "vbar", "pbar")):
+            assert f[key][i] == pytest.approx(win[:, comp].sum() / navg, rel=1e-13, abs=1e-15)
+        assert f["rpos"][i] == (rpos0[i] + 1) % navg
+        assert f["J2"][i] == pytest.approx(rho_c * (f["u"][i] - f["ubar"][i])
+                                           + (f["p"][i] - f["pbar"][i]), rel=1e-9, abs=1e-13)
+
+
+def test_integrator_stages_local_error():
+    """The integrator (the paper defers it to the EDAC paper; read as the midpoint
+    predictor-corrector whose stages update u, then u~ = u + tau a_bg, then x = x^n + tau u~,
+    then p): velocity and pressure take the rates at the midpoint state, so their one-step
+    error is O(h^3) (falling 8 times per halving of h; forward Euler, or a predictor of length
+    h, gives O(h^2), a factor 4); the position takes the transport velocity at the end of the
+    stage, x^(n+1) = x^n + h u^(n+1) = x^n + h u^n + h^2 a^(n+1/2), whose one-step error is
+    +h^2 a / 2 (a position update with the midpoint velocity would give 0, one with u^n
+    -h^2 a / 2).  Reference: the same state after 64 steps of h / 64.  p_b = 0 (no transport
+    shift, itself proportional to h) and p_avg off (its neighbour count is not smooth in the
+    positions) keep the map smooth; the seeded jitter makes the lattice disordered."""
+    def make(h):
+        c = cases.taylor_green(n=16, nu=0.05, jitter=0.2, seed=9)
+        c.params.pb = 0.0
+        c.params.use_pavg = 0
+        c.params.dt = h
+        return c
+
+    dt = cases.taylor_green(n=16, nu=0.05).params.dt
+    o0 = oracle.OracleSim(make(dt))
+    a0 = np.concatenate([o0.field("au"), o0.field("av")])
+    err_u, err_p, coef = {}, {}, {}
+    for h in (dt, dt / 2, dt / 4):
+        o = oracle.OracleSim(make(h))
+        o.step(1)
+        r = oracle.OracleSim(make(h / 64))
+        r.step(64)
+        err_u[h] = np.abs(o.field("u") - r.field("u")).max()
+        err_p[h] = np.abs(o.field("p") - r.field("p")).max()
+        dxy = np.concatenate([o.field("x") - r.field("x"), o.field("y") - r.field("y")])
+        coef[h] = dxy / (0.5 * h * h * a0)
+    for e in (err_u, err_p):
+        assert 7.0 < e[dt] / e[dt / 2] < 9.0, e
+        assert 7.0 < e[dt / 2] / e[dt / 4] < 9.0, e
+    sel = np.abs(a0) > 0.3 * np.abs(a0).max()
+    c4 = coef[dt / 4][sel]
+    assert np.all(np.abs(c4 - 1.0) < 0.07), (c4.min(), c4.max())
