@@ -38,10 +38,9 @@ FLOPS_PER_PAIR_A = 20
 FLOPS_PER_PAIR_B = 90
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the pair kernels from
-# one ncu capture of the current kernels on the 247k-particle cylinder, scaled by particle count
-# to the 1.51M workload (bytes grow with the particles: one read of the cell-ordered arrays).
-TRAFFIC = {"pass_a": 112.7e6, "pass_b": 172.9e6}  # profiles/pair_kernels_cylinder_dx25_full.md (D/100)
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the pair kernels,
+# measured with ncu on the 1.51M-particle workload itself.
+TRAFFIC = {"pass_a": 112.7e6, "pass_b": 172.9e6}
 
 
 def parse():
@@ -59,6 +58,11 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--tangent-steps", type=int, default=400,
                     help="steps of the gradient workload (0: skip it)")
+    ap.add_argument("--force-steps", type=int, default=2000,
+                    help="steps over which the mixed path's drag and lift are compared with "
+                         "the fp64 path's")
+    ap.add_argument("--developed-steps", type=int, default=400,
+                    help="steps timed after --force-steps steps (a flow past its start)")
     return ap.parse_args()
 
 
@@ -267,7 +271,8 @@ def run_tangent(steps, dev):
 
 # -------------------------------------------------------------------------- reference
 def cpu_oracle_rate(case, steps):
-    """The oracle as it stands (binned neighbour mode, OpenMP on all host cores)."""
+    """The oracle as it stands (binned neighbour mode, OpenMP on all host cores); also its
+    force history over those steps."""
     import oracle
     t0 = time.perf_counter()
     sim = oracle.OracleSim(case, neighbor_mode=1)
@@ -276,7 +281,9 @@ def cpu_oracle_rate(case, steps):
     hist = sim.step(steps)
     dt = time.perf_counter() - t0
     ps = float(sum(h["n_active"] for h in hist))
-    return ps / dt, dt, t_init
+    fx = np.array([h["fx"] for h in hist])
+    fy = np.array([h["fy"] for h in hist])
+    return ps / dt, dt, t_init, fx, fy
 
 
 def run_reference(args, rank, world, dist):
@@ -326,7 +333,8 @@ def main():
     torch.cuda.set_device(dev)
     case = cases.cylinder(dx=args.dx)
     K, W = args.steps, args.warmup
-    hist_cap = max(4096, K + W + 64)
+    F = max(args.force_steps, 0)
+    hist_cap = max(4096, K + W + 200 + F + args.developed_steps)
 
     # ---------------------------------------------------------------- mixed (headline)
     sm = binding.Solver(case, precision="mixed", use_graphs=True, device=str(dev),
@@ -351,7 +359,6 @@ def main():
     ps_local = float(np.sum(h["n_active"]))
     t_max, ps_all = reduce_max_sum(dist, ms / 1e3, ps_local, dev if dist else None)
     value = ps_all / t_max
-    fx_mixed = sm.history(W + K)["fx"]
 
     # --------------------------------------------- roofline of the dominant kernel (pass B)
     nb = sm.state(("nnb",))
@@ -391,6 +398,33 @@ def main():
     kernels = {k: round(v["ms_per_launch"], 5) for k, v in prof.items()}
     for k, (pp, f) in cand.items():
         kernels[k + "_tflops"] = pp * f / (prof[k]["ms_per_launch"] * 1e-3) / 1e12
+    # the same run past its start: to F steps, then Kd steps timed (graph replay, events)
+    developed = None
+    done = W + K + kp
+    Kd = args.developed_steps
+    if Kd > 0:
+        if F > done:
+            sm.step(F - done)
+            done = F
+        torch.cuda.synchronize(dev)
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        sm.step(Kd)
+        d1.record(stream)
+        torch.cuda.synchronize(dev)
+        dms = d0.elapsed_time(d1)
+        hd = sm.history(Kd)
+        nbd = sm.state(("nnb",))
+        developed = {"value": float(np.sum(hd["n_active"])) / (dms * 1e-3) * world, "unit": UNIT,
+                     "ms_per_step": dms / Kd, "steps_timed": Kd, "steps_before": done,
+                     "mean_neighbours": float(np.mean(nbd["nnb"])),
+                     "mean_neighbours_at_headline": float(np.mean(nb["nnb"])),
+                     "note": "the headline's run continued past the impulsive start (t = "
+                             f"{done * case.params.dt:.3f} D/U), same graph, CUDA events"}
+        done += Kd
+    fx_mixed = sm.history(done)["fx"]
+    fy_mixed = sm.history(done)["fy"]
     sm.close()
     del sm
     torch.cuda.empty_cache()
@@ -410,7 +444,10 @@ def main():
     ms64 = e0.elapsed_time(e1)
     h64 = s64.history(K64)
     v64 = float(np.sum(h64["n_active"])) / (ms64 / 1e3) * world
-    fx64 = s64.history(W + K64)["fx"]
+    if F > W + K64:
+        s64.step(F - W - K64)
+    h64all = s64.history(max(F, W + K64))
+    fx64, fy64 = h64all["fx"], h64all["fy"]
     # fp64 pair passes against the measured fp64 FMA peak
     kp64 = 2
     for kname in ("pass_b", "pass_a"):
@@ -427,6 +464,14 @@ def main():
     nc = min(len(fx64), len(fx_mixed))
     scale = max(float(np.abs(fx64[:nc]).max()), 1e-12)
     drag_err = float(np.abs(fx_mixed[:nc] - fx64[:nc]).max()) / scale
+    forces = {"steps": nc,
+              "drag_max_rel": drag_err,
+              "lift_max_rel_to_drag": float(np.abs(fy_mixed[:nc] - fy64[:nc]).max()) / scale,
+              "mean_drag_rel": float(abs(fx_mixed[:nc].mean() - fx64[:nc].mean())
+                                     / max(abs(fx64[:nc].mean()), 1e-300)),
+              "fp64_lift_max": float(np.abs(fy64[:nc]).max()),
+              "note": "mixed vs fp64 GPU path, per step from the impulsive start; the lift is "
+                      "round-off this early (symmetric flow), so it is scaled by the drag"}
     s64.close()
     del s64
     torch.cuda.empty_cache()
@@ -466,10 +511,19 @@ def main():
     # ---------------------------------------------------------------------- CPU baseline
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, el, t_init = cpu_oracle_rate(case, args.cpu_steps)
+        rate, el, t_init, fxo, fyo = cpu_oracle_rate(case, args.cpu_steps)
         cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{args.cpu_steps} full oracle steps of the workload ({case.n} particles), "
                          f"binned-neighbour mode, fp64, OpenMP, {el:.1f} s"}
+        no = min(len(fxo), len(fx_mixed), len(fx64))
+        if no:
+            so = max(float(np.abs(fxo[:no]).max()), 1e-300)
+            forces["vs_oracle"] = {
+                "steps": no,
+                "mixed_drag_max_rel": float(np.abs(fx_mixed[:no] - fxo[:no]).max()) / so,
+                "mixed_lift_max_rel_to_drag": float(np.abs(fy_mixed[:no] - fyo[:no]).max()) / so,
+                "fp64_drag_max_rel": float(np.abs(fx64[:no] - fxo[:no]).max()) / so,
+                "fp64_lift_max_rel_to_drag": float(np.abs(fy64[:no] - fyo[:no]).max()) / so}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -486,6 +540,7 @@ def main():
                               "pair_kernels": roof64},
                 "mixed_over_fp64": value / v64 if v64 else None,
                 "drag_rel_err_mixed_vs_fp64": drag_err, "drag_steps_compared": nc,
+                "forces_mixed_vs_fp64": forces, "developed": developed,
                 "batched": batched,
                 "gradient": tangent,
                 "kernel_ms_per_launch": kernels, "eager_step_ms": step_ms_eager}

@@ -103,12 +103,21 @@ def test_neighbor_sets_bit_exact(prec, name):
 
 # ------------------------------------------------------------------------ step windows
 def _compare_window(s, ref, prec, tol_mult=1.0):
+    """State after a window of steps: positions, velocities, pressure and density of every
+    particle, and the rates of the step's last evaluation (du/dt, dp/dt, on the floors of
+    EVAL_FIELDS) of the fluid particles, the ones the next predictor integrates with (the
+    oracle zeroes the rates of the other tags at every evaluation; the library leaves those
+    unused slots alone)."""
     g = s.state(("x", "y", "u", "v", "p", "rho", "au", "ap"))
     r = ref.fields()
     np.testing.assert_array_equal(g["id"], r["id"])
     np.testing.assert_array_equal(g["tag"], r["tag"])
+    p = ref.params
     errs = {k: _rel_err(g[k], r[k], f) for k, f in
             (("x", 1.0), ("y", 1.0), ("u", 1.0), ("v", 1.0), ("p", 0.5), ("rho", 1.0))}
+    fl = r["tag"] == FLUID
+    errs.update({k: _rel_err(g[k][fl], r[k][fl], f) for k, f in
+                 (("au", p.U ** 2 / p.h), ("ap", p.rho0 * p.U ** 3 / p.h))})
     bad = {k: v for k, v in errs.items() if not v < TOL[prec] * tol_mult}
     assert not bad, f"{prec}: {bad}"
     return errs
@@ -730,12 +739,30 @@ def test_mean_drag_autograd_function():
 
 @pytest.mark.gpu
 def test_tangent_gradient_on_the_d25_cylinder_over_400_steps():
-    """The gradient workload: cylinder at dx = D/25 (~98k particles), modes a_k ~ N(0, 0.02)
-    (seed 0), mean drag over 400 steps.  Central differences (eps = 1e-6) of two modes agree
-    with the tangent model to 1e-5 relative.  p_avg is off here: its neighbour count jumps when
-    a pair crosses the support radius, so the map that central differences see is not smooth,
-    while the tangent model holds the neighbour sets fixed (with p_avg on, the short windows of
-    the tests above agree to ~1e-8)."""
+    """The gradient workload as configured: cylinder at dx = D/25 (~98k particles), p_avg on,
+    modes a_k ~ N(0, 0.02) (seed 0), mean drag over 400 steps.  Central differences of all 8
+    modes agree with the tangent model to 1e-5 of the largest component.  The step size of the
+    differences is eps = 1e-8: with p_avg on, the neighbour count in p_avg jumps when a pair
+    crosses the support radius, and at eps = 1e-6 and 1e-7 some +-eps runs take such a
+    crossing one step apart (their neighbour counts differ mid-run), which adds a term the
+    map's derivative does not have (up to 3e-2 of the smallest components); at 1e-8 no run
+    pair does, and fp64 round-off (1e-16 of L / eps ~ 6e-8) stays far below the bar."""
+    from paper_1907_04034_gb300 import gradient
+
+    c = cases.cylinder(dx=1.0 / 25.0)
+    assert c.params.use_pavg == 1
+    a = np.random.default_rng(0).normal(0.0, 0.02, 8)
+    L, g, _ = gradient.drag_gradient(c, a, 400)
+    gf, same = gradient.central_differences(c, a, 400, eps=1e-8)
+    assert all(same.values()), same
+    np.testing.assert_allclose(g, gf, rtol=0, atol=1e-5 * np.abs(gf).max())
+
+
+@pytest.mark.gpu
+def test_tangent_gradient_on_the_d25_cylinder_without_pavg():
+    """The same workload with p_avg off (a map without the count jump): central differences
+    at eps = 1e-6 of the first and last modes agree with the tangent model to 1e-5
+    relative, each."""
     from paper_1907_04034_gb300 import gradient
 
     c = cases.cylinder(dx=1.0 / 25.0)
@@ -746,3 +773,27 @@ def test_tangent_gradient_on_the_d25_cylinder_over_400_steps():
     assert all(same.values()), same
     for k in (0, 7):
         assert abs(g[k] - gf[k]) <= 1e-5 * abs(gf[k]), (k, g[k], gf[k])
+
+
+# ------------------------------------------------- mixed path against fp64 (forces over time)
+@pytest.mark.gpu
+def test_mixed_forces_match_fp64_on_the_d100_cylinder():
+    """The mixed-precision workload (1.5M-particle cylinder, dx = D/100): over 400 steps from
+    the impulsive start the drag and lift of the mixed path agree with the fp64 path's to 1e-4
+    of the drag (the lift is at round-off level this early, so the drag is its scale), and the
+    mean drag to 1e-4 relative."""
+    c = cases.cylinder(dx=1.0 / 100.0)
+    n = 400
+    out = {}
+    for prec in PRECS:
+        s = binding.Solver(c, precision=prec, use_graphs=True, max_history=n + 16)
+        s.step(n)
+        out[prec] = s.history(n)
+        s.close()
+    fx6, fy6 = out["fp64"]["fx"], out["fp64"]["fy"]
+    fxm, fym = out["mixed"]["fx"], out["mixed"]["fy"]
+    scale = np.abs(fx6).max()
+    assert scale > 0.1
+    assert np.abs(fxm - fx6).max() / scale < 1e-4
+    assert np.abs(fym - fy6).max() / scale < 1e-4
+    assert abs(fxm.mean() - fx6.mean()) / abs(fx6.mean()) < 1e-4
