@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--batch-channels", type=int, default=64,
                     help="uneven channels of the batched measurement (0: skip it)")
-    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--tangent-steps", type=int, default=400,
                     help="steps of the gradient workload (0: skip it)")
     ap.add_argument("--force-steps", type=int, default=2000,
@@ -178,56 +178,98 @@ def fp32_peak_tflops(sm_count, max_mhz):
 # ------------------------------------------------------------------------------ batched
 def run_batched(n_chan, steps, dev):
     """The batched workload: uneven pulse channels (seeded sizes, spacings, Re and pulse
-    centres), mixed path, every member's tiling picked by the autotuner, all advanced by one
-    graph launch per step.  Also timed: the same members stepped one after the other."""
+    centres), mixed path, all advanced by one graph launch per step, in the two forms of the
+    library: graph branches (each member's own kernels, tiling picked per member by the
+    autotuner) and fused (each kernel launched once over all members; the members' common
+    tiling picked by timing a few).  Also timed: the members stepped one after the other."""
     import torch
     from paper_1907_04034_gb300 import binding, cases
 
     chans = cases.batch_channels(n=n_chan, seed=0)
+    hist = 3 * steps + 400
     sol = [binding.Solver(c, precision="mixed", use_graphs=True, device=str(dev),
-                          max_history=2 * steps + 64) for c in chans]
+                          max_history=hist) for c in chans]
+    done = 0
+
+    def timed(b, k):
+        nonlocal done
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        b.step(k)
+        e1.record(b.stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        ps = sum(float(np.sum(s.history(done + k)["n_active"][done:done + k])) for s in sol)
+        done += k
+        return ms, ps
+
+    def warm(b, k):
+        nonlocal done
+        b.step(k)
+        torch.cuda.synchronize(dev)
+        done += k
+
+    out = {}
+    # graph branches, per-member autotuned tilings
     tilings = [s.autotune(trials=2)[:2] for s in sol]
     b = binding.Batch(sol)
-    warm = 5
-    b.step(warm)
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(b.stream)
-    b.step(steps)
-    e1.record(b.stream)
-    torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1)
-    ps = 0.0
-    for s in sol:
-        h = s.history(warm + steps)
-        ps += float(np.sum(h["n_active"][warm:warm + steps]))
+    warm(b, 5)
+    ms, ps = timed(b, steps)
     kps = b.kernels_per_step()
     b.close()
+    from collections import Counter
+    out["branches"] = {"value": ps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                       "steps": steps, "kernels_per_graph_launch": kps,
+                       "tilings": {f"{tx}x{tpb}": k for (tx, tpb), k in Counter(tilings).items()}}
+    # fused: one common tiling, the fastest of a few over 20 steps each
+    best = None
+    trial = {}
+    for tx, tpb in ((8, 128), (11, 160), (6, 128), (16, 256)):
+        for s in sol:
+            s.set_tiling(tx, tpb)
+        b = binding.Batch(sol, fused=True)
+        warm(b, 2)
+        tms, _ = timed(b, 20)
+        b.close()
+        trial[f"{tx}x{tpb}"] = tms / 20
+        if best is None or tms < best[0]:
+            best = (tms, tx, tpb)
+    for s in sol:
+        s.set_tiling(best[1], best[2])
+    b = binding.Batch(sol, fused=True)
+    warm(b, 5)
+    ms, ps = timed(b, steps)
+    kps = b.kernels_per_step()
+    b.close()
+    out["fused"] = {"value": ps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                    "steps": steps, "kernels_per_graph_launch": kps,
+                    "tiling": f"{best[1]}x{best[2]}", "tiling_trials_ms_per_step": trial}
     # the same members one after the other (each its own graph, one host thread)
-    seq_steps = max(1, steps // 4)
+    seq_steps = max(1, steps // 10)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for s in sol:
         s.step(seq_steps)
     torch.cuda.synchronize(dev)
     seq = time.perf_counter() - t0
-    seq_ps = sum(float(np.sum(s.history(warm + steps + seq_steps)["n_active"][warm + steps:]))
+    seq_ps = sum(float(np.sum(s.history(done + seq_steps)["n_active"][done:done + seq_steps]))
                  for s in sol)
     for s in sol:
         s.close()
     sizes = [c.n for c in chans]
-    from collections import Counter
-    return {"value": ps / (ms * 1e-3), "unit": UNIT, "channels": n_chan, "steps": steps,
-            "ms_per_step": ms / steps, "particles": int(sum(sizes)),
-            "particles_min_max": [int(min(sizes)), int(max(sizes))],
-            "kernels_per_graph_launch": kps,
-            "tilings": {f"{tx}x{tpb}": k for (tx, tpb), k in Counter(tilings).items()},
-            "members_one_after_another": {"value": seq_ps / seq, "unit": UNIT,
-                                          "steps": seq_steps,
-                                          "note": "host wall clock, each member its own graph"},
-            "workload": "uneven pulse channels: N ~ U[2k, 60k], dx ~ U[0.005, 0.03], "
-                        "Re ~ U[50, 500], pulse centre uniform (seed 0); mixed path"}
+    form = max(("branches", "fused"), key=lambda k: out[k]["value"])
+    res = dict(out[form])
+    res.update({"form": form, "channels": n_chan, "particles": int(sum(sizes)),
+                "particles_min_max": [int(min(sizes)), int(max(sizes))],
+                "branches": out["branches"], "fused": out["fused"],
+                "members_one_after_another": {"value": seq_ps / seq, "unit": UNIT,
+                                              "steps": seq_steps,
+                                              "note": "host wall clock, each member its own graph"},
+                "workload": "uneven pulse channels: N ~ U[2k, 60k], dx ~ U[0.005, 0.03], "
+                            "Re ~ U[50, 500], pulse centre uniform (seed 0); mixed path"})
+    return res
 
 
 # ------------------------------------------------------------------------------ gradient

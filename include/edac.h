@@ -336,6 +336,28 @@ edac_status edac_autotune(edac_ctx *ctx, int trials, int *tile_cells, int *threa
 typedef struct edac_batch edac_batch;
 edac_status edac_batch_create(edac_ctx *const *ctxs, int n, void *cuda_stream, edac_batch **out);
 
+/* Fused batch: the step of every member, as with edac_batch_create, but each kernel of
+ * the step is launched once over the blocks of all members, so that one step of the whole
+ * batch is one graph of about 21 kernel nodes instead of about 20 per member.  The paper
+ * has no counterpart (as for edac_batch_create).  Each block of such a launch looks up its
+ * member in a block-offset table and runs the single-system kernel body on that member's
+ * data, so every member keeps its own cell grid, parameters, time step, tiling and outlet.
+ * Its results are bitwise those of stepping it alone on the fp64 path; on the mixed path
+ * they agree to fp32 rounding (the batched kernels are separate compilations of the same
+ * bodies, in which the compiler may fuse a multiply and an add differently), and runs
+ * stay bitwise reproducible.  The tables (the members' device
+ * parameters and one offset table per kernel shape) live in caller-owned device memory of
+ * edac_batch_workspace_bytes(n) bytes, 256-byte aligned, kept alive while the batch exists;
+ * the library allocates nothing.  The members must share the precision; the mixed pair
+ * passes run with the largest thread count of the members' tilings.  Stepped, counted and
+ * released with edac_batch_step, edac_batch_launch_count and edac_batch_destroy; as for
+ * edac_batch_create, configure the members first and keep them alive.  Errors: those of
+ * edac_batch_create, and EDAC_E_INVALID for a missing, small or misaligned workspace or
+ * members of different precision.  Synchronises cuda_stream once (the table upload). */
+edac_status edac_batch_workspace_bytes(int n, size_t *bytes);
+edac_status edac_batch_create_fused(edac_ctx *const *ctxs, int n, void *cuda_stream,
+                                    void *d_workspace, size_t bytes, edac_batch **out);
+
 /* nsteps steps of every member: nsteps graph launches on the batch stream, which
  * first waits for the work queued on the members' streams; the members' streams
  * then wait for the batch.  Asynchronous. */

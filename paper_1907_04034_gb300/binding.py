@@ -44,6 +44,7 @@ EXPORTS = ("edac_workspace_bytes", "edac_create", "edac_set_inlet", "edac_set_ou
            "edac_density_static", "edac_fma_peak", "edac_conversion_check", "edac_set_tiling",
            "edac_autotune",
            "edac_batch_create", "edac_batch_step", "edac_batch_launch_count", "edac_batch_destroy",
+           "edac_batch_workspace_bytes", "edac_batch_create_fused",
            "edac_set_inlet_transient", "edac_set_outlet_reference", "edac_probe",
            "edac_tangent_workspace_bytes", "edac_tangent_enable", "edac_step_tangent",
            "edac_read_tangent_history", "edac_last_error", "edac_destroy")
@@ -153,6 +154,8 @@ def load(path: Optional[str] = None):
         L.edac_set_tiling.argtypes = [_P, i32, i32]
         L.edac_autotune.argtypes = [_P, i32, C.POINTER(i32), C.POINTER(i32), _DP]
         L.edac_batch_create.argtypes = [C.POINTER(_P), i32, _P, C.POINTER(_P)]
+        L.edac_batch_workspace_bytes.argtypes = [i32, C.POINTER(sz)]
+        L.edac_batch_create_fused.argtypes = [C.POINTER(_P), i32, _P, _P, sz, C.POINTER(_P)]
         L.edac_batch_step.argtypes = [_P, i32]
         L.edac_batch_launch_count.argtypes = [_P, C.POINTER(i64)]
         L.edac_batch_destroy.argtypes = [_P]
@@ -459,11 +462,13 @@ class Solver:
 
 
 class Batch:
-    """Independent systems advanced together: one graph launch per step whose branches are
-    the members' steps (edac_batch_create / edac_batch_step).  The members are ``Solver``
+    """Independent systems advanced together, one graph launch per step (edac_batch_step).
+    fused=False: the graph's branches are the members' steps (edac_batch_create); fused=True:
+    each kernel of the step is launched once over all members (edac_batch_create_fused, whose
+    member tables live in a torch-allocated device workspace).  The members are ``Solver``
     objects on one device, each with its own stream; configure them first."""
 
-    def __init__(self, solvers, stream=None):
+    def __init__(self, solvers, stream=None, fused: bool = False):
         import torch
 
         self.lib = load()
@@ -476,9 +481,21 @@ class Batch:
         self.stream = stream if stream is not None else torch.cuda.Stream(dev, priority=-1)
         arr = (C.c_void_p * len(self.solvers))(*[s.ctx.value for s in self.solvers])
         self.b = C.c_void_p()
+        self.fused = bool(fused)
+        self.workspace = None
         with torch.cuda.device(dev):
-            rc = self.lib.edac_batch_create(arr, len(self.solvers), C.c_void_p(self.stream.cuda_stream),
-                                            C.byref(self.b))
+            if self.fused:
+                nb = C.c_size_t(0)
+                rc = self.lib.edac_batch_workspace_bytes(len(self.solvers), C.byref(nb))
+                if rc != 0:
+                    raise EdacError(rc, self.lib.edac_last_error(None).decode())
+                self.workspace = torch.empty(int(nb.value), dtype=torch.uint8, device=dev)
+                rc = self.lib.edac_batch_create_fused(
+                    arr, len(self.solvers), C.c_void_p(self.stream.cuda_stream),
+                    C.c_void_p(self.workspace.data_ptr()), nb.value, C.byref(self.b))
+            else:
+                rc = self.lib.edac_batch_create(arr, len(self.solvers),
+                                                C.c_void_p(self.stream.cuda_stream), C.byref(self.b))
         if rc != 0:
             raise EdacError(rc, self.lib.edac_last_error(None).decode())
 

@@ -1110,9 +1110,43 @@ struct edac_batch {
     std::vector<cudaEvent_t> ev;  // [0] fork, [1..n] joins, [n+1] done
     std::vector<int> kper;        // kernels per step of each member
     int kernels = 0;
+    bool fused = false;           // one launch per kernel over all members (edac_batch_create_fused)
+    BatchPlan plan{};
 };
 
 namespace {
+
+// One step of every member of a fused batch: the single-system launch sequence (stages with
+// the cell count fused in, cell builds, pass A, boundary, pass B, recycling), each kernel
+// launched once over the blocks of all members.
+int issue_step_batch(const BatchPlan &p, cudaStream_t s)
+{
+    int n = 0;
+    n += launch_stage_batch(p, s, 0);
+    n += launch_rebuild_batch(p, s);
+    n += launch_pass_a_batch(p, s);
+    n += launch_boundary_batch(p, s, 0);
+    n += launch_pass_b_batch(p, s);
+    n += launch_stage_batch(p, s, 1);
+    n += launch_rebuild_batch(p, s);
+    n += launch_pass_a_batch(p, s);
+    n += launch_boundary_batch(p, s, 1);
+    n += launch_pass_b_batch(p, s);
+    n += launch_recycle_batch(p, s);
+    return n;
+}
+
+// Layout of a fused batch's device workspace: the members' Dev, then one block-offset table
+// ([n + 1] ints) per kernel shape.
+size_t batch_layout(int n, size_t *off_tables)
+{
+    size_t off = ((size_t)n * sizeof(Dev) + 255) & ~(size_t)255;
+    for (int k = 0; k < BK_NUM; ++k) {
+        if (off_tables) off_tables[k] = off;
+        off += (((size_t)n + 1) * sizeof(int) + 255) & ~(size_t)255;
+    }
+    return off;
+}
 
 void batch_free(edac_batch *b)
 {
@@ -1177,6 +1211,99 @@ edac_status edac_batch_create(edac_ctx *const *ctxs, int n, void *cuda_stream, e
         return fail(nullptr, EDAC_E_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
     }
     b->kernels = k;
+    *out = b;
+    return EDAC_OK;
+}
+
+edac_status edac_batch_workspace_bytes(int n, size_t *bytes)
+{
+    if (!bytes || n < 1) return fail(nullptr, EDAC_E_INVALID, "bad batch workspace arguments");
+    *bytes = batch_layout(n, nullptr);
+    return EDAC_OK;
+}
+
+edac_status edac_batch_create_fused(edac_ctx *const *ctxs, int n, void *cuda_stream,
+                                    void *d_workspace, size_t bytes, edac_batch **out)
+{
+    if (!out) return fail(nullptr, EDAC_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || n < 1) return fail(nullptr, EDAC_E_INVALID, "no contexts");
+    cudaStream_t ms = (cudaStream_t)cuda_stream;
+    if (!ms) return fail(nullptr, EDAC_E_INVALID, "a batch needs a non-default stream");
+    size_t tab[BK_NUM];
+    const size_t need = batch_layout(n, tab);
+    if (!d_workspace || bytes < need || ((uintptr_t)d_workspace & 255u))
+        return fail(nullptr, EDAC_E_INVALID, "batch workspace missing, too small or not 256-byte aligned");
+    for (int i = 0; i < n; ++i) {
+        edac_ctx *c = ctxs[i];
+        if (!c) return fail(nullptr, EDAC_E_INVALID, "NULL context in the batch");
+        if (!c->loaded || c->failed) return fail(nullptr, EDAC_E_STATE, "batch member without particles or in error");
+        if (!c->stream || c->stream == ms) return fail(nullptr, EDAC_E_INVALID, "each member needs a non-default stream other than the batch's");
+        if (any_profiling(c)) return fail(nullptr, EDAC_E_STATE, "batch member with kernel profiling on");
+        if (c->mixed != ctxs[0]->mixed) return fail(nullptr, EDAC_E_INVALID, "fused batch members must share the precision");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) return fail(nullptr, EDAC_E_INVALID, "batch members must be distinct");
+    }
+    edac_batch *b = new edac_batch();
+    b->ctx.assign(ctxs, ctxs + n);
+    b->stream = ms;
+    b->fused = true;
+    b->ev.assign((size_t)n + 2, nullptr);
+    for (auto &e : b->ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            batch_free(b);
+            return fail(nullptr, EDAC_E_CUDA, "event create");
+        }
+    // member table and block offsets, copied into the caller's workspace
+    char *ws = static_cast<char *>(d_workspace);
+    std::vector<Dev> devs((size_t)n);
+    std::vector<int> offs((size_t)BK_NUM * (n + 1), 0);
+    BatchPlan &p = b->plan;
+    p.n = n;
+    p.mixed = ctxs[0]->mixed;
+    p.pair_tpb = 64;
+    p.any_mirror = false;
+    for (int i = 0; i < n; ++i) {
+        const edac_ctx *c = ctxs[i];
+        devs[i] = c->d;
+        p.pair_tpb = std::max(p.pair_tpb, c->d.tile_tpb);
+        p.any_mirror = p.any_mirror || (c->d.ph.has_outlet && c->d.ph.outlet_kind == OUT_MIRROR);
+        for (int k = 0; k < BK_NUM; ++k) {
+            long long nb = batch_blocks(c->d, k);
+            long long tot = (long long)offs[(size_t)k * (n + 1) + i] + nb;
+            if (nb < 0 || tot > (1LL << 30)) {
+                batch_free(b);
+                return fail(nullptr, EDAC_E_INVALID, "fused batch grid too large");
+            }
+            offs[(size_t)k * (n + 1) + i + 1] = (int)tot;
+        }
+    }
+    p.devs = reinterpret_cast<const Dev *>(ws);
+    for (int k = 0; k < BK_NUM; ++k) {
+        p.off[k] = reinterpret_cast<const int *>(ws + tab[k]);
+        p.total[k] = offs[(size_t)k * (n + 1) + n];
+    }
+    cudaError_t e = cudaMemcpyAsync(ws, devs.data(), sizeof(Dev) * (size_t)n, cudaMemcpyHostToDevice, ms);
+    for (int k = 0; k < BK_NUM && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(ws + tab[k], offs.data() + (size_t)k * (n + 1), sizeof(int) * (size_t)(n + 1),
+                            cudaMemcpyHostToDevice, ms);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ms);
+    // one step of all members: one launch per kernel, captured once
+    int k = 0;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(ms, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        k = issue_step_batch(p, ms);
+        cudaGraph_t gr = nullptr;
+        e = cudaStreamEndCapture(ms, &gr);
+        b->graph = gr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, gr, 0);
+    }
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return fail(nullptr, EDAC_E_CUDA, std::string("fused batch: ") + cudaGetErrorString(e));
+    }
+    b->kernels = k;
+    b->kper.assign((size_t)n, k);
     *out = b;
     return EDAC_OK;
 }

@@ -102,20 +102,26 @@ __device__ __forceinline__ int block_exclusive_scan_1024(int v, int *sh_warp, in
     return r;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_reduce(Dev d)
+__device__ __forceinline__ void scan_reduce(const Dev &d, int bid)
 {
     __shared__ int sh[32];
     const int n = d.g.ncells;
-    const int c0 = blockIdx.x * SCAN_TILE + threadIdx.x * 4;
+    const int c0 = bid * SCAN_TILE + threadIdx.x * 4;
     int v = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) v += (c0 + q < n) ? d.cell_count[c0 + q] : 0;
     int total;
     block_exclusive_scan_1024(v, sh, total);
-    if (threadIdx.x == 0) d.scan_part[blockIdx.x] = total;
+    if (threadIdx.x == 0) d.scan_part[bid] = total;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_top(Dev d, int nblk)
+__global__ void __launch_bounds__(1024) k_scan_reduce(Dev d) { scan_reduce(d, blockIdx.x); }
+__global__ void __launch_bounds__(1024) k_scan_reduce_b(BatchGrid bg)
+{
+    run_member(bg, [](const Dev &d, int b, int) { scan_reduce(d, b); });
+}
+
+__device__ __forceinline__ void scan_top(const Dev &d, int nblk)
 {
     __shared__ int sh[32];
     int run = 0;
@@ -134,16 +140,24 @@ __global__ void __launch_bounds__(1024) k_scan_top(Dev d, int nblk)
     }
 }
 
-__global__ void __launch_bounds__(1024) k_scan_down(Dev d)
+__global__ void __launch_bounds__(1024) k_scan_top(Dev d, int nblk) { scan_top(d, nblk); }
+__global__ void __launch_bounds__(1024) k_scan_top_b(BatchGrid bg)
+{
+    run_member(bg, [](const Dev &d, int, int) {
+        scan_top(d, (d.g.ncells + SCAN_TILE - 1) / SCAN_TILE);
+    });
+}
+
+__device__ __forceinline__ void scan_down(const Dev &d, int bid)
 {
     __shared__ int sh[32];
     const int n = d.g.ncells;
-    const int c0 = blockIdx.x * SCAN_TILE + threadIdx.x * 4;
+    const int c0 = bid * SCAN_TILE + threadIdx.x * 4;
     int v[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) v[q] = (c0 + q < n) ? d.cell_count[c0 + q] : 0;
     int total;
-    int run = block_exclusive_scan_1024(v[0] + v[1] + v[2] + v[3], sh, total) + d.scan_part[blockIdx.x];
+    int run = block_exclusive_scan_1024(v[0] + v[1] + v[2] + v[3], sh, total) + d.scan_part[bid];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         if (c0 + q < n) d.cell_start[c0 + q] = run;
@@ -151,14 +165,23 @@ __global__ void __launch_bounds__(1024) k_scan_down(Dev d)
     }
 }
 
-__global__ void k_cell_scatter(Dev d)
+__global__ void __launch_bounds__(1024) k_scan_down(Dev d) { scan_down(d, blockIdx.x); }
+__global__ void __launch_bounds__(1024) k_scan_down_b(BatchGrid bg)
 {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.cap; s += gridDim.x * blockDim.x) {
+    run_member(bg, [](const Dev &d, int b, int) { scan_down(d, b); });
+}
+
+__device__ __forceinline__ void cell_scatter(const Dev &d, int bid, int nblk)
+{
+    for (int s = bid * blockDim.x + threadIdx.x; s < d.cap; s += nblk * blockDim.x) {
         const int c = d.slot_cell[s];
         if (c < 0) continue;
         d.order_raw[d.cell_start[c] + d.within[s]] = s;
     }
 }
+
+__global__ void k_cell_scatter(Dev d) { cell_scatter(d, blockIdx.x, gridDim.x); }
+__global__ void k_cell_scatter_b(BatchGrid bg) { run_member(bg, [](const Dev &d, int b, int nb) { cell_scatter(d, b, nb); }); }
 
 // One warp per cell: rank the cell's slots (ascending slot, so the cell order does not depend
 // on the order of the counting atomics), write the order, clear the cell's count for the next
@@ -197,12 +220,12 @@ __device__ __forceinline__ void gather_one(const Dev &d, int s, int k, int c)
 // not depend on the order of the counting atomics; the thread then gathers the cell-ordered
 // copies the pair kernels read.  Cells hold ~13 particles, so the rank costs ~13 cached loads.
 template <int MIXED>
-__global__ void k_cell_gather(Dev d)
+__device__ __forceinline__ void cell_gather(const Dev &d, int bid, int nblk)
 {
     const int n = d.cnt->n_alive;
-    const int stride = gridDim.x * blockDim.x;
+    const int stride = nblk * blockDim.x;
     // uniform trip count per warp so that warp_append sees all 32 lanes
-    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+    for (int base = bid * blockDim.x; base < n; base += stride) {
         const int e = base + threadIdx.x;
         bool is_bnd = false;
         int k = 0;
@@ -220,6 +243,14 @@ __global__ void k_cell_gather(Dev d)
         const int slot = warp_append(&d.cnt->n_bnd, is_bnd);
         if (is_bnd) d.bnd[slot] = k;
     }
+}
+
+template <int MIXED>
+__global__ void k_cell_gather(Dev d) { cell_gather<MIXED>(d, blockIdx.x, gridDim.x); }
+template <int MIXED>
+__global__ void k_cell_gather_b(BatchGrid bg)
+{
+    run_member(bg, [](const Dev &d, int b, int nb) { cell_gather<MIXED>(d, b, nb); });
 }
 
 // ---------------------------------------------------------------------------- stages
@@ -259,11 +290,11 @@ __device__ __forceinline__ void ring_sample(const Dev &d, int s, double un, doub
 // COUNT: also the first step of the next cell build (count_slot) at each slot's new position,
 // which saves k_cell_count its pass over the positions.
 template <bool CORR, int MIXED, bool COUNT>
-__global__ void k_stage(Dev d, double tau)
+__device__ __forceinline__ void stage(const Dev &d, double tau, int bid, int nblk)
 {
     const Geo &g = d.g;
     const Phys &ph = d.ph;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < d.cap; s += gridDim.x * blockDim.x) {
+    for (int s = bid * blockDim.x + threadIdx.x; s < d.cap; s += nblk * blockDim.x) {
         const uint8_t t = d.tag[s];
         if (t == FLUID) {
             double x0, y0, u0, v0, p0;
@@ -320,6 +351,17 @@ __global__ void k_stage(Dev d, double tau)
     }
 }
 
+template <bool CORR, int MIXED, bool COUNT>
+__global__ void k_stage(Dev d, double tau) { stage<CORR, MIXED, COUNT>(d, tau, blockIdx.x, gridDim.x); }
+// batched: each member's own time step (predictor dt/2, corrector dt)
+template <bool CORR, int MIXED, bool COUNT>
+__global__ void k_stage_b(BatchGrid bg)
+{
+    run_member(bg, [](const Dev &d, int b, int nb) {
+        stage<CORR, MIXED, COUNT>(d, CORR ? d.ph.dt : 0.5 * d.ph.dt, b, nb);
+    });
+}
+
 // ------------------------------------------------------------------------- recycling
 // Ring buffer of a particle that becomes fluid: all samples = current (u, v, p).
 __device__ __forceinline__ void ring_fill(const Dev &d, int s)
@@ -342,11 +384,11 @@ __device__ __forceinline__ void ring_fill(const Dev &d, int s)
 // inlet particle is spawned by k_end_step).
 // Events go to per-kind lists by warp-aggregated appends; k_end_step puts them in
 // ascending id order before ids and slots are handed out.
-__global__ void k_recycle_mark(Dev d)
+__device__ __forceinline__ void recycle_mark(const Dev &d, int bid, int nblk)
 {
     const Phys &ph = d.ph;
-    const int stride = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x; base < d.cap; base += stride) {
+    const int stride = nblk * blockDim.x;
+    for (int base = bid * blockDim.x; base < d.cap; base += stride) {
         const int s = base + threadIdx.x;
         bool del = false, out = false, spawn = false;
         if (s < d.cap) {
@@ -389,6 +431,12 @@ __global__ void k_recycle_mark(Dev d)
     }
 }
 
+__global__ void k_recycle_mark(Dev d) { recycle_mark(d, blockIdx.x, gridDim.x); }
+__global__ void k_recycle_mark_b(BatchGrid bg)
+{
+    run_member(bg, [](const Dev &d, int b, int nb) { recycle_mark(d, b, nb); });
+}
+
 // rank of key[i] among key[0..n) (keys are unique particle ids)
 __device__ __forceinline__ int rank_of(const unsigned long long *key, int n, int i)
 {
@@ -416,7 +464,7 @@ __device__ double block_sum_1024(double v, double *sh)
 // (Eq. tvf-momentum_solid summed over the body; fixed-shape tree), the canonical
 // ordering of the recycling events, slot and id hand-out for spawned inlet particles
 // (ascending parent id), the mass flux, and one history record.
-__global__ void __launch_bounds__(1024) k_end_step(Dev d, double *scratch_m)
+__device__ __forceinline__ void end_step(const Dev &d, double *scratch_m)
 {
     __shared__ double sh[1024];
     Counters *C = d.cnt;
@@ -494,6 +542,12 @@ __global__ void __launch_bounds__(1024) k_end_step(Dev d, double *scratch_m)
     }
 }
 
+__global__ void __launch_bounds__(1024) k_end_step(Dev d, double *scratch_m) { end_step(d, scratch_m); }
+__global__ void __launch_bounds__(1024) k_end_step_b(BatchGrid bg)
+{
+    run_member(bg, [](const Dev &d, int, int) { end_step(d, d.scratch_m); });
+}
+
 // Set-up after an upload: u~ = u, ring buffers and outlet memory from the initial fields.
 __global__ void k_init(Dev d)
 {
@@ -565,6 +619,48 @@ int launch_init(const Dev &d, cudaStream_t s)
 {
     k_init<<<grid_for(d.cap), TPB, 0, s>>>(d);
     return 1;
+}
+
+// ---------------------------------------------------------------- batched launches
+int launch_stage_batch(const BatchPlan &p, cudaStream_t s, int corrector)
+{
+    const int gb = p.total[BK_CAP];
+    const BatchGrid bg = p.grid(BK_CAP);
+    if (corrector) {
+        if (p.mixed) k_stage_b<true, 1, true><<<gb, TPB, 0, s>>>(bg);
+        else k_stage_b<true, 0, true><<<gb, TPB, 0, s>>>(bg);
+    } else {
+        if (p.mixed) k_stage_b<false, 1, true><<<gb, TPB, 0, s>>>(bg);
+        else k_stage_b<false, 0, true><<<gb, TPB, 0, s>>>(bg);
+    }
+    return 1;
+}
+
+// the cell count was fused into the stages (counted)
+int launch_rebuild_batch(const BatchPlan &p, cudaStream_t s)
+{
+    k_scan_reduce_b<<<p.total[BK_SCAN], 1024, 0, s>>>(p.grid(BK_SCAN));
+    k_scan_top_b<<<p.total[BK_ONE], 1024, 0, s>>>(p.grid(BK_ONE));
+    k_scan_down_b<<<p.total[BK_SCAN], 1024, 0, s>>>(p.grid(BK_SCAN));
+    k_cell_scatter_b<<<p.total[BK_CAP], TPB, 0, s>>>(p.grid(BK_CAP));
+    if (p.mixed) k_cell_gather_b<1><<<p.total[BK_CAP], TPB, 0, s>>>(p.grid(BK_CAP));
+    else k_cell_gather_b<0><<<p.total[BK_CAP], TPB, 0, s>>>(p.grid(BK_CAP));
+    return 5;
+}
+
+int launch_recycle_batch(const BatchPlan &p, cudaStream_t s)
+{
+    k_recycle_mark_b<<<p.total[BK_CAP], TPB, 0, s>>>(p.grid(BK_CAP));
+    k_end_step_b<<<p.total[BK_ONE], 1024, 0, s>>>(p.grid(BK_ONE));
+    return 2;
+}
+
+int cells_batch_blocks(const Dev &d, int kind)
+{
+    if (kind == BK_CAP) return grid_for(d.cap);
+    if (kind == BK_SCAN) return (d.g.ncells + SCAN_TILE - 1) / SCAN_TILE;
+    if (kind == BK_ONE) return 1;
+    return -1;
 }
 
 }  // namespace edac

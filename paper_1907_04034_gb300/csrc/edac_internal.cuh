@@ -344,6 +344,80 @@ __device__ __forceinline__ void inlet_uv(const Phys &ph, double y, double t, dou
     }
 }
 
+// ------------------------------------------------------------- batches in one launch
+// A batched launch runs one kernel over the blocks of every member of a batch of systems:
+// member m owns blocks [off[m], off[m + 1]) of the grid (members with no blocks are skipped).
+// Each block finds its member, copies the member's Dev into shared memory and runs the
+// single-system body with its block index and block count within the member's range, so
+// that a member's results do not depend on the batch it runs in.
+struct BatchGrid {
+    const Dev *devs;  // [n] device copies of the members' Dev
+    const int *off;   // [n + 1] block offsets of this kernel
+    int n;
+};
+
+// the member that owns grid block b: the largest m with off[m] <= b
+__device__ __forceinline__ int batch_member(const int *off, int n, int b)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class Body>
+__device__ __forceinline__ void run_member(const BatchGrid &bg, Body &&body)
+{
+    constexpr int W = (int)(sizeof(Dev) / sizeof(int2));
+    static_assert(sizeof(Dev) % sizeof(int2) == 0, "Dev copied in 8-byte words");
+    __shared__ int2 sdev[W];
+    __shared__ int sinfo[3];
+    if (threadIdx.x == 0) {
+        const int m = batch_member(bg.off, bg.n, (int)blockIdx.x);
+        sinfo[0] = m;
+        sinfo[1] = __ldg(bg.off + m);
+        sinfo[2] = __ldg(bg.off + m + 1);
+    }
+    __syncthreads();
+    const int2 *src = reinterpret_cast<const int2 *>(bg.devs + sinfo[0]);
+    for (int i = threadIdx.x; i < W; i += blockDim.x) sdev[i] = __ldg(src + i);
+    __syncthreads();
+    body(*reinterpret_cast<const Dev *>(sdev), (int)blockIdx.x - sinfo[1], sinfo[2] - sinfo[1]);
+}
+
+// Grids of a batched step, one block-offset table per kernel shape.
+enum : int {
+    BK_CAP,      // grid-stride over the slots, 256 threads (stage, scatter, gather, recycling)
+    BK_SCAN,     // one 1024-thread block per 4096 cells (scan partials)
+    BK_ONE,      // one 1024-thread block (scan top, end of step)
+    BK_TILES,    // one block per cell tile (mixed pair passes)
+    BK_CAP128,   // grid-stride over the particles, 128 threads (fp64 pair passes)
+    BK_BND,      // boundary kernel, 256 threads
+    BK_MIRROR,   // mirrored outlet, 256 threads (members with that outlet only)
+    BK_NUM
+};
+struct BatchPlan {
+    int n, mixed;
+    int pair_tpb;               // threads of the mixed pair passes' blocks
+    const Dev *devs;            // device
+    const int *off[BK_NUM];     // device, [n + 1] each
+    int total[BK_NUM];          // blocks of each kernel shape over all members
+    bool any_mirror;
+    BatchGrid grid(int k) const { return BatchGrid{devs, off[k], n}; }
+};
+// blocks of one member for a kernel shape
+int batch_blocks(const Dev &d, int kind);
+// one step of every member of the batch (the launch sequence of a single step), on s
+int launch_stage_batch(const BatchPlan &p, cudaStream_t s, int corrector);
+int launch_rebuild_batch(const BatchPlan &p, cudaStream_t s);
+int launch_pass_a_batch(const BatchPlan &p, cudaStream_t s);
+int launch_boundary_batch(const BatchPlan &p, cudaStream_t s, int end_of_step);
+int launch_pass_b_batch(const BatchPlan &p, cudaStream_t s);
+int launch_recycle_batch(const BatchPlan &p, cudaStream_t s);
+
 // ------------------------------------------------------------------- host-side launchers
 // Every launcher issues its kernels on `s` and returns the number of launches issued.
 // counted: the cell count was fused into the preceding stage (launch_stage with count)

@@ -82,12 +82,12 @@ struct BodyA64 {
     }
 };
 
-__global__ void __launch_bounds__(TPB) k_pass_a64(Dev d)
+__device__ __forceinline__ void pass_a64(const Dev &d, int bid, int nblk)
 {
     __shared__ unsigned lst_all[LMAX * TPB];
     unsigned *lst = lst_all + threadIdx.x;
     const int n = d.cnt->n_alive;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    for (int k = bid * blockDim.x + threadIdx.x; k < n; k += nblk * blockDim.x) {
         int cx, cy;
         cell_of(d, k, cx, cy);
         const float4 pi = d.P[k];
@@ -106,6 +106,12 @@ __global__ void __launch_bounds__(TPB) k_pass_a64(Dev d)
         d.vol[s] = V;
         d.nnb[s] = f.n + 1;
     }
+}
+
+__global__ void __launch_bounds__(TPB) k_pass_a64(Dev d) { pass_a64(d, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(TPB) k_pass_a64_b(BatchGrid bg)
+{
+    run_member(bg, [](const Dev &d, int b, int nb) { pass_a64(d, b, nb); });
 }
 
 // ------------------------------------------------------------------ fp64 path: pass B
@@ -170,13 +176,13 @@ struct BodyB64 {
     }
 };
 
-__global__ void __launch_bounds__(TPB) k_pass_b64(Dev d)
+__device__ __forceinline__ void pass_b64(const Dev &d, int bid, int nblk)
 {
     __shared__ unsigned lst_all[LMAX * TPB];
     unsigned *lst = lst_all + threadIdx.x;
     const Phys &ph = d.ph;
     const int n = d.cnt->n_alive;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    for (int k = bid * blockDim.x + threadIdx.x; k < n; k += nblk * blockDim.x) {
         const int t = d.stag[k] & 0x7f;
         const bool fl = (t == FLUID || t == INLET);
         const bool solid = (t == WALL && ph.wall_drag[0]) || (t == SLIPWALL && ph.wall_drag[1]);
@@ -209,6 +215,12 @@ __global__ void __launch_bounds__(TPB) k_pass_b64(Dev d)
             d.abv[s] = -ph.pb / mi * f.gys;
         }
     }
+}
+
+__global__ void __launch_bounds__(TPB) k_pass_b64(Dev d) { pass_b64(d, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(TPB) k_pass_b64_b(BatchGrid bg)
+{
+    run_member(bg, [](const Dev &d, int b, int nb) { pass_b64(d, b, nb); });
 }
 
 // ------------------------------------------------------------------ mixed-path pair bodies
@@ -488,11 +500,11 @@ struct CandRows {
     }
 };
 
-__device__ __forceinline__ int tile_of_block(const Dev &d, int &cx0, int &cy)
+__device__ __forceinline__ int tile_of_block(const Dev &d, int bid, int &cx0, int &cy)
 {
     const int tpr = (d.g.nx + d.tile_tx - 1) / d.tile_tx;
-    cy = blockIdx.x / tpr;
-    cx0 = (blockIdx.x - cy * tpr) * d.tile_tx;
+    cy = bid / tpr;
+    cx0 = (bid - cy * tpr) * d.tile_tx;
     return cy < d.g.ny;
 }
 
@@ -610,14 +622,14 @@ __device__ __forceinline__ void for_mask(const CandRows &cr, uint4 m, Body &&bod
     fold();
 }
 
-__global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled(Dev d)
+__device__ __forceinline__ void pass_a_tiled(const Dev &d, int bid)
 {
     __shared__ TileHdr th;
     __shared__ float2 spos[CT_HMAX];
     __shared__ float smass[CT_HMAX];
     __shared__ int sgj[CT_HMAX];
     int cx0, cy;
-    if (!tile_of_block(d, cx0, cy)) return;
+    if (!tile_of_block(d, bid, cx0, cy)) return;
     if (threadIdx.x < 32) tile_setup(d, cx0, cy, th);
     __syncthreads();
     const bool fits = th.H <= CT_HMAX;
@@ -677,6 +689,12 @@ __global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled(Dev d)
         d.vol[s] = f2d(V);
         d.nnb[s] = f.n;
     }
+}
+
+__global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled(Dev d) { pass_a_tiled(d, blockIdx.x); }
+__global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled_b(BatchGrid bg)
+{
+    run_member(bg, [](const Dev &d, int b, int) { pass_a_tiled(d, b); });
 }
 
 template <bool SOLID>
@@ -763,7 +781,7 @@ __device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th,
     }
 }
 
-__global__ void __launch_bounds__(CT_TPB) k_pass_b_tiled(Dev d)
+__device__ __forceinline__ void pass_b_tiled(const Dev &d, int bid)
 {
     __shared__ TileHdr th;
     __shared__ float2 spos[CT_HMAX];
@@ -773,7 +791,7 @@ __global__ void __launch_bounds__(CT_TPB) k_pass_b_tiled(Dev d)
     __shared__ int sgj[CT_HMAX];
     const Phys &ph = d.ph;
     int cx0, cy;
-    if (!tile_of_block(d, cx0, cy)) return;
+    if (!tile_of_block(d, bid, cx0, cy)) return;
     if (threadIdx.x < 32) tile_setup(d, cx0, cy, th);
     __syncthreads();
     const bool fits = th.H <= CT_HMAX;
@@ -791,6 +809,12 @@ __global__ void __launch_bounds__(CT_TPB) k_pass_b_tiled(Dev d)
         else if ((t == WALL && ph.wall_drag[0]) || (t == SLIPWALL && ph.wall_drag[1]))
             pass_b_particle<true>(d, th, fits, cy, cx0, ii, spos, sq, sb, stg, sgj);
     }
+}
+
+__global__ void __launch_bounds__(CT_TPB) k_pass_b_tiled(Dev d) { pass_b_tiled(d, blockIdx.x); }
+__global__ void __launch_bounds__(CT_TPB, 4) k_pass_b_tiled_b(BatchGrid bg)
+{
+    run_member(bg, [](const Dev &d, int b, int) { pass_b_tiled(d, b); });
 }
 
 // --------------------------------------------------------------------- boundary kernel
@@ -1166,7 +1190,7 @@ constexpr int BND_CHUNK = 8;
 constexpr int BND_STASH = 17;  // stash row stride (doubles): odd, against bank conflicts
 
 template <int MIXED>
-__global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
+__device__ __forceinline__ void boundary(const Dev &d, int end_of_step, int bid, int nblk)
 {
     typedef typename std::conditional<MIXED, float, double>::type T;
     constexpr int NAI = mirror_na(1);
@@ -1176,9 +1200,9 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
     const Phys &ph = d.ph;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = d.cnt->n_bnd;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int nwarps = (nblk * blockDim.x) >> 5;
     const T a2 = narrow<T>(ph.a2), a2h = narrow<T>(ph.a2h), inv_h = narrow<T>(ph.inv_h);
-    for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * BND_CHUNK; base < nb;
+    for (int base = ((bid * blockDim.x + threadIdx.x) >> 5) * BND_CHUNK; base < nb;
          base += nwarps * BND_CHUNK) {
     const int nchunk = min(BND_CHUNK, nb - base);
     bool inlet_mine = false;  // lane i: chunk particle i is an inlet particle to solve
@@ -1340,18 +1364,29 @@ __global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
     }
 }
 
+template <int MIXED>
+__global__ void __launch_bounds__(256) k_boundary(Dev d, int end_of_step)
+{
+    boundary<MIXED>(d, end_of_step, blockIdx.x, gridDim.x);
+}
+template <int MIXED>
+__global__ void __launch_bounds__(256) k_boundary_b(BatchGrid bg, int end_of_step)
+{
+    run_member(bg, [&](const Dev &d, int b, int nb) { boundary<MIXED>(d, end_of_step, b, nb); });
+}
+
 // Mirrored outlet (Sec. 3.2 at the outlet), once per step: p, u, v of every outlet particle
 // by the Taylor extrapolation about k = (2 x_out - x_o, y_o); the particle advects with that
 // u.  One warp per boundary particle, outlet particles only.
 template <int MIXED>
-__global__ void __launch_bounds__(256) k_outlet_mirror(Dev d)
+__device__ __forceinline__ void outlet_mirror(const Dev &d, int bid, int nblk)
 {
     __shared__ int wbuf[8][CMP_CAP];
     const Phys &ph = d.ph;
     const int lane = threadIdx.x & 31;
     const int nb = d.cnt->n_bnd;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nwarps) {
+    const int nwarps = (nblk * blockDim.x) >> 5;
+    for (int b = (bid * blockDim.x + threadIdx.x) >> 5; b < nb; b += nwarps) {
         const int k = d.bnd[b];
         if ((d.stag[k] & 0x7f) != OUTLET) continue;
         const int s = d.order[k];
@@ -1370,6 +1405,14 @@ __global__ void __launch_bounds__(256) k_outlet_mirror(Dev d)
             d.redp[s] = 0;
         }
     }
+}
+
+template <int MIXED>
+__global__ void __launch_bounds__(256) k_outlet_mirror(Dev d) { outlet_mirror<MIXED>(d, blockIdx.x, gridDim.x); }
+template <int MIXED>
+__global__ void __launch_bounds__(256) k_outlet_mirror_b(BatchGrid bg)
+{
+    run_member(bg, [](const Dev &d, int b, int nb) { outlet_mirror<MIXED>(d, b, nb); });
 }
 
 // Debug: exact neighbour ids of every particle, with the membership test of the passes.
@@ -1433,6 +1476,49 @@ int launch_pass_b(const Dev &d, cudaStream_t s, int mixed)
     if (mixed) k_pass_b_tiled<<<tiles(d), d.tile_tpb, 0, s>>>(d);
     else k_pass_b64<<<grid_for(d.cap, TPB), TPB, 0, s>>>(d);
     return 1;
+}
+
+// ---------------------------------------------------------------- batched launches
+int launch_pass_a_batch(const BatchPlan &p, cudaStream_t s)
+{
+    if (p.mixed) k_pass_a_tiled_b<<<p.total[BK_TILES], p.pair_tpb, 0, s>>>(p.grid(BK_TILES));
+    else k_pass_a64_b<<<p.total[BK_CAP128], TPB, 0, s>>>(p.grid(BK_CAP128));
+    return 1;
+}
+
+int launch_boundary_batch(const BatchPlan &p, cudaStream_t s, int end_of_step)
+{
+    if (p.mixed) k_boundary_b<1><<<p.total[BK_BND], 256, 0, s>>>(p.grid(BK_BND), end_of_step);
+    else k_boundary_b<0><<<p.total[BK_BND], 256, 0, s>>>(p.grid(BK_BND), end_of_step);
+    if (end_of_step && p.any_mirror) {
+        if (p.mixed) k_outlet_mirror_b<1><<<p.total[BK_MIRROR], 256, 0, s>>>(p.grid(BK_MIRROR));
+        else k_outlet_mirror_b<0><<<p.total[BK_MIRROR], 256, 0, s>>>(p.grid(BK_MIRROR));
+        return 2;
+    }
+    return 1;
+}
+
+int launch_pass_b_batch(const BatchPlan &p, cudaStream_t s)
+{
+    if (p.mixed) k_pass_b_tiled_b<<<p.total[BK_TILES], p.pair_tpb, 0, s>>>(p.grid(BK_TILES));
+    else k_pass_b64_b<<<p.total[BK_CAP128], TPB, 0, s>>>(p.grid(BK_CAP128));
+    return 1;
+}
+
+int cells_batch_blocks(const Dev &d, int kind);
+
+// Blocks of one member for each kernel shape: the grids of the single-system launches.
+int batch_blocks(const Dev &d, int kind)
+{
+    switch (kind) {
+    case BK_TILES: return tiles(d);
+    case BK_CAP128: return grid_for(d.cap, TPB);
+    case BK_BND: return min(grid_for(d.cap, 64 * BND_CHUNK), 152 * 3);
+    case BK_MIRROR:
+        return (d.ph.has_outlet && d.ph.outlet_kind == OUT_MIRROR) ? min(grid_for(d.cap, 64), 152 * 16)
+                                                                  : 0;
+    default: return cells_batch_blocks(d, kind);
+    }
 }
 
 int launch_neighbor_dump(const Dev &d, cudaStream_t s, int mixed, const long long *start,
