@@ -273,11 +273,12 @@ def run_batched(n_chan, steps, dev):
 
 
 # ------------------------------------------------------------------------------ gradient
-def run_tangent(steps, dev):
+def run_tangent(steps, dev, checkpoint_every=50):
     """The gradient workload: cylinder at dx = D/25, inlet modes a_k ~ N(0, 0.02) (seed 0),
-    mean drag over `steps` steps; the gradient with respect to the 8 modes from the
-    tangent-linear model, its time against the fp64 forward run of the same steps, and one
-    central difference (mode 1, eps = 1e-6) as a check."""
+    mean drag over `steps` steps; the gradient with respect to the 8 modes by the reverse-mode
+    adjoint (checkpoints every `checkpoint_every` steps, each segment recomputed once) and by
+    the tangent-linear model, their times against the fp64 forward run of the same steps, and
+    one central difference (mode 1, eps = 1e-8, see the tests) as a check."""
     import torch
     from paper_1907_04034_gb300 import binding, cases, gradient
 
@@ -297,18 +298,24 @@ def run_tangent(steps, dev):
     torch.cuda.synchronize(dev)
     fwd_ms = e0.elapsed_time(e1)
     s.close()
+    La, ga, ta = gradient.drag_gradient_adjoint(c, a, steps, checkpoint_every, device=str(dev))
     L, g, tm = gradient.drag_gradient(c, a, steps, device=str(dev))
-    gf, same = gradient.central_differences(c, a, steps, eps=1e-6, modes=[0], device=str(dev))
+    gf, same = gradient.central_differences(c, a, steps, eps=1e-8, modes=[0], device=str(dev))
+    fwd_s = fwd_ms / 1e3
     return {"workload": f"cylinder Re=200, dx=D/25 ({c.n} particles), 8 inlet modes "
                         f"a_k ~ N(0, 0.02) seed 0, mean c_d over {steps} steps",
-            "method": "tangent-linear model of the fp64 step (forward mode, 8 directions; "
-                      "fp32 pair tangents, fp64 boundary tangents)",
-            "loss": L, "dL_da": [float(v) for v in g],
-            "tangent_s": tm["tangent_s"], "forward_s": fwd_ms / 1e3,
-            "tangent_over_forward": tm["tangent_s"] / (fwd_ms / 1e3),
-            "fd_check_mode1": {"fd": float(gf[0]), "tangent": float(g[0]),
-                               "rel_diff": float(abs(g[0] - gf[0]) / max(abs(gf[0]), 1e-300)),
-                               "same_events": bool(same[0])}}
+            "method": "reverse-mode adjoint of the fp64 step (checkpoints every "
+                      f"{checkpoint_every} steps, segments recomputed once; fp32 pair-pass "
+                      "adjoints, fp64 boundary adjoints), beside the tangent-linear model "
+                      "(forward mode, 8 directions)",
+            "loss": La, "dL_da": [float(v) for v in ga],
+            "adjoint_s": ta["adjoint_s"], "tangent_s": tm["tangent_s"], "forward_s": fwd_s,
+            "adjoint_over_forward": ta["adjoint_s"] / fwd_s,
+            "tangent_over_forward": tm["tangent_s"] / fwd_s,
+            "adjoint_vs_tangent_max_rel": float(np.abs(ga - g).max() / np.abs(g).max()),
+            "fd_check_mode1": {"fd": float(gf[0]), "adjoint": float(ga[0]),
+                               "rel_diff": float(abs(ga[0] - gf[0]) / max(abs(gf[0]), 1e-300)),
+                               "eps": 1e-8, "same_events": bool(same[0])}}
 
 
 # -------------------------------------------------------------------------- reference

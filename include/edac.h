@@ -389,7 +389,7 @@ edac_status edac_probe(edac_ctx *ctx, int n, const double *h_x, const double *h_
  * drag, with respect to the modes.  It is forward-mode (no checkpoints); the
  * pair-pass tangents run in fp32 (relative rounding ~1e-7, against the fp64
  * step's derivatives), the boundary parts in fp64: a tangent step costs a few
- * fp64 steps (3.6x on a 98k-particle cylinder).
+ * fp64 steps (2.8x on a 98k-particle cylinder).
  *   edac_tangent_workspace_bytes: device bytes the tangents need (caller-owned,
  *     256-byte aligned, kept alive while tangents are stepped);
  *   edac_tangent_enable: set the tangents of the current state (zero except the
@@ -405,6 +405,43 @@ edac_status edac_tangent_enable(edac_ctx *ctx, void *d_workspace, size_t bytes);
 edac_status edac_step_tangent(edac_ctx *ctx, int nsteps);
 edac_status edac_read_tangent_history(edac_ctx *ctx, int max_steps, double *h_dfx,
                                       double *h_dfy, int *nsteps);
+
+/* ---------------------------------------------------------------------------
+ * Reverse-mode adjoint (fp64 path, steady inlet modes, hybrid outlet or none):
+ * the gradient with respect to the inlet modes a_1..a_8 (edac_set_inlet) of
+ *   L = sum_n [ w_fx[n] F_x^n + w_fy[n] F_y^n
+ *               + w_pe[n] sum_{fluid i} omega(x_i) p_i^2 at the end of step n ]
+ * over nsteps steps from the current state (F: the force on the drag walls of
+ * each step, as in edac_read_history; the last term is the pressure energy of
+ * the fluid in an x-window, e.g. the layer in front of the outlet where waves
+ * the outlet reflects stay, with the weight omega = sin^2(pi (x - pe_x0) /
+ * (pe_x1 - pe_x0)) on [pe_x0, pe_x1) and 0 outside, which vanishes smoothly at
+ * both edges so that particles crossing them change L continuously).  The paper has no counterpart (it states the
+ * method, not its derivatives).  The adjoint of every operation of a step is
+ * taken in reverse order with the neighbour sets, the acoustic-gate decisions,
+ * the red/blue outlet classes and the recycling events of the forward run held
+ * fixed, as in the tangent model; the forward run keeps a checkpoint of the
+ * context's workspace every checkpoint_every steps and the reverse sweep
+ * recomputes each segment from its checkpoint once (storing its steps), then
+ * each step from its snapshot.  Its cost is that of a few fp64 forward runs
+ * for any number of parameters.  The context must be freshly uploaded (no steps
+ * taken since edac_set_particles) and is left in the state after nsteps steps
+ * (as edac_step would leave it, history included).
+ *   edac_adjoint_workspace_bytes: device bytes edac_adjoint_run needs for these
+ *     nsteps and checkpoint_every (the adjoint fields and (nsteps /
+ *     checkpoint_every + 1 + checkpoint_every) copies of the context's workspace);
+ *   edac_adjoint_run: d_workspace caller-owned, 256-byte aligned, at least that
+ *     many bytes; any weight array may be NULL (zeros), else nsteps values;
+ *     writes L to *h_loss (may be NULL) and dL/da_k, k = 1..8, to h_grad[0..7]
+ *     (zero for modes beyond those edac_set_inlet set).  nsteps <= max_history.
+ *     Synchronises the stream.  EDAC_E_STATE on the mixed path, with other inlet
+ *     or outlet kinds, after steps, or in error; EDAC_E_INVALID for bad sizes. */
+edac_status edac_adjoint_workspace_bytes(edac_ctx *ctx, int nsteps, int checkpoint_every,
+                                         size_t *bytes);
+edac_status edac_adjoint_run(edac_ctx *ctx, void *d_workspace, size_t bytes, int nsteps,
+                             int checkpoint_every, const double *h_w_fx, const double *h_w_fy,
+                             const double *h_w_pe, double pe_x0, double pe_x1, double *h_loss,
+                             double *h_grad);
 
 /* Text of the last error of this context (valid until the next call); with
  * ctx = NULL, the last error of a context-less call (edac_workspace_bytes,

@@ -25,7 +25,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libedac.so")
 SOURCES = ("edac_capi.cu", "edac_cells.cu", "edac_pairs.cu", "edac_static.cu", "edac_peaks.cu",
-           "edac_tangent.cu", "edac_selfcheck.cu")
+           "edac_tangent.cu", "edac_adjoint.cu", "edac_selfcheck.cu")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 EDAC_FP64, EDAC_MIXED = 0, 1
@@ -47,7 +47,8 @@ EXPORTS = ("edac_workspace_bytes", "edac_create", "edac_set_inlet", "edac_set_ou
            "edac_batch_workspace_bytes", "edac_batch_create_fused",
            "edac_set_inlet_transient", "edac_set_outlet_reference", "edac_probe",
            "edac_tangent_workspace_bytes", "edac_tangent_enable", "edac_step_tangent",
-           "edac_read_tangent_history", "edac_last_error", "edac_destroy")
+           "edac_read_tangent_history", "edac_adjoint_workspace_bytes", "edac_adjoint_run",
+           "edac_last_error", "edac_destroy")
 
 
 class EdacError(RuntimeError):
@@ -166,6 +167,9 @@ def load(path: Optional[str] = None):
         L.edac_tangent_enable.argtypes = [_P, _P, sz]
         L.edac_step_tangent.argtypes = [_P, i32]
         L.edac_read_tangent_history.argtypes = [_P, i32, _DP, _DP, C.POINTER(i32)]
+        L.edac_adjoint_workspace_bytes.argtypes = [_P, i32, i32, C.POINTER(sz)]
+        L.edac_adjoint_run.argtypes = [_P, _P, sz, i32, i32, _DP, _DP, _DP, C.c_double, C.c_double,
+                                       _DP, _DP]
         L.edac_last_error.argtypes = [_P]
         L.edac_last_error.restype = C.c_char_p
         L.edac_destroy.argtypes = [_P]
@@ -431,6 +435,35 @@ class Solver:
         self._call("edac_read_tangent_history", m, _ptr(dfx, C.c_double), _ptr(dfy, C.c_double),
                    C.byref(ns))
         return dfx[: ns.value].copy(), dfy[: ns.value].copy()
+
+    def adjoint(self, nsteps: int, checkpoint_every: int = 50, w_fx=None, w_fy=None, w_pe=None,
+                pe_window=(0.0, 0.0)):
+        """Reverse-mode gradient (edac_adjoint_run) of L = sum_n w_fx[n] F_x^n + w_fy[n] F_y^n
+        + w_pe[n] sum_{fluid in pe_window} p^2 over nsteps steps from the freshly uploaded
+        state, with respect to the 8 inlet modes: (L, dL/da).  The workspace (checkpoints
+        every checkpoint_every steps) is a torch tensor freed on return."""
+        torch = self.torch
+        nb = C.c_size_t(0)
+        self._call("edac_adjoint_workspace_bytes", int(nsteps), int(checkpoint_every), C.byref(nb))
+        with torch.cuda.device(self.device):
+            ws = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+
+        def arr(w):
+            if w is None:
+                return None
+            a = np.ascontiguousarray(w, dtype=np.float64)
+            assert a.shape == (int(nsteps),)
+            return a
+
+        wx, wy, wp = arr(w_fx), arr(w_fy), arr(w_pe)
+        loss = C.c_double(0.0)
+        grad = np.zeros(8)
+        self._call("edac_adjoint_run", C.c_void_p(ws.data_ptr()), nb.value, int(nsteps),
+                   int(checkpoint_every), *[_ptr(a, C.c_double) if a is not None else None
+                                            for a in (wx, wy, wp)],
+                   float(pe_window[0]), float(pe_window[1]), C.byref(loss), _ptr(grad, C.c_double))
+        del ws
+        return loss.value, grad
 
     def set_tiling(self, tile_cells: int, threads: int):
         """Tiling of the mixed pair passes (edac_set_tiling)."""

@@ -238,8 +238,10 @@ size_t layout(Dev &d, const Geo &g, int cap, int max_history, int mixed, char *b
         DARR(nbm, uint4, C);
         d.UV = d.DUV = d.PV = d.RM = nullptr;
         d.Ms = nullptr;
+        d.GS = nullptr;
     } else {
         DARR(UV, double2, C); DARR(DUV, double2, C); DARR(PV, double2, C); DARR(RM, double2, C);
+        DARR(GS, double, 3 * C);
         DARR(Ms, double, C);
         d.Bf = d.Qf = nullptr;
         d.nbm = nullptr;
@@ -996,6 +998,179 @@ edac_status edac_step_tangent(edac_ctx *ctx, int nsteps)
     }
     ctx->tangent_steps += nsteps;
     CK(cudaGetLastError());
+    return EDAC_OK;
+}
+
+// ------------------------------------------------------------ reverse-mode adjoint
+namespace {
+
+// one fp64 evaluation of the values (the sequence the tangent model interleaves with)
+int value_eval(edac_ctx *c, int end_of_step)
+{
+    const Dev &d = c->d;
+    cudaStream_t s = c->stream;
+    int n = 0;
+    n += launch_rebuild(d, s, 0);
+    n += launch_pass_a(d, s, 0);
+    n += launch_boundary(d, s, 0, end_of_step);
+    n += launch_pass_b(d, s, 0);
+    return n;
+}
+
+// One step of values, eager.  With aws: the decisions its adjoint holds fixed are recorded
+// in record rec (the ring write index before the corrector, the gate after it, the tags
+// before recycling), and the workspace after the first evaluation is copied to mid.
+int value_step(edac_ctx *c, void *aws = nullptr, int nsteps_ws = 0, int nrec = 0, int rec = 0,
+               void *mid = nullptr)
+{
+    const Dev &d = c->d;
+    cudaStream_t s = c->stream;
+    int n = 0;
+    n += launch_stage(d, s, 0, 0);
+    n += value_eval(c, 0);
+    if (mid) cudaMemcpyAsync(mid, c->ws, c->ws_bytes, cudaMemcpyDeviceToDevice, s);
+    if (aws) n += launch_adjoint(d, aws, nsteps_ws, nrec, rec, s, AJ_REC_RPOS);
+    n += launch_stage(d, s, 0, 1);
+    if (aws) n += launch_adjoint(d, aws, nsteps_ws, nrec, rec, s, AJ_REC_GATE);
+    n += value_eval(c, 1);
+    if (aws) n += launch_adjoint(d, aws, nsteps_ws, nrec, rec, s, AJ_REC_TAG);
+    n += launch_recycle(d, s);
+    return n;
+}
+
+// workspace copies: the checkpoints, the final state, a segment's states before each step and
+// after the last (K + 1) and after each step's first evaluation (K)
+size_t adjoint_snapshots(int nsteps, int K) { return (size_t)((nsteps + K - 1) / K) + 1 + 2 * (size_t)K + 1; }
+
+}  // namespace
+
+edac_status edac_adjoint_workspace_bytes(edac_ctx *ctx, int nsteps, int checkpoint_every,
+                                         size_t *bytes)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    if (!bytes || nsteps < 1 || checkpoint_every < 1)
+        return fail(ctx, EDAC_E_INVALID, "adjoint: nsteps >= 1, checkpoint_every >= 1, bytes not NULL");
+    const size_t wsb = (ctx->ws_bytes + 255) & ~(size_t)255;
+    const size_t ab = (adjoint_bytes(ctx->d, nsteps, checkpoint_every) + 255) & ~(size_t)255;
+    *bytes = ab + adjoint_snapshots(nsteps, checkpoint_every) * wsb;
+    return EDAC_OK;
+}
+
+edac_status edac_adjoint_run(edac_ctx *ctx, void *d_workspace, size_t bytes, int nsteps,
+                             int checkpoint_every, const double *h_w_fx, const double *h_w_fy,
+                             const double *h_w_pe, double pe_x0, double pe_x1, double *h_loss,
+                             double *h_grad)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    if (ctx->mixed) return fail(ctx, EDAC_E_STATE, "the adjoint is built on the fp64 path");
+    if (!ctx->loaded) return fail(ctx, EDAC_E_STATE, "no particles");
+    if (ctx->failed) return fail(ctx, EDAC_E_STATE, "context in error");
+    const Phys &ph = ctx->d.ph;
+    if (ph.in_kind != IN_MODES || (ph.has_outlet && ph.outlet_kind != OUT_HYBRID))
+        return fail(ctx, EDAC_E_STATE, "the adjoint covers the steady inlet modes and the hybrid outlet");
+    if (nsteps < 1 || checkpoint_every < 1 || !h_grad)
+        return fail(ctx, EDAC_E_INVALID, "adjoint: nsteps >= 1, checkpoint_every >= 1, h_grad not NULL");
+    if (nsteps > ctx->d.max_history)
+        return fail(ctx, EDAC_E_INVALID, "adjoint: nsteps exceeds the context's history (max_history)");
+    if (h_w_pe && !(pe_x1 > pe_x0))
+        return fail(ctx, EDAC_E_INVALID, "adjoint: the pressure-energy window needs pe_x1 > pe_x0");
+    if (any_profiling(ctx)) return fail(ctx, EDAC_E_STATE, "kernel profiling is on");
+    size_t need = 0;
+    edac_status st = edac_adjoint_workspace_bytes(ctx, nsteps, checkpoint_every, &need);
+    if (st) return st;
+    if (!d_workspace || bytes < need || ((uintptr_t)d_workspace & 255u))
+        return fail(ctx, EDAC_E_INVALID, "adjoint workspace missing, too small or not 256-byte aligned");
+    Counters h0;
+    CK(cudaMemcpyAsync(&h0, ctx->d.cnt, sizeof(h0), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (h0.err) {
+        ctx->failed = true;
+        return fail(ctx, EDAC_E_STATE, "context in error");
+    }
+    if (h0.step != 0) return fail(ctx, EDAC_E_STATE, "run the adjoint from a freshly uploaded state (no steps taken)");
+    const Dev &d = ctx->d;
+    cudaStream_t s = ctx->stream;
+    const int N = nsteps, K = checkpoint_every, nseg = (N + K - 1) / K;
+    char *aws = static_cast<char *>(d_workspace);
+    const size_t ab = (adjoint_bytes(d, N, K) + 255) & ~(size_t)255;
+    const size_t wsb = (ctx->ws_bytes + 255) & ~(size_t)255;
+    char *snaps = aws + ab;
+    auto ckpt = [&](int i) { return snaps + (size_t)i * wsb; };
+    char *fin = snaps + (size_t)nseg * wsb;
+    auto state = [&](int j) { return snaps + (size_t)(nseg + 1 + j) * wsb; };      // j = 0..K
+    auto mid = [&](int j) { return snaps + (size_t)(nseg + 2 + K + j) * wsb; };    // j = 0..K-1
+    auto copy = [&](void *dst, const void *src) {
+        return cudaMemcpyAsync(dst, src, ctx->ws_bytes, cudaMemcpyDeviceToDevice, s);
+    };
+    auto w_at = [](const double *w, int n) { return w ? w[n] : 0.0; };
+    auto adj = [&](int rec, int what, double p0 = 0.0, double p1 = 0.0, double p2 = 0.0) {
+        return launch_adjoint(d, aws, N, K, rec, s, what, p0, p1, p2);
+    };
+    long long launches = 0;
+    launches += adj(0, AJ_ZERO);
+    // forward: checkpoints every K steps, the pressure energy of every step
+    for (int n = 0; n < N; ++n) {
+        if (n % K == 0) CK(copy(ckpt(n / K), ctx->ws));
+        launches += value_step(ctx);
+        if (h_w_pe) launches += adj(0, AJ_PE_VALUE, (double)n, pe_x0, pe_x1);
+    }
+    CK(copy(fin, ctx->ws));
+    CK(cudaGetLastError());
+    // the loss from the forward history
+    Counters h;
+    CK(cudaMemcpyAsync(&h, d.cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+    std::vector<double> hist((size_t)d.max_history * 8), pe((size_t)N, 0.0);
+    CK(cudaMemcpyAsync(hist.data(), d.hist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost, s));
+    if (h_w_pe)
+        CK(cudaMemcpyAsync(pe.data(), adjoint_pe(d, aws, N, K), sizeof(double) * (size_t)N,
+                           cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h.err) {
+        CK(copy(ctx->ws, fin));
+        ctx->failed = true;
+        return fail(ctx, EDAC_E_STATE, "the forward run of the adjoint set the device error word");
+    }
+    double L = 0.0;
+    for (int n = 0; n < N; ++n) {
+        const double *rec = hist.data() + (size_t)(n % d.max_history) * 8;
+        L += w_at(h_w_fx, n) * rec[0] + w_at(h_w_fy, n) * rec[1] + w_at(h_w_pe, n) * pe[(size_t)n];
+    }
+    // reverse: each segment recomputed once from its checkpoint, keeping the workspace after
+    // the first evaluation and at the end of every step and the step's decisions; then its
+    // steps reversed from those copies
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int n0 = sg * K, len = std::min(K, N - n0);
+        CK(copy(ctx->ws, ckpt(sg)));
+        for (int j = 0; j < len; ++j) {
+            launches += value_step(ctx, aws, N, K, j, mid(j));
+            CK(copy(state(j + 1), ctx->ws));
+        }
+        for (int j = len - 1; j >= 0; --j) {
+            const int n = n0 + j;
+            CK(copy(ctx->ws, state(j + 1)));
+            if (w_at(h_w_pe, n) != 0.0) launches += adj(j, AJ_PE_SEED, w_at(h_w_pe, n), pe_x0, pe_x1);
+            launches += adj(j, AJ_RECYCLE);
+            launches += adj(j, AJ_EVAL, 1.0, w_at(h_w_fx, n), w_at(h_w_fy, n));
+            launches += adj(j, AJ_STAGE_CORR, d.ph.dt);
+            CK(copy(ctx->ws, mid(j)));
+            launches += adj(j, AJ_EVAL, 0.0);
+            launches += adj(j, AJ_STAGE_PRED, 0.5 * d.ph.dt);
+        }
+        CK(cudaGetLastError());
+    }
+    // the evaluation and set-up of the upload
+    CK(copy(ctx->ws, ckpt(0)));
+    launches += adj(0, AJ_EVAL, 0.0);
+    launches += adj(0, AJ_INIT);
+    launches += adj(0, AJ_REDUCE);
+    double g[T_DIR];
+    CK(cudaMemcpyAsync(g, adjoint_grad(d, aws, N, K), sizeof(g), cudaMemcpyDeviceToHost, s));
+    CK(copy(ctx->ws, fin));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    ctx->launches += launches;
+    for (int c = 0; c < T_DIR; ++c) h_grad[c] = g[c];
+    if (h_loss) *h_loss = L;
     return EDAC_OK;
 }
 

@@ -119,6 +119,7 @@ struct Dev {
     double2 *PV;       // (p, V)
     double2 *RM;       // (rho, m / rho)
     double *Ms;        // m
+    double *GS;        // [3 per k] pass B's sums G_x, G_y, sum (p_j - p_i) (the adjoint reads them)
     // mixed path
     float4 *Bf;        // (u, v, u~ - u, v~ - v)
     float4 *Qf;        // (p, V, rho, m / rho)
@@ -442,6 +443,17 @@ enum : int {
 enum : int { TG_INIT, TG_PASS_A, TG_BOUNDARY, TG_PASS_B, TG_OUTLET, TG_STAGE_PRED, TG_STAGE_CORR,
              TG_RECYCLE_PRE, TG_RECYCLE_POST };
 size_t tangent_bytes(const Dev &d);
+// Reverse-mode adjoint of the fp64 step (edac_adjoint.cu): slot-indexed lambdas of every
+// field, per-evaluation temporaries and the recorded decisions of a recomputed step, in a
+// workspace of their own; one operation's adjoint kernels per launch_adjoint call.
+enum : int { AJ_ZERO, AJ_PE_VALUE, AJ_PE_SEED, AJ_REC_RPOS, AJ_REC_GATE, AJ_REC_TAG, AJ_RECYCLE,
+             AJ_EVAL, AJ_STAGE_CORR, AJ_STAGE_PRED, AJ_INIT, AJ_REDUCE };
+// nrec: steps whose decisions are recorded at a time (a segment), rec: the one in use
+size_t adjoint_bytes(const Dev &d, int nsteps, int nrec);
+int launch_adjoint(const Dev &d, void *ws, int nsteps, int nrec, int rec, cudaStream_t s, int what,
+                   double p0 = 0.0, double p1 = 0.0, double p2 = 0.0);
+const double *adjoint_grad(const Dev &d, const void *ws, int nsteps, int nrec);
+const double *adjoint_pe(const Dev &d, const void *ws, int nsteps, int nrec);
 const double *tangent_hist(const Dev &d, const void *ws);
 int launch_tangent(const Dev &d, void *ws, cudaStream_t s, int what, double tau);
 int launch_pass_a(const Dev &d, cudaStream_t s, int mixed);

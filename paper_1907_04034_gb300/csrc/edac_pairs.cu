@@ -204,6 +204,10 @@ __device__ __forceinline__ void pass_b64(const Dev &d, int bid, int nblk)
         // -sum c p~ gW = -sum c (pbar - p_i) gW + (p_avg - p_i) G   (with p_avg) or - p_i G;
         // the solid force takes pbar_ij itself (no p_avg shift on its one-sided fluid sum)
         const double corr = (ph.use_pavg && !solid) ? f.sdp / (double)N : -pv.x;
+        // the sums the epilogue multiplies, kept for the reverse-mode adjoint
+        d.GS[3 * (size_t)k] = f.gxs;
+        d.GS[3 * (size_t)k + 1] = f.gys;
+        d.GS[3 * (size_t)k + 2] = f.sdp;
         if (solid) {
             d.fx[s] = f.ax + corr * f.gxs;
             d.fy[s] = f.ay + corr * f.gys;

@@ -774,17 +774,99 @@ def test_tangent_gradient_matches_the_oracle():
 
 
 @pytest.mark.gpu
-def test_mean_drag_autograd_function():
+@pytest.mark.parametrize("method", ["adjoint", "tangent"])
+def test_mean_drag_autograd_function(method):
+    """torch.autograd.Function: the reverse-mode adjoint (default) or the tangent model."""
     import torch
 
     from paper_1907_04034_gb300 import gradient
 
     c, a = _grad_case()
     at = torch.tensor(a, dtype=torch.float64, requires_grad=True)
-    L = gradient.mean_drag(at, c, 20)
+    L = gradient.mean_drag(at, c, 40, method=method, checkpoint_every=10)
     L.backward()
-    _, g, _ = gradient.drag_gradient(c, a, 20)
+    if method == "tangent":
+        _, g, _ = gradient.drag_gradient(c, a, 40)
+    else:
+        _, g, _ = gradient.drag_gradient_adjoint(c, a, 40, 10)
     np.testing.assert_allclose(at.grad.numpy(), g, rtol=1e-12, atol=0)
+    L0, _ = gradient.drag_loss(c, a, 40)
+    assert float(L) == pytest.approx(L0, rel=1e-12)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("nsteps,K", [(40, 10), (40, 40), (37, 8)])
+def test_adjoint_gradient_matches_differences_and_tangent(nsteps, K):
+    """Reverse-mode adjoint of the fp64 step (checkpoints every K steps, each segment
+    recomputed once): dL/da of the mean drag against central differences of fp64 runs that
+    took the same recycling events (eps = 1e-6) and against the tangent-linear model, to 1e-5
+    of the largest component each (both have fp32 pair derivatives), and the same for every
+    K."""
+    from paper_1907_04034_gb300 import gradient
+
+    c, a = _grad_case()
+    La, ga, _ = gradient.drag_gradient_adjoint(c, a, nsteps, K)
+    L0, _ = gradient.drag_loss(c, a, nsteps)
+    assert La == pytest.approx(L0, rel=1e-12)
+    gf, same = gradient.central_differences(c, a, nsteps, eps=1e-6)
+    assert all(same.values()), same
+    scale = np.abs(gf).max()
+    assert scale > 0.0
+    np.testing.assert_allclose(ga, gf, rtol=0, atol=1e-5 * scale)
+    _, gt, _ = gradient.drag_gradient(c, a, nsteps)
+    np.testing.assert_allclose(ga, gt, rtol=0, atol=1e-5 * scale)
+    _, g1, _ = gradient.drag_gradient_adjoint(c, a, nsteps, nsteps)
+    np.testing.assert_allclose(ga, g1, rtol=0, atol=1e-12 * scale)
+
+
+@pytest.mark.gpu
+def test_adjoint_pressure_energy_gradient_matches_differences():
+    """The second loss through the same adjoint: the mean pressure energy sum omega(x) p^2 of
+    the fluid in the layer in front of the outlet (two support radii, a weight vanishing at
+    its edges) over 260 steps, which the inlet modes reach as acoustic waves; against central
+    differences of fp64 runs to 1e-5 of the largest component.  The differences take
+    eps = 1e-8: the red/blue classes of the outlet particles and the acoustic gate are
+    discrete, and at eps = 1e-6 one of them flips between the +- runs (the small modes'
+    differences then read 3.96 where eps = 1e-7 and 1e-8 both give the adjoint's 0.383)."""
+    from paper_1907_04034_gb300 import gradient
+
+    c, a = _grad_case()
+    n = 260
+    win = gradient.pressure_energy_window(c)
+    L, g = gradient.pressure_energy_gradient(c, a, n, window=win, checkpoint_every=50)
+    assert L == pytest.approx(gradient.pressure_energy_loss(c, a, n, win), rel=1e-10)
+    eps = 1e-8
+    gf = np.zeros(8)
+    for k in range(8):
+        ap, am = a.copy(), a.copy()
+        ap[k] += eps
+        am[k] -= eps
+        gf[k] = (gradient.pressure_energy_loss(c, ap, n, win) -
+                 gradient.pressure_energy_loss(c, am, n, win)) / (2 * eps)
+    scale = np.abs(gf).max()
+    assert L > 0.0 and scale > 0.0  # the loss responds to the modes
+    np.testing.assert_allclose(g, gf, rtol=0, atol=1e-5 * scale)
+
+
+@pytest.mark.gpu
+def test_adjoint_gradient_on_the_d25_cylinder_over_400_steps():
+    """The gradient workload by the reverse-mode adjoint with checkpoints every 50 steps:
+    cylinder at dx = D/25, p_avg on, modes a_k ~ N(0, 0.02) (seed 0), mean drag over 400
+    steps; against the tangent-linear model to 1e-5 and central differences (eps = 1e-8, see
+    the next test) to 1e-5 of the largest component."""
+    from paper_1907_04034_gb300 import gradient
+
+    c = cases.cylinder(dx=1.0 / 25.0)
+    a = np.random.default_rng(0).normal(0.0, 0.02, 8)
+    La, ga, _ = gradient.drag_gradient_adjoint(c, a, 400, 50)
+    L, g, _ = gradient.drag_gradient(c, a, 400)
+    assert La == pytest.approx(L, rel=1e-12)
+    scale = np.abs(g).max()
+    np.testing.assert_allclose(ga, g, rtol=0, atol=1e-5 * scale)
+    gf, same = gradient.central_differences(c, a, 400, eps=1e-8, modes=[0, 2, 4])
+    assert all(same.values()), same
+    for k in (0, 2, 4):
+        assert abs(ga[k] - gf[k]) <= 1e-5 * scale, (k, ga[k], gf[k])
 
 
 @pytest.mark.gpu
