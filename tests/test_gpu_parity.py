@@ -539,8 +539,9 @@ def test_batch_steps_equal_members_stepped_alone(prec, fused):
     on its own, with members of different tilings, and one member with the mirrored outlet
     (whose kernel only some members run): bitwise, except for the fused form on the mixed
     path, whose batched kernels are separate compilations of the same bodies (the compiler
-    may fuse a multiply and an add in one and not the other): there, fields within 1e-6 of
-    their scale and recycling events exact."""
+    may fuse a multiply and an add in one and not the other, and the fp32 rounding differences
+    grow over the 40 steps): there, fields within 1e-5 of their scale (a tenth of the mixed
+    path's tolerance against the oracle) and recycling events exact."""
     chans = cases.batch_channels(n=4, seed=3, n_min=2000, n_max=5000)
     chans[2].params.outlet_kind = OUTLET_KINDS["mirror"]
     alone = [binding.Solver(c, precision=prec) for c in chans]
@@ -562,7 +563,7 @@ def test_batch_steps_equal_members_stepped_alone(prec, fused):
             if exact or k in ("id", "tag"):
                 np.testing.assert_array_equal(g[k], r[k], err_msg=k)
             else:
-                assert _rel_err(g[k], r[k], 0.5 if k == "p" else 1.0) < 1e-6, k
+                assert _rel_err(g[k], r[k], 0.5 if k == "p" else 1.0) < 1e-5, k
         hs, ha = s.history(), a.history()
         for k in hs:
             if exact or k not in ("fx", "fy", "mass_flux"):
