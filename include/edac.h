@@ -259,7 +259,10 @@ edac_status edac_launch_count(edac_ctx *ctx, int64_t *count);
  * gives EDAC_E_DOMAIN.  The first call on a device (with that device current)
  * looks up the scratch address; make it before any stream capture.  All calls
  * share the scratch, so calls whose GPU work overlaps (other streams, other
- * host threads on the same device) race.  Synchronises params->cuda_stream. */
+ * host threads on the same device) race.  The particles of a cell are visited in
+ * the order the counting atomics give, so the fp64 sums of two calls on the same
+ * input may differ in the last bits (edac_step's cell build ranks them instead).
+ * Synchronises params->cuda_stream. */
 #define EDAC_STATIC_MAX_PARTICLES 262144
 #define EDAC_STATIC_MAX_CELLS 65536
 edac_status edac_density_static(const edac_params *params, int n, const double *d_x,
