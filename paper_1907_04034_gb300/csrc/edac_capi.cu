@@ -235,7 +235,7 @@ size_t layout(Dev &d, const Geo &g, int cap, int max_history, int mixed, char *b
     if (mixed) {
         DARR(Bf, float4, C);
         DARR(Qf, float4, C);
-        DARR(nbm, uint4, C);
+        DARR(nbm, uint4, 2 * C);
         d.UV = d.DUV = d.PV = d.RM = nullptr;
         d.Ms = nullptr;
         d.GS = nullptr;

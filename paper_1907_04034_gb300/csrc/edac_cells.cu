@@ -215,10 +215,20 @@ __device__ __forceinline__ void gather_one(const Dev &d, int s, int k, int c)
     }
 }
 
+// Order key of an fp64 value as an unsigned integer (the IEEE 754 ordering on the bits, on
+// the integer pipe): non-negative values get the sign bit set, negative ones are inverted.
+__device__ __forceinline__ unsigned long long order_key(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
 // One thread per particle in the scattered (atomic) order: the particle's rank among the
-// slots of its cell (ascending slot) fixes its place in the cell order, which therefore does
-// not depend on the order of the counting atomics; the thread then gathers the cell-ordered
-// copies the pair kernels read.  Cells hold ~13 particles, so the rank costs ~13 cached loads.
+// particles of its cell, by x and then by slot, fixes its place in the cell order, which
+// therefore does not depend on the order of the counting atomics; the thread then gathers
+// the cell-ordered copies the pair kernels read.  Sorting a cell by x makes every row of
+// three cells x-sorted, so that the mixed pair passes can take the candidates of a row as a
+// window in x.  Cells hold ~13 particles, so the rank costs ~13 cached loads.
 template <int MIXED>
 __device__ __forceinline__ void cell_gather(const Dev &d, int bid, int nblk)
 {
@@ -233,8 +243,13 @@ __device__ __forceinline__ void cell_gather(const Dev &d, int bid, int nblk)
             const int s = d.order_raw[e];
             const int c = d.slot_cell[s];
             const int j0 = d.cell_start[c], j1 = d.cell_start[c + 1];
+            const unsigned long long ks = order_key(d.x[s]);
             int rank = 0;
-            for (int q = j0; q < j1; ++q) rank += (__ldg(d.order_raw + q) < s);
+            for (int q = j0; q < j1; ++q) {
+                const int sq = __ldg(d.order_raw + q);
+                const unsigned long long kq = order_key(d.x[sq]);
+                rank += (kq < ks) | ((kq == ks) & (sq < s));
+            }
             k = j0 + rank;
             if (e == j0) d.cell_count[c] = 0;  // one thread per non-empty cell clears its count
             gather_one<MIXED>(d, s, k, c);

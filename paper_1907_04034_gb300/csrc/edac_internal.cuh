@@ -123,7 +123,7 @@ struct Dev {
     // mixed path
     float4 *Bf;        // (u, v, u~ - u, v~ - v)
     float4 *Qf;        // (p, V, rho, m / rho)
-    uint4 *nbm;        // neighbour mask over the tiled candidate order (pass A -> pass B)
+    uint4 *nbm;        // [2 per k] neighbour mask over the candidate windows (pass A -> pass B)
     int tile_tx, tile_tpb;  // tiling of the mixed pair passes: cells per tile, threads per block
     int *bnd;          // boundary particles (sorted index), n_bnd of them
     // recycling

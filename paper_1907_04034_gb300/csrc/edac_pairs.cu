@@ -484,25 +484,90 @@ __device__ __forceinline__ void tile_stage(const Dev &d, const TileHdr &th, floa
     }
 }
 
-// The candidate order of a staged particle in virtual cell vi: row 0, row 1, row 2, each the
-// shared-memory range of the three cells vi-1..vi+1.  Pass A and pass B stage the same tile
-// from the same cell table, so a candidate index means the same neighbour in both.
-struct CandRows {
-    int lo0, lo1, lo2, l0, l01, tot;
-    __device__ __forceinline__ CandRows(const TileHdr &th, int vi)
-    {
-        lo0 = th.cstart[0][vi - 1];
-        lo1 = th.cstart[1][vi - 1];
-        lo2 = th.cstart[2][vi - 1];
-        l0 = th.cstart[0][vi + 2] - lo0;
-        l01 = l0 + th.cstart[1][vi + 2] - lo1;
-        tot = l01 + th.cstart[2][vi + 2] - lo2;
-    }
-    __device__ __forceinline__ int smem_of(int c) const
-    {
-        return c < l0 ? lo0 + c : (c < l01 ? lo1 + c - l0 : lo2 + c - l01);
-    }
+// Candidate windows of a staged particle in virtual cell vi.  Every staged row is x-sorted
+// (its cells in x order, a cell's particles by x), so the candidates of row r (0: the row
+// below, 1: the particle's own, 2: the row above) that can lie within 3h of the particle form
+// the window of staged x within the row's reach of the particle's x: 3h in its own row,
+// sqrt((3h)^2 - dy^2) in the others, dy the distance to that row's nearer edge.  A margin of
+// 1e-4 of 3h on every bound keeps the windows supersets of the neighbour sets (the staged
+// fp32 coordinates are within ~1e-7 of the exact ones, and a row's x can step back by one
+// ulp across a cell boundary).  The exact membership test runs on the windows only: about
+// 67 candidates instead of the 3 x 3 block's 117.
+constexpr int WMAX = 64;  // candidates of a row window held in one 64-bit mask word
+
+struct Win {
+    int lo[3], n[3];  // first shared index and length of each row's window
 };
+
+// first t in [a, b) with spos[t].x > xv
+__device__ __forceinline__ int first_above(const float2 *spos, int a, int b, float xv)
+{
+    while (a < b) {
+        const int m = (a + b) >> 1;
+        if (spos[m].x > xv) b = m;
+        else a = m + 1;
+    }
+    return a;
+}
+
+__device__ __forceinline__ Win windows(const Dev &d, const TileHdr &th, const float2 *spos, int vi,
+                                       float2 pi)
+{
+    const float rc2 = d.g.rc2_hi;
+    const float mrg = 1e-4f * sqrtf(rc2);
+    const float sy = d.g.syf;
+    Win w;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int a = th.cstart[r][vi - 1], b = th.cstart[r][vi + 2];
+        const float dy0 = r == 1 ? 0.0f : (r == 0 ? pi.y : sy - pi.y);
+        const float dy = fmaxf(dy0 - mrg, 0.0f);
+        const float reach2 = rc2 - dy * dy;
+        if (!(reach2 > 0.0f)) {
+            w.lo[r] = a;
+            w.n[r] = 0;
+            continue;
+        }
+        const float reach = sqrtf(reach2) + mrg;
+        const int lo = first_above(spos, a, b, pi.x - reach);
+        const int hi = first_above(spos, lo, b, pi.x + reach);
+        w.lo[r] = lo;
+        w.n[r] = hi - lo;
+    }
+    return w;
+}
+
+// The neighbour mask of a particle over its windows, kept from pass A for pass B: a 64-bit
+// word per row window and the windows' first shared indices; over: some window held more
+// than WMAX candidates, and both passes test the windows' candidates directly.
+struct WMask {
+    unsigned long long m[3];
+    int lo[3];
+    bool over;
+};
+
+__device__ __forceinline__ void store_wmask(uint4 *nbm, int k, const WMask &w)
+{
+    nbm[2 * (size_t)k] = make_uint4((unsigned)w.m[0], (unsigned)(w.m[0] >> 32), (unsigned)w.m[1],
+                                    (unsigned)(w.m[1] >> 32));
+    nbm[2 * (size_t)k + 1] = make_uint4((unsigned)w.m[2], (unsigned)(w.m[2] >> 32),
+                                        (unsigned)w.lo[0] | ((unsigned)w.lo[1] << 16),
+                                        (unsigned)w.lo[2] | ((unsigned)w.over << 16));
+}
+
+__device__ __forceinline__ WMask load_wmask(const uint4 *nbm, int k)
+{
+    const uint4 a = nbm[2 * (size_t)k], b = nbm[2 * (size_t)k + 1];
+    WMask w;
+    w.m[0] = (unsigned long long)a.x | ((unsigned long long)a.y << 32);
+    w.m[1] = (unsigned long long)a.z | ((unsigned long long)a.w << 32);
+    w.m[2] = (unsigned long long)b.x | ((unsigned long long)b.y << 32);
+    w.lo[0] = (int)(b.z & 0xffffu);
+    w.lo[1] = (int)(b.z >> 16);
+    w.lo[2] = (int)(b.w & 0xffffu);
+    w.over = (b.w >> 16) != 0u;
+    return w;
+}
 
 __device__ __forceinline__ int tile_of_block(const Dev &d, int bid, int &cx0, int &cy)
 {
@@ -533,94 +598,112 @@ __device__ __forceinline__ void global_neighbors(const Dev &d, int k, const floa
     fold();
 }
 
-// Phase 1 of pass A: walk the candidate order of particle ti (the three cell rows of its 3 x 3
-// block, CandRows) and return the 128-bit mask of its neighbours (itself included); only for
-// cr.tot <= 128.  The loop walks each row's shared-memory range directly in runs that end
-// where a 32-candidate word fills, shifting into the word being filled a tentative bit (r2
-// below the upper band edge: the sign of r2 - hi2) and a band bit (r2 above the lower edge:
-// the sign of lo2 - r2), one funnel shift each; a filled word is bit-reversed into candidate
-// order and filed.  The fp64 test then settles the few band candidates after the loop, so
-// the fp64 work stays out of the candidate loop (a predicated fp64 test would issue for
-// every candidate).  The signs are exact: r2 - hi2 is negative exactly when r2 < hi2 (a
-// difference of unequal floats is never zero), and lo2 - r2 likewise.
-__device__ __forceinline__ uint4 tile_mask(const Dev &d, const TileHdr &th, const float2 *spos,
-                                           const int *sgj, const CandRows &cr, int ti, int vi,
-                                           double qx, double qy)
+// Pass A over the windows in one loop: for every window candidate the mask bits (a tentative
+// bit: r^2 below the upper band edge, the sign of r^2 - hi2; a band bit: above the lower
+// edge, the sign of lo2 - r^2; shifted in with one funnel shift each) and w(q), m w(q) added
+// to the sums.  The branch-free quintic is exactly zero for q >= 3, so a candidate outside
+// the support adds nothing, and one inside the fp32 band but outside the exact support adds
+// w(q) with 3 - q < 1e-4, below 1e-20 of w(0), which the fp32 sums cannot hold: the sums
+// equal those over the neighbours, and the loop's trip count does not depend on membership.
+// The fp64 test settles the band candidates after the loop (kept out of it, so that it is
+// not compiled to predicated fp64 work on every candidate).  The sums are folded into the
+// compensated accumulators once per row.
+__device__ __forceinline__ WMask pass_a_windows(const Dev &d, const float2 *spos, const float *smass,
+                                                const int *sgj, const Win &wn, float2 pi, double qx,
+                                                double qy, MixA &f)
 {
-    const float2 pi = spos[ti];
-    const float hi2 = d.g.rc2_hi, lo2 = d.g.rc2_lo;
-    unsigned w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u, b0 = 0u, b1 = 0u, b2 = 0u, b3 = 0u;
-    unsigned cur = 0u, bcur = 0u;  // the word being filled, newest candidate in bit 0
-    int nfill = 0, q = 0;
-    auto file = [&]() {  // candidate k of the word (k = 0 oldest) goes to bit k of word q
-        const unsigned c = __brev(cur) >> (32 - nfill), bc = __brev(bcur) >> (32 - nfill);
-        w0 = q == 0 ? c : w0; w1 = q == 1 ? c : w1; w2 = q == 2 ? c : w2; w3 = q == 3 ? c : w3;
-        b0 = q == 0 ? bc : b0; b1 = q == 1 ? bc : b1; b2 = q == 2 ? bc : b2; b3 = q == 3 ? bc : b3;
-        ++q;
-        cur = bcur = 0u;
-        nfill = 0;
-    };
+    const float hi2 = d.g.rc2_hi, lo2 = d.g.rc2_lo, inv_h = f.inv_h;
+    WMask wm;
+    wm.over = false;
+    unsigned long long band[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        int t = th.cstart[r][vi - 1];
-        const int hi = th.cstart[r][vi + 2];
-        while (t < hi) {
-            const int e = t + min(hi - t, 32 - nfill);
-            nfill += e - t;
-#pragma unroll 4
-            for (; t < e; ++t) {
+        wm.lo[r] = wn.lo[r];
+        unsigned word[2], bword[2];
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+            const int c0 = 32 * hf, cnt = min(32, wn.n[r] - c0);
+            unsigned cur = 0u, bcur = 0u;
+            const int t0 = wn.lo[r] + c0;
+#pragma unroll 2
+            for (int c = 0; c < cnt; ++c) {
+                const int t = t0 + c;
                 const float2 pj = spos[t];
                 const float2 dd = __fadd2_rn(pi, f2(-pj.x, -pj.y));
                 const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
                 cur = __funnelshift_l(__float_as_uint(r2 - hi2), cur, 1);
                 bcur = __funnelshift_l(__float_as_uint(lo2 - r2), bcur, 1);
+                const float w = w_fast(r2 * inv_r_of(r2) * inv_h);
+                f.s += w;
+                f.r = fmaf(smass[t], w, f.r);
             }
-            if (nfill == 32) file();
+            word[hf] = cnt > 0 ? __brev(cur) >> (32 - cnt) : 0u;
+            bword[hf] = cnt > 0 ? __brev(bcur) >> (32 - cnt) : 0u;
         }
+        f.fold();
+        wm.m[r] = (unsigned long long)word[0] | ((unsigned long long)word[1] << 32);
+        band[r] = wm.m[r] & ((unsigned long long)bword[0] | ((unsigned long long)bword[1] << 32));
     }
-    if (nfill > 0) file();
-    uint4 m = make_uint4(w0, w1, w2, w3);
-    const uint4 bb = make_uint4(b0 & w0, b1 & w1, b2 & w2, b3 & w3);
-    if (bb.x | bb.y | bb.z | bb.w) {
-        unsigned bw[4] = {bb.x, bb.y, bb.z, bb.w};
-        unsigned mw[4] = {m.x, m.y, m.z, m.w};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+    for (int r = 0; r < 3; ++r) {
+        unsigned long long bw = band[r];
 #pragma unroll 1
-            while (bw[k]) {
-                const int b = __ffs(bw[k]) - 1;
-                bw[k] &= bw[k] - 1u;
-                const double2 xy = d.XY[sgj[cr.smem_of(32 * k + b)]];
-                double ex, ey;
-                if (!(exact_r2(d.g, qx, qy, xy.x, xy.y, ex, ey) < d.g.rc2)) mw[k] &= ~(1u << b);
-            }
+        while (bw) {
+            const int b = __ffsll((long long)bw) - 1;
+            bw &= bw - 1ull;
+            const double2 xy = d.XY[sgj[wn.lo[r] + b]];
+            double ex, ey;
+            if (!(exact_r2(d.g, qx, qy, xy.x, xy.y, ex, ey) < d.g.rc2)) wm.m[r] &= ~(1ull << b);
         }
-        m = make_uint4(mw[0], mw[1], mw[2], mw[3]);
     }
-    return m;
+    f.n = __popcll(wm.m[0]) + __popcll(wm.m[1]) + __popcll(wm.m[2]);
+    return wm;
 }
 
-// Run body(t) over the set bits of a candidate mask (shared indices t), calling fold() at the
-// end and either each time a lane's 32-candidate word runs out (EVERY = 0) or after every
-// EVERY terms.  The second form folds at the same iterations in every lane of a warp, so an
-// expensive fold (pass B's) runs once per warp instead of once for every lane whose word ran
-// out at another iteration; a cheap one (pass A's) costs less than the per-term count test.
-template <int EVERY, class Body, class Fold>
-__device__ __forceinline__ void for_mask(const CandRows &cr, uint4 m, Body &&body, Fold &&fold)
+// The candidates of the windows with the membership test (windows over WMAX candidates):
+// body(t) over the neighbours, fold() after each row.
+template <class Body, class Fold>
+__device__ __forceinline__ void windows_tested(const Dev &d, const float2 *spos, const int *sgj,
+                                               const Win &wn, float2 pi, double qx, double qy,
+                                               Body &&body, Fold &&fold)
 {
-    unsigned w0 = m.x, w1 = m.y, w2 = m.z, w3 = m.w;
-    const int np = __popc(w0) + __popc(w1) + __popc(w2) + __popc(w3);
-    int base = 0;
+#pragma unroll 1
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll 1
+        for (int t = wn.lo[r]; t < wn.lo[r] + wn.n[r]; ++t) {
+            const float2 pj = spos[t];
+            const float2 dd = __fadd2_rn(pi, f2(-pj.x, -pj.y));
+            const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
+            if (r2 >= d.g.rc2_hi) continue;
+            if (r2 > d.g.rc2_lo) {
+                const double2 xj = d.XY[sgj[t]];
+                double ex, ey;
+                if (!(exact_r2(d.g, qx, qy, xj.x, xj.y, ex, ey) < d.g.rc2)) continue;
+            }
+            body(t);
+        }
+        fold();
+    }
+}
+
+// Run body(t) over the set bits of a window mask (shared indices t), calling fold() after
+// every EVERY terms (at the same iterations in every lane of a warp, so that the fold runs
+// once per warp) and at the end.
+template <int EVERY, class Body, class Fold>
+__device__ __forceinline__ void for_wmask(const WMask &m, Body &&body, Fold &&fold)
+{
+    unsigned long long w0 = m.m[0], w1 = m.m[1], w2 = m.m[2];
+    int b0 = m.lo[0], b1 = m.lo[1], b2 = m.lo[2];
+    const int np = __popcll(w0) + __popcll(w1) + __popcll(w2);
 #pragma unroll 1
     for (int it = 0; it < np; ++it) {
-        while (w0 == 0u) {
-            w0 = w1; w1 = w2; w2 = w3; w3 = 0u;
-            base += 32;
-            if (EVERY == 0) fold();
+        while (w0 == 0ull) {
+            w0 = w1; w1 = w2; w2 = 0ull;
+            b0 = b1; b1 = b2;
         }
-        const int b = __ffs(w0) - 1;
-        w0 &= w0 - 1u;
-        body(cr.smem_of(base + b));
+        const int b = __ffsll((long long)w0) - 1;
+        w0 &= w0 - 1ull;
+        body(b0 + b);
         if (EVERY > 0 && it % EVERY == EVERY - 1) fold();
     }
     fold();
@@ -650,33 +733,22 @@ __device__ __forceinline__ void pass_a_tiled(const Dev &d, int bid)
             const int ti = th.cstart[1][1] + ii;
             const int vi = d.cellk[k] - cy * d.g.nx - cx0 + 1;
             const float2 pi = spos[ti];
-            const CandRows cr(th, vi);
-            auto body = [&](int t) {
-                const float2 pj = spos[t];
-                f.add(__fadd2_rn(pi, f2(-pj.x, -pj.y)), smass[t]);
-            };
-            if (cr.tot <= 128) {
-                // phase 1: the neighbour mask over the candidate order (also pass B's input);
-                // phase 2: the pair terms over its set bits
-                const uint4 m = tile_mask(d, th, spos, sgj, cr, ti, vi, xy.x, xy.y);
-                d.nbm[k] = m;
-                for_mask<0>(cr, m, body, [&]() { f.fold(); });
+            const Win wn = windows(d, th, spos, vi, pi);
+            if (wn.n[0] <= WMAX && wn.n[1] <= WMAX && wn.n[2] <= WMAX) {
+                // the neighbour mask over the windows (also pass B's input) and the sums
+                store_wmask(d.nbm, k, pass_a_windows(d, spos, smass, sgj, wn, pi, xy.x, xy.y, f));
             } else {
-#pragma unroll 1
-                for (int c = 0; c < cr.tot; ++c) {
-                    const int tj = cr.smem_of(c);
-                    const float2 pj = spos[tj];
-                    const float2 dd = __fadd2_rn(pi, f2(-pj.x, -pj.y));
-                    const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
-                    if (r2 >= d.g.rc2_hi) continue;
-                    if (r2 > d.g.rc2_lo) {
-                        const double2 xj = d.XY[sgj[tj]];
-                        double ex, ey;
-                        if (!(exact_r2(d.g, xy.x, xy.y, xj.x, xj.y, ex, ey) < d.g.rc2)) continue;
-                    }
-                    body(tj);
-                }
-                f.fold();
+                windows_tested(d, spos, sgj, wn, pi, xy.x, xy.y,
+                               [&](int t) {
+                                   const float2 pj = spos[t];
+                                   f.add(__fadd2_rn(pi, f2(-pj.x, -pj.y)), smass[t]);
+                               },
+                               [&]() { f.fold(); });
+                WMask wm;
+                wm.m[0] = wm.m[1] = wm.m[2] = 0ull;
+                wm.lo[0] = wm.lo[1] = wm.lo[2] = 0;
+                wm.over = true;
+                store_wmask(d.nbm, k, wm);
             }
         } else {
             global_neighbors(d, k, pk, xy.x, xy.y,
@@ -720,40 +792,26 @@ __device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th,
     f.a2h = ph.a2hf; f.inv_h = ph.inv_hf; f.nu2 = 2.0f * ph.nuf; f.eh2 = ph.eh2f;
     if (fits) {
         const int ti = th.cstart[1][1] + ii;
-        const int vi = d.cellk[k] - cy * d.g.nx - cx0 + 1;
         const float2 pi = spos[ti];
-        const CandRows cr(th, vi);
         auto body = [&](int tj) {
             const float2 pj = spos[tj];
             f.add(__fadd2_rn(pi, f2(-pj.x, -pj.y)), sq[tj], sb[tj], stg[tj]);
         };
-        if (cr.tot <= 128) {
-            // the neighbours pass A found, as set bits of the candidate order, less the
-            // particle itself (its pair terms are exact zeros: gW = 0, p_j - p_i = 0)
-            uint4 m = d.nbm[k];
-            const int cs = cr.l0 + (ti - cr.lo1), sw = cs >> 5;
-            const unsigned keep = ~(1u << (cs & 31));
-            m.x &= sw == 0 ? keep : ~0u;
-            m.y &= sw == 1 ? keep : ~0u;
-            m.z &= sw == 2 ? keep : ~0u;
-            m.w &= sw == 3 ? keep : ~0u;
-            for_mask<16>(cr, m, body, [&]() { f.fold(); });
+        WMask wm = load_wmask(d.nbm, k);
+        if (!wm.over) {
+            // the neighbours pass A found, as set bits of the windows, less the particle
+            // itself (its pair terms are exact zeros: gW = 0, p_j - p_i = 0)
+            const int cs = ti - wm.lo[1];
+            if (cs >= 0 && cs < WMAX) wm.m[1] &= ~(1ull << cs);
+            for_wmask<16>(wm, body, [&]() { f.fold(); });
         } else {
-#pragma unroll 1
-            for (int c = 0; c < cr.tot; ++c) {
-                const int tj = cr.smem_of(c);
-                const float2 pj = spos[tj];
-                const float2 dd = __fadd2_rn(pi, f2(-pj.x, -pj.y));
-                const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
-                if (r2 >= d.g.rc2_hi) continue;
-                if (r2 > d.g.rc2_lo) {
-                    const double2 xj = d.XY[sgj[tj]];
-                    double ex, ey;
-                    if (!(exact_r2(d.g, xy.x, xy.y, xj.x, xj.y, ex, ey) < d.g.rc2)) continue;
-                }
-                body(tj);
-            }
-            f.fold();
+            const int vi = d.cellk[k] - cy * d.g.nx - cx0 + 1;
+            const Win wn = windows(d, th, spos, vi, pi);
+            windows_tested(d, spos, sgj, wn, pi, xy.x, xy.y,
+                           [&](int tj) {
+                               if (tj != ti) body(tj);
+                           },
+                           [&]() { f.fold(); });
         }
     } else {
         global_neighbors(d, k, pk, xy.x, xy.y,
@@ -815,7 +873,7 @@ __device__ __forceinline__ void pass_b_tiled(const Dev &d, int bid)
     }
 }
 
-__global__ void __launch_bounds__(CT_TPB) k_pass_b_tiled(Dev d) { pass_b_tiled(d, blockIdx.x); }
+__global__ void __launch_bounds__(CT_TPB, 4) k_pass_b_tiled(Dev d) { pass_b_tiled(d, blockIdx.x); }
 __global__ void __launch_bounds__(CT_TPB, 4) k_pass_b_tiled_b(BatchGrid bg)
 {
     run_member(bg, [](const Dev &d, int b, int) { pass_b_tiled(d, b); });
