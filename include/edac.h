@@ -165,9 +165,15 @@ edac_status edac_set_outlet(edac_ctx *ctx, double x_out, int n_layers, int kind,
 
 /* Solid-wall behaviour of tag EDAC_WALL or EDAC_SLIPWALL (Sec. 2 cites Adami et
  * al. 2012): slip = 0 gives the ghost velocity 2 u_wall - <u_fluid>, slip = 1
- * (normal along y) gives (<u>, -<v>); count_in_drag = 1 adds the particles'
- * force (Eq. tvf-momentum_solid) to the drag/lift history.  Defaults: WALL
- * no-slip counted in drag, SLIPWALL slip not counted. */
+ * (normal along y) gives (<u>, -<v>).  count_in_drag adds the particles' force
+ * (Eq. tvf-momentum_solid) to the drag/lift history: 0 not counted; 1 summed
+ * over fluid neighbours with p~_ij the interpolated pressure (rho_j p_i + rho_i
+ * p_j)/(rho_i + rho_j) (the solid-solid pairs of that antisymmetric form cancel
+ * in the body's total); 2 the equation as printed, summed over every neighbour
+ * with the solid particle's own p_avg,i (Eq. pavg) in p~_ij when p_avg is on.
+ * The tangent model and the adjoint take 1 only (EDAC_E_STATE otherwise).
+ * Other values: EDAC_E_INVALID.  Defaults: WALL no-slip counted (1), SLIPWALL
+ * slip not counted. */
 edac_status edac_set_wall(edac_ctx *ctx, int tag, int slip, double uw, double vw,
                           int count_in_drag);
 
@@ -207,6 +213,35 @@ edac_status edac_read_state(edac_ctx *ctx, int cap, uint64_t *h_id, uint8_t *h_t
 edac_status edac_read_history(edac_ctx *ctx, int max_steps, double *h_fx, double *h_fy,
                               double *h_mass_flux, int *h_n_active, int *h_n_spawn,
                               int *h_n_delete, int *h_n_to_outlet, int *nsteps);
+
+/* Recycling event log: the transitions of Sec. 3.4 taken at the end of each step,
+ * one record per event with the step (the step counter after it: 1 for the first
+ * step after edac_set_particles), the kind, the particle id and a second id:
+ *   EDAC_EVENT_DELETE     an outlet particle past x_out + L_out was removed (other 0)
+ *   EDAC_EVENT_TO_OUTLET  a fluid particle past x_out became an outlet particle
+ *                         (other 0)
+ *   EDAC_EVENT_SPAWN      an inlet particle past x_in became fluid (other: its id)
+ *                         and the new inlet particle id was created upstream of it
+ * Within a step: deletions, then conversions to outlet, then spawns, each kind in
+ * ascending id (spawns in ascending parent id, which is ascending new id).
+ * edac_events_bytes: device bytes of a log of max_events records.
+ * edac_events_enable: caller-owned device memory, 256-byte aligned, kept alive while
+ *   it is set (d_log NULL switches the log off); synchronises the stream and empties
+ *   the log.  A step whose events do not all fit is not logged; its events are
+ *   counted as dropped.  A batch member logs into the log set before
+ *   edac_batch_create.  The forward steps of edac_adjoint_run are logged once.
+ * edac_read_events: synchronises, copies the records oldest first into the host
+ *   arrays (each may be NULL; cap: their length), sets *n to their number and
+ *   *n_dropped (may be NULL) to the events not logged, then empties the log.  cap
+ *   below the logged count: EDAC_E_INVALID with *n = that count, log kept.  No log
+ *   set: EDAC_E_STATE. */
+#define EDAC_EVENT_DELETE 0
+#define EDAC_EVENT_TO_OUTLET 1
+#define EDAC_EVENT_SPAWN 2
+edac_status edac_events_bytes(int max_events, size_t *bytes);
+edac_status edac_events_enable(edac_ctx *ctx, void *d_log, size_t bytes);
+edac_status edac_read_events(edac_ctx *ctx, int cap, int *h_step, int *h_kind, uint64_t *h_id,
+                             uint64_t *h_other, int *n, int64_t *n_dropped);
 
 /* Debug: bytes of caller-owned device scratch that edac_read_neighbors() needs at
  * the current positions (rebuilds the cell list and re-counts neighbours;

@@ -81,6 +81,8 @@ class CState(C.Structure):
         ("J2p", _DP), ("advp", _DP), ("redp", _IP),
         ("x0", _DP), ("y0", _DP), ("u0", _DP), ("v0", _DP), ("p0", _DP),
         ("next_id", C.c_uint64), ("error", C.c_int), ("t", C.c_double), ("nstep", C.c_int),
+        ("ev", C.POINTER(C.c_uint64)), ("ev_cap", C.c_int), ("ev_len", C.c_int),
+        ("ev_dropped", C.c_longlong),
     ]
 
 
@@ -182,7 +184,8 @@ _I32 = ("nnb", "rpos", "redp")
 class OracleSim:
     """One particle system integrated by the oracle."""
 
-    def __init__(self, case, neighbor_mode: int = 0, params=None, capacity=None):
+    def __init__(self, case, neighbor_mode: int = 0, params=None, capacity=None,
+                 max_events: int = 0):
         self.case = case
         self.params = params if params is not None else case.params
         self.cp = make_params(self.params, neighbor_mode=neighbor_mode)
@@ -206,6 +209,12 @@ class OracleSim:
         st.id = self.a["id"].ctypes.data_as(C.POINTER(C.c_uint64))
         st.next_id = 0
         st.error = 0
+        # recycling event log (4 words per event: step, kind, id, other id)
+        self.a["ev"] = np.zeros(4 * max(int(max_events), 1), dtype=np.uint64)
+        st.ev = self.a["ev"].ctypes.data_as(C.POINTER(C.c_uint64)) if max_events > 0 else None
+        st.ev_cap = int(max_events)
+        st.ev_len = 0
+        st.ev_dropped = 0
         self.st = st
         self.history = []
         rc = lib().orc_init(C.byref(self.cp), C.byref(self.st))
@@ -239,6 +248,18 @@ class OracleSim:
         if rc:
             raise RuntimeError(f"oracle step failed ({rc})")
         return recs
+
+    def events(self) -> dict:
+        """The recycling events logged since the last call, then empties the log: arrays
+        step, kind (0 delete, 1 fluid->outlet, 2 spawn), id, other (a spawn's parent id)
+        and the number of events dropped for want of room."""
+        k = int(self.st.ev_len)
+        e = self.a["ev"][: 4 * k].reshape(k, 4).copy()
+        out = {"step": e[:, 0].astype(np.int64), "kind": e[:, 1].astype(np.int64),
+               "id": e[:, 2].copy(), "other": e[:, 3].copy(), "dropped": int(self.st.ev_dropped)}
+        self.st.ev_len = 0
+        self.st.ev_dropped = 0
+        return out
 
     def neighbors(self):
         """CSR lists (start[n+1], idx) of array indices, j ascending."""

@@ -95,6 +95,10 @@ typedef struct {
     int error; /* 1: capacity exceeded, 2: particle outside the domain box */
     double t;  /* time of the state: nstep dt */
     int nstep; /* steps done */
+    /* event log (may be NULL): 4 words per event (step, kind, id, other id) */
+    uint64_t *ev;
+    int ev_cap, ev_len;
+    long long ev_dropped;
 } orc_state;
 
 /* one history record per step */
@@ -622,7 +626,10 @@ static void inlet_mirror(const orc_params *P, orc_state *S)
  * cancel in the total, so the fluid-only sum is the body force of Eq.
  * (tvf-momentum_solid); a p_avg,i shift on the one-sided fluid sum would instead
  * subtract about p_i times the surface element and remove the pressure drag
- * that the c_d of Table clcd (Sec. 4.6) contains.
+ * that the c_d of Table clcd (Sec. 4.6) contains.  wall_drag = 2 takes the
+ * equation as printed instead: the sum runs over every neighbour (solid ones
+ * included) and p~_ij carries the solid particle's own p_avg,i (Eq. pavg over
+ * all its neighbours) when p_avg is on.
  * ------------------------------------------------------------------------- */
 static void pass_b(const orc_params *P, orc_state *S, const nlist *L)
 {
@@ -635,11 +642,12 @@ static void pass_b(const orc_params *P, orc_state *S, const nlist *L)
         int ti = S->tag[i];
         int do_fluid = (ti == ORC_FLUID || ti == ORC_INLET);
         int do_solid = is_wall(ti) && P->wall_drag[wall_index(ti)];
+        int literal = do_solid && P->wall_drag[wall_index(ti)] == 2;
         S->au[i] = S->av[i] = S->ap[i] = S->abu[i] = S->abv[i] = 0.0;
         S->fx[i] = S->fy[i] = 0.0;
         if (!do_fluid && !do_solid) continue;
         double pavg = 0.0;
-        if (P->use_pavg && !do_solid) {
+        if (P->use_pavg && (!do_solid || literal)) {
             double sp = 0.0;
             for (int t = L->start[i]; t < L->start[i + 1]; t++) sp += S->p[L->idx[t]];
             pavg = sp / (double)S->nnb[i];
@@ -650,7 +658,7 @@ static void pass_b(const orc_params *P, orc_state *S, const nlist *L)
         double dxs, dys;
         for (int t = L->start[i]; t < L->start[i + 1]; t++) {
             int j = L->idx[t];
-            if (do_solid && S->tag[j] != ORC_FLUID) continue;
+            if (do_solid && !literal && S->tag[j] != ORC_FLUID) continue;
             double r2 = sep(P, S->x[i], S->y[i], S->x[j], S->y[j], &dxs, &dys);
             double r = sqrt(r2);
             double gx = 0.0, gy = 0.0;
@@ -968,18 +976,61 @@ static void move_rec(orc_state *S, int a, int b)
  * Reading: transitions are taken once per step after the outlet update, in
  * ascending id; new ids are handed out in ascending parent id; the new inlet
  * particle copies its parent's y, p and m and takes u = u(y), v = 0. */
+typedef struct {
+    uint64_t id;
+    int i;
+} id_index;
+
+static int by_id(const void *a, const void *b)
+{
+    uint64_t x = ((const id_index *)a)->id, y = ((const id_index *)b)->id;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* Event log: the step's events, kind by kind (deletions, conversions to outlet,
+ * spawns), each list already in ascending id; a step whose events do not all fit
+ * is counted as dropped. */
+static void log_events(orc_state *S, const id_index *del, int nd, const id_index *out, int no,
+                       const id_index *par, const uint64_t *new_id, int ns)
+{
+    if (!S->ev) return;
+    int tot = nd + no + ns;
+    if (S->ev_len + tot > S->ev_cap) {
+        S->ev_dropped += tot;
+        return;
+    }
+    uint64_t *e = S->ev + 4 * (size_t)S->ev_len;
+    for (int k = 0; k < tot; k++, e += 4) {
+        e[0] = (uint64_t)S->nstep;
+        if (k < nd) {
+            e[1] = 0; e[2] = del[k].id; e[3] = 0;
+        } else if (k < nd + no) {
+            e[1] = 1; e[2] = out[k - nd].id; e[3] = 0;
+        } else {
+            e[1] = 2; e[2] = new_id[k - nd - no]; e[3] = par[k - nd - no].id;
+        }
+    }
+    S->ev_len += tot;
+}
+
 static void recycle(const orc_params *P, orc_state *S, orc_hist *H)
 {
     int n = S->n;
     double L_in = P->n_in_layers * P->dx, L_out = P->n_out_layers * P->dx;
     int nspawn = 0, ndel = 0, nout = 0;
     double mflux = 0.0;
-    int *spawn = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
-    unsigned char *del = (unsigned char *)calloc((size_t)(n > 0 ? n : 1), 1);
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    id_index *spawn = (id_index *)malloc(sizeof(id_index) * nn);
+    id_index *dels = (id_index *)malloc(sizeof(id_index) * nn);
+    id_index *outs = (id_index *)malloc(sizeof(id_index) * nn);
+    uint64_t *new_id = (uint64_t *)malloc(sizeof(uint64_t) * nn);
+    unsigned char *del = (unsigned char *)calloc(nn, 1);
     for (int i = 0; i < n; i++) {
         int t = S->tag[i];
         if (P->has_outlet && t == ORC_OUTLET && S->x[i] >= P->x_out + L_out) {
             del[i] = 1;
+            dels[ndel].id = S->id[i];
+            dels[ndel].i = i;
             ndel++;
         } else if (P->has_outlet && t == ORC_FLUID && S->x[i] >= P->x_out) {
             S->tag[i] = ORC_OUTLET;
@@ -998,20 +1049,28 @@ static void recycle(const orc_params *P, orc_state *S, orc_hist *H)
             S->redp[i] = 0;
             S->advp[i] = S->ubar[i];
             mflux += S->m[i];
+            outs[nout].id = S->id[i];
+            outs[nout].i = i;
             nout++;
         } else if (P->has_inlet && t == ORC_INLET && S->x[i] >= P->x_in) {
             S->tag[i] = ORC_FLUID;
             ring_fill(P, S, i);
-            spawn[nspawn++] = i;
+            spawn[nspawn].id = S->id[i];
+            spawn[nspawn].i = i;
+            nspawn++;
         }
     }
+    /* ascending id within each kind; new ids follow the parents' order */
+    qsort(spawn, (size_t)nspawn, sizeof(id_index), by_id);
+    qsort(dels, (size_t)ndel, sizeof(id_index), by_id);
+    qsort(outs, (size_t)nout, sizeof(id_index), by_id);
     /* new inlet particles: data taken before compaction moves the parents */
     double *nx_ = (double *)malloc(sizeof(double) * (size_t)(nspawn + 1));
     double *ny_ = (double *)malloc(sizeof(double) * (size_t)(nspawn + 1));
     double *np_ = (double *)malloc(sizeof(double) * (size_t)(nspawn + 1));
     double *nm_ = (double *)malloc(sizeof(double) * (size_t)(nspawn + 1));
     for (int k = 0; k < nspawn; k++) {
-        int i = spawn[k];
+        int i = spawn[k].i;
         nx_[k] = S->x[i] - L_in;
         ny_[k] = S->y[i];
         np_[k] = S->p[i];
@@ -1024,6 +1083,7 @@ static void recycle(const orc_params *P, orc_state *S, orc_hist *H)
         w++;
     }
     S->n = w;
+    int made = 0;
     for (int k = 0; k < nspawn; k++) {
         if (S->n >= S->cap) {
             S->error = 1;
@@ -1042,6 +1102,7 @@ static void recycle(const orc_params *P, orc_state *S, orc_hist *H)
         S->m[i] = nm_[k];
         S->tag[i] = ORC_INLET;
         S->id[i] = S->next_id++;
+        new_id[made++] = S->id[i];
         S->rho[i] = S->V[i] = 0.0;
         S->nnb[i] = 0;
         S->au[i] = S->av[i] = S->ap[i] = S->abu[i] = S->abv[i] = 0.0;
@@ -1057,7 +1118,11 @@ static void recycle(const orc_params *P, orc_state *S, orc_hist *H)
     H->n_to_outlet = nout;
     H->mass_flux = mflux / P->dt;
     H->n_active = S->n;
+    log_events(S, dels, ndel, outs, nout, spawn, new_id, made);
     free(spawn);
+    free(dels);
+    free(outs);
+    free(new_id);
     free(del);
     free(nx_);
     free(ny_);

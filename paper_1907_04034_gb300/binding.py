@@ -35,6 +35,8 @@ FIELDS = ("x", "y", "u", "v", "ut", "vt", "p", "m", "rho", "vol", "au", "av", "a
           "fx", "fy", "nnb", "ubar", "vbar", "pbar", "J2", "J2p", "advp", "redp", "rpos")
 FIELD_ID = {k: i for i, k in enumerate(FIELDS)}
 KERNELS = {"pass_a": 0, "pass_b": 1, "rebuild": 2, "boundary": 3, "stage": 4, "recycle": 5}
+EVENT_DELETE, EVENT_TO_OUTLET, EVENT_SPAWN = 0, 1, 2
+EVENT_RECORD_BYTES = 24
 
 # every symbol the header declares
 EXPORTS = ("edac_workspace_bytes", "edac_create", "edac_set_inlet", "edac_set_outlet",
@@ -48,6 +50,7 @@ EXPORTS = ("edac_workspace_bytes", "edac_create", "edac_set_inlet", "edac_set_ou
            "edac_set_inlet_transient", "edac_set_outlet_reference", "edac_probe",
            "edac_tangent_workspace_bytes", "edac_tangent_enable", "edac_step_tangent",
            "edac_read_tangent_history", "edac_adjoint_workspace_bytes", "edac_adjoint_run",
+           "edac_events_bytes", "edac_events_enable", "edac_read_events",
            "edac_last_error", "edac_destroy")
 
 
@@ -170,6 +173,11 @@ def load(path: Optional[str] = None):
         L.edac_adjoint_workspace_bytes.argtypes = [_P, i32, i32, C.POINTER(sz)]
         L.edac_adjoint_run.argtypes = [_P, _P, sz, i32, i32, _DP, _DP, _DP, C.c_double, C.c_double,
                                        _DP, _DP]
+        L.edac_events_bytes.argtypes = [i32, C.POINTER(sz)]
+        L.edac_events_enable.argtypes = [_P, _P, sz]
+        L.edac_read_events.argtypes = [_P, i32, C.POINTER(i32), C.POINTER(i32),
+                                       C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                       C.POINTER(i32), C.POINTER(i64)]
         L.edac_last_error.argtypes = [_P]
         L.edac_last_error.restype = C.c_char_p
         L.edac_destroy.argtypes = [_P]
@@ -282,6 +290,7 @@ class Solver:
         self.torch = torch
         self.case = case
         self.params = params if params is not None else case.params
+        self.event_log = None
         self.precision = {"fp64": EDAC_FP64, "mixed": EDAC_MIXED}[precision]
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
@@ -412,6 +421,37 @@ class Solver:
         self._call("edac_probe", len(xs), _ptr(xs, C.c_double), _ptr(ys, C.c_double),
                    _ptr(out, C.c_double))
         return out
+
+    # ------------------------------------------------------------------ event log
+    def events_enable(self, max_events: int):
+        """Log the recycling events of every step (edac_events_enable) into a device tensor
+        of max_events records; 0 switches the log off."""
+        if max_events <= 0:
+            self._call("edac_events_enable", None, 0)
+            self.event_log = None
+            return
+        nb = C.c_size_t(0)
+        self._check(self.lib.edac_events_bytes(int(max_events), C.byref(nb)), None)
+        with self.torch.cuda.device(self.device):
+            log = self.torch.empty(int(nb.value), dtype=self.torch.uint8, device=self.device)
+        self._call("edac_events_enable", C.c_void_p(log.data_ptr()), nb.value)
+        self.event_log = log
+
+    def events(self) -> dict:
+        """The logged events since the last call, oldest first (edac_read_events): arrays
+        step, kind (EVENT_*), id, other, and the number of events dropped."""
+        cap = int(self.event_log.numel()) // EVENT_RECORD_BYTES if self.event_log is not None else 0
+        step = np.zeros(max(cap, 1), np.int32)
+        kind = np.zeros(max(cap, 1), np.int32)
+        ids = np.zeros(max(cap, 1), np.uint64)
+        other = np.zeros(max(cap, 1), np.uint64)
+        n = C.c_int(0)
+        dropped = C.c_int64(0)
+        self._call("edac_read_events", cap, _ptr(step, C.c_int), _ptr(kind, C.c_int),
+                   _ptr(ids, C.c_uint64), _ptr(other, C.c_uint64), C.byref(n), C.byref(dropped))
+        k = n.value
+        return {"step": step[:k].copy(), "kind": kind[:k].copy(), "id": ids[:k].copy(),
+                "other": other[:k].copy(), "dropped": int(dropped.value)}
 
     # ------------------------------------------------------------ tangent-linear model
     def tangent_enable(self):

@@ -74,7 +74,9 @@ class Params:
     # (Sec. 3.1.1), 3 method of characteristics (Sec. 3.3), 4 mirroring (Sec. 3.2)
     outlet_kind: int = 0
     moc_ref: tuple = ()        # (u_ref, p_ref) of the characteristic outlet; () = (U, 0)
-    # walls: per wall tag (WALL, SLIPWALL): slip flag, wall velocity, counted in drag
+    # walls: per wall tag (WALL, SLIPWALL): slip flag, wall velocity, counted in drag (0 no;
+    # 1 fluid neighbours with the interpolated pressure; 2 Eq. tvf-momentum_solid as printed:
+    # every neighbour, p~_ij with the solid particle's p_avg)
     wall_slip: tuple = (0, 1)
     wall_u: tuple = (0.0, 0.0)
     wall_v: tuple = (0.0, 0.0)

@@ -251,7 +251,7 @@ __device__ __forceinline__ int passb_kind(const Dev &d, int k)
 {
     const int t = d.stag[k] & 0x7f;
     if (t == FLUID || t == INLET) return 1;
-    if ((t == WALL && d.ph.wall_drag[0]) || (t == SLIPWALL && d.ph.wall_drag[1])) return 2;
+    if (drag_mode(d.ph, t)) return 2;
     return 0;
 }
 

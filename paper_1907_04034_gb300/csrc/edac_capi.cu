@@ -2,6 +2,7 @@
 // workspace layout, step orchestration (eager or one CUDA graph per step, replayed),
 // uploads and canonical (ascending-id) read-back.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -23,6 +24,12 @@ static_assert(edac::OUT_HYBRID == EDAC_OUTLET_HYBRID && edac::OUT_DONOTHING == E
                   edac::OUT_CHARACTERISTIC == EDAC_OUTLET_CHARACTERISTIC &&
                   edac::OUT_MIRROR == EDAC_OUTLET_MIRROR,
               "outlet kinds of the header and the kernels agree");
+static_assert(edac::EV_DELETE == EDAC_EVENT_DELETE && edac::EV_TO_OUTLET == EDAC_EVENT_TO_OUTLET &&
+                  edac::EV_SPAWN == EDAC_EVENT_SPAWN,
+              "event kinds of the header and the kernels agree");
+static_assert(edac::FLUID == EDAC_FLUID && edac::INLET == EDAC_INLET && edac::OUTLET == EDAC_OUTLET &&
+                  edac::WALL == EDAC_WALL && edac::SLIPWALL == EDAC_SLIPWALL,
+              "particle tags of the header and the kernels agree");
 
 using namespace edac;
 
@@ -493,7 +500,8 @@ edac_status edac_probe(edac_ctx *ctx, int n, const double *h_x, const double *h_
 edac_status edac_set_wall(edac_ctx *ctx, int tag, int slip, double uw, double vw, int count_in_drag)
 {
     if (!ctx) return EDAC_E_INVALID;
-    if ((tag != EDAC_WALL && tag != EDAC_SLIPWALL) || !is_fin(uw) || !is_fin(vw))
+    if ((tag != EDAC_WALL && tag != EDAC_SLIPWALL) || !is_fin(uw) || !is_fin(vw) ||
+        count_in_drag < 0 || count_in_drag > 2)
         return fail(ctx, EDAC_E_INVALID, "bad wall arguments");
     if (ctx->loaded) return fail(ctx, EDAC_E_STATE, "set walls before edac_set_particles");
     const int w = tag == EDAC_WALL ? 0 : 1;
@@ -501,7 +509,7 @@ edac_status edac_set_wall(edac_ctx *ctx, int tag, int slip, double uw, double vw
     ph.wall_slip[w] = slip ? 1 : 0;
     ph.wall_u[w] = uw;
     ph.wall_v[w] = vw;
-    ph.wall_drag[w] = count_in_drag ? 1 : 0;
+    ph.wall_drag[w] = count_in_drag;
     drop_graph(ctx);
     return EDAC_OK;
 }
@@ -550,7 +558,7 @@ edac_status edac_set_particles(edac_ctx *ctx, int n, const double *h_x, const do
                 return;
             }
             const int t = h_tag[i];
-            if ((t == EDAC_WALL && d.ph.wall_drag[0]) || (t == EDAC_SLIPWALL && d.ph.wall_drag[1]))
+            if (drag_mode(d.ph, t))
                 drag_part[c].push_back(i);
         }
     };
@@ -804,6 +812,56 @@ edac_status edac_read_history(edac_ctx *ctx, int max_steps, double *h_fx, double
     return EDAC_OK;
 }
 
+edac_status edac_events_bytes(int max_events, size_t *bytes)
+{
+    if (!bytes || max_events < 0) return EDAC_E_INVALID;
+    *bytes = sizeof(EventRec) * (size_t)max_events;
+    return EDAC_OK;
+}
+
+edac_status edac_events_enable(edac_ctx *ctx, void *d_log, size_t bytes)
+{
+    if (!ctx) return EDAC_E_INVALID;
+    if (d_log && (((uintptr_t)d_log & 255u) || bytes < sizeof(EventRec)))
+        return fail(ctx, EDAC_E_INVALID, "event log not 256-byte aligned or smaller than one record");
+    // kernels already issued keep the previous log: let them finish before it is released
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->d.evlog = static_cast<EventRec *>(d_log);
+    ctx->d.ev_cap = d_log ? (int)std::min<size_t>(bytes / sizeof(EventRec), (size_t)INT_MAX) : 0;
+    CK(cudaMemsetAsync(&ctx->d.cnt->ev_len, 0, sizeof(int), ctx->stream));
+    CK(cudaMemsetAsync(&ctx->d.cnt->ev_dropped, 0, sizeof(unsigned long long), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);
+    return EDAC_OK;
+}
+
+edac_status edac_read_events(edac_ctx *ctx, int cap, int *h_step, int *h_kind, uint64_t *h_id,
+                             uint64_t *h_other, int *n, int64_t *n_dropped)
+{
+    if (!ctx || !n || cap < 0) return EDAC_E_INVALID;
+    if (!ctx->d.evlog) return fail(ctx, EDAC_E_STATE, "no event log: call edac_events_enable first");
+    Counters h;
+    CK(cudaMemcpyAsync(&h, ctx->d.cnt, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *n = h.ev_len;
+    if (h.ev_len > cap) return fail(ctx, EDAC_E_INVALID, "cap is below the number of logged events");
+    std::vector<EventRec> rec((size_t)std::max(h.ev_len, 1));
+    if (h.ev_len > 0)
+        CK(cudaMemcpyAsync(rec.data(), ctx->d.evlog, sizeof(EventRec) * (size_t)h.ev_len,
+                           cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemsetAsync(&ctx->d.cnt->ev_len, 0, sizeof(int), ctx->stream));
+    CK(cudaMemsetAsync(&ctx->d.cnt->ev_dropped, 0, sizeof(unsigned long long), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < h.ev_len; ++i) {
+        if (h_step) h_step[i] = rec[i].step;
+        if (h_kind) h_kind[i] = rec[i].kind;
+        if (h_id) h_id[i] = rec[i].id;
+        if (h_other) h_other[i] = rec[i].other;
+    }
+    if (n_dropped) *n_dropped = (int64_t)h.ev_dropped;
+    return EDAC_OK;
+}
+
 edac_status edac_neighbor_scratch_bytes(edac_ctx *ctx, size_t *bytes)
 {
     if (!ctx || !bytes) return EDAC_E_INVALID;
@@ -962,6 +1020,8 @@ edac_status edac_tangent_enable(edac_ctx *ctx, void *d_workspace, size_t bytes)
     const Phys &ph = ctx->d.ph;
     if (ph.in_kind != IN_MODES || (ph.has_outlet && ph.outlet_kind != OUT_HYBRID))
         return fail(ctx, EDAC_E_STATE, "the tangent model needs the steady inlet modes and the hybrid outlet");
+    if (ph.wall_drag[0] == 2 || ph.wall_drag[1] == 2)
+        return fail(ctx, EDAC_E_STATE, "the tangent model takes the solid force over fluid neighbours (count_in_drag 1)");
     if (!d_workspace || bytes < tangent_bytes(ctx->d) || ((uintptr_t)d_workspace & 255u))
         return fail(ctx, EDAC_E_INVALID, "tangent workspace missing, too small or not 256-byte aligned");
     ctx->tws = d_workspace;
@@ -1068,6 +1128,8 @@ edac_status edac_adjoint_run(edac_ctx *ctx, void *d_workspace, size_t bytes, int
     const Phys &ph = ctx->d.ph;
     if (ph.in_kind != IN_MODES || (ph.has_outlet && ph.outlet_kind != OUT_HYBRID))
         return fail(ctx, EDAC_E_STATE, "the adjoint covers the steady inlet modes and the hybrid outlet");
+    if (ph.wall_drag[0] == 2 || ph.wall_drag[1] == 2)
+        return fail(ctx, EDAC_E_STATE, "the adjoint takes the solid force over fluid neighbours (count_in_drag 1)");
     if (nsteps < 1 || checkpoint_every < 1 || !h_grad)
         return fail(ctx, EDAC_E_INVALID, "adjoint: nsteps >= 1, checkpoint_every >= 1, h_grad not NULL");
     if (nsteps > ctx->d.max_history)

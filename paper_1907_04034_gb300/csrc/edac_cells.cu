@@ -478,7 +478,9 @@ __device__ double block_sum_1024(double v, double *sh)
 // End of a step, one block of 1024 threads: the drag/lift sum over the solid particles
 // (Eq. tvf-momentum_solid summed over the body; fixed-shape tree), the canonical
 // ordering of the recycling events, slot and id hand-out for spawned inlet particles
-// (ascending parent id), the mass flux, and one history record.
+// (ascending parent id), the mass flux, one history record and, when a log is set, the
+// step's events (deletions, conversions to outlet, spawns; each kind in ascending id) or,
+// when they do not all fit, their count as dropped.
 __device__ __forceinline__ void end_step(const Dev &d, double *scratch_m)
 {
     __shared__ double sh[1024];
@@ -497,8 +499,15 @@ __device__ __forceinline__ void end_step(const Dev &d, double *scratch_m)
     const int n_del = min(C->n_del, LIST_MAX);
     const int n_out = min(C->n_out, LIST_MAX);
     const int n_spawn = min(C->n_spawn, LIST_MAX);
+    const int ev0 = C->ev_len, stepno = C->step + 1;
+    const int n_ev = n_del + n_out + min(n_spawn, C->free_top + n_del);
+    const bool logged = d.evlog != nullptr && (long long)ev0 + n_ev <= (long long)d.ev_cap;
     // mass flux: converted masses summed in ascending id order
-    for (int i = t; i < n_out; i += 1024) scratch_m[rank_of(d.ev_out_key, n_out, i)] = d.ev_out_m[i];
+    for (int i = t; i < n_out; i += 1024) {
+        const int r = rank_of(d.ev_out_key, n_out, i);
+        scratch_m[r] = d.ev_out_m[i];
+        if (logged) d.evlog[ev0 + n_del + r] = EventRec{d.ev_out_key[i], 0ull, stepno, EV_TO_OUTLET};
+    }
     __syncthreads();
     double ms = 0.0;
     for (int i = t; i < n_out; i += 1024) ms += scratch_m[i];
@@ -508,6 +517,7 @@ __device__ __forceinline__ void end_step(const Dev &d, double *scratch_m)
     for (int i = t; i < n_del; i += 1024) {
         const int r = rank_of(d.ev_del_key, n_del, i);
         d.free_stack[top0 + r] = d.ev_del_slot[i];
+        if (logged) d.evlog[ev0 + r] = EventRec{d.ev_del_key[i], 0ull, stepno, EV_DELETE};
     }
     __syncthreads();
     const int top1 = top0 + n_del;
@@ -528,6 +538,8 @@ __device__ __forceinline__ void end_step(const Dev &d, double *scratch_m)
         d.p[s] = d.p[ps];
         d.m[s] = d.m[ps];
         d.id[s] = id0 + (unsigned long long)r;
+        if (logged)
+            d.evlog[ev0 + n_del + n_out + r] = EventRec{id0 + (unsigned long long)r, d.ev_spawn_key[i], stepno, EV_SPAWN};
         d.au[s] = d.av[s] = d.ap[s] = d.abu[s] = d.abv[s] = 0.0;
         d.fx[s] = d.fy[s] = 0.0;
         d.rho[s] = d.vol[s] = 0.0;
@@ -554,6 +566,8 @@ __device__ __forceinline__ void end_step(const Dev &d, double *scratch_m)
         C->step += 1;
         C->hist_len = min(C->hist_len + 1, d.max_history);
         C->n_del = 0; C->n_out = 0; C->n_spawn = 0;
+        if (logged) C->ev_len = ev0 + n_ev;
+        else if (d.evlog) C->ev_dropped += (unsigned long long)n_ev;
     }
 }
 

@@ -57,9 +57,16 @@ struct Phys {
     int in_kind;                     // IN_*: inlet velocity in time
     double in_prm[4];                // its parameters
     double x_out, L_out, I_thr;
-    int wall_slip[2], wall_drag[2];
+    int wall_slip[2], wall_drag[2];  // wall_drag: 0 off, 1 fluid neighbours, 2 every neighbour
     double wall_u[2], wall_v[2];
 };
+
+// How a particle of tag t enters the drag: 0 not at all, 1 its force over its fluid
+// neighbours with the interpolated pressure, 2 Eq. tvf-momentum_solid over every neighbour.
+__host__ __device__ __forceinline__ int drag_mode(const Phys &ph, int t)
+{
+    return t == WALL ? ph.wall_drag[0] : t == SLIPWALL ? ph.wall_drag[1] : 0;
+}
 
 // Device counters (one struct in the workspace).
 struct Counters {
@@ -77,7 +84,18 @@ struct Counters {
     int err_rec, err_tag;
     unsigned long long err_id;
     double err_x, err_y;
+    // recycling event log: records written since the last read, events not logged
+    int ev_len;
+    unsigned long long ev_dropped;
 };
+
+// One recycling event of the log (EDAC_EVENT_*): the particle id, a second id (a spawn's
+// parent), the step counter after the step and the kind.
+struct EventRec {
+    unsigned long long id, other;
+    int step, kind;
+};
+enum : int { EV_DELETE = 0, EV_TO_OUTLET = 1, EV_SPAWN = 2 };
 
 // Everything a kernel may touch.
 struct Dev {
@@ -131,6 +149,8 @@ struct Dev {
     unsigned long long *ev_spawn_key; int *ev_spawn_slot;   // [LIST_MAX]
     unsigned long long *ev_del_key;   int *ev_del_slot;     // [LIST_MAX]
     unsigned long long *ev_out_key;   double *ev_out_m;     // [LIST_MAX]
+    EventRec *evlog;   // caller-owned event log (nullptr: not logged), ev_cap records
+    int ev_cap;
     int *drag_slots;   // [n_drag], ascending slot
     int2 *spawn_map;   // [LIST_MAX] (parent slot, new slot) of the last step's spawns
     double *scratch_m; // [LIST_MAX]

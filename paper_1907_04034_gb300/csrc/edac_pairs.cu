@@ -128,12 +128,13 @@ __global__ void __launch_bounds__(TPB) k_pass_a64_b(BatchGrid bg)
 // G_i = sum_j c_ij gW, which is also the background-pressure sum.  The self pair contributes
 // exact zeros (gW = 0, p_j - p_i = 0).
 // Solid particles counted in the drag: F_i = sum_{j fluid} c_ij [ -p~_ij gW + eta~_ij
-// u_ij (gW . r_ij)/(r^2 + eta h^2) ] with u_ij = u_g,i - u_j (Eq. tvf-momentum_solid).
+// u_ij (gW . r_ij)/(r^2 + eta h^2) ] with u_ij = u_g,i - u_j (Eq. tvf-momentum_solid), or
+// with all_nb (the equation as printed) the same sum over every neighbour.
 struct BodyB64 {
     const Dev &d;
     double qx, qy;
     double pi, Vi, rhoi, ui, vi, dui, dvi, mi_inv;
-    bool solid;
+    bool solid, all_nb;
     double ax = 0, ay = 0, apd = 0, gxs = 0, gys = 0, sdp = 0;
     __device__ BodyB64(const Dev &dd, double x, double y) : d(dd), qx(x), qy(y) {}
     __device__ void operator()(unsigned e)
@@ -143,7 +144,7 @@ struct BodyB64 {
         const double2 pv = d.PV[j];  // (p, V)
         const double dp = pv.x - pi;
         sdp += dp;
-        if (solid && (d.stag[j] & 0x7f) != FLUID) return;
+        if (solid && !all_nb && (d.stag[j] & 0x7f) != FLUID) return;
         const double2 xy = d.XY[j];
         double dx, dy;
         const double r2 = exact_r2(d.g, qx, qy, xy.x, xy.y, dx, dy);
@@ -185,7 +186,8 @@ __device__ __forceinline__ void pass_b64(const Dev &d, int bid, int nblk)
     for (int k = bid * blockDim.x + threadIdx.x; k < n; k += nblk * blockDim.x) {
         const int t = d.stag[k] & 0x7f;
         const bool fl = (t == FLUID || t == INLET);
-        const bool solid = (t == WALL && ph.wall_drag[0]) || (t == SLIPWALL && ph.wall_drag[1]);
+        const int dm = drag_mode(ph, t);
+        const bool solid = dm != 0;
         if (!fl && !solid) continue;
         int cx, cy;
         cell_of(d, k, cx, cy);
@@ -200,10 +202,12 @@ __device__ __forceinline__ void pass_b64(const Dev &d, int bid, int nblk)
         f.dui = duv.x; f.dvi = duv.y;
         f.mi_inv = 1.0 / d.Ms[k];
         f.solid = solid;
+        f.all_nb = dm == 2;
         listed_neighbors(d, k, xy.x, xy.y, cx, cy, pk.x, pk.y, lst, f);
         // -sum c p~ gW = -sum c (pbar - p_i) gW + (p_avg - p_i) G   (with p_avg) or - p_i G;
-        // the solid force takes pbar_ij itself (no p_avg shift on its one-sided fluid sum)
-        const double corr = (ph.use_pavg && !solid) ? f.sdp / (double)N : -pv.x;
+        // the solid force over its fluid neighbours takes pbar_ij itself (no p_avg shift on
+        // that one-sided sum)
+        const double corr = (ph.use_pavg && dm != 1) ? f.sdp / (double)N : -pv.x;
         // the sums the epilogue multiplies, kept for the reverse-mode adjoint
         d.GS[3 * (size_t)k] = f.gxs;
         d.GS[3 * (size_t)k + 1] = f.gys;
@@ -308,9 +312,10 @@ struct MixA {
 };
 
 // Pass B body for a fluid / inlet particle i (SOLID = false) or a solid particle counted in
-// the drag (SOLID = true: fluid neighbours only, no A-term, no pressure rate).
+// the drag (SOLID = true: fluid neighbours only unless all_nb, no A-term, no pressure rate).
 template <bool SOLID>
 struct MixB {
+    bool all_nb = false;
     // i-side constants
     float2 ui;       // (u_i, v_i)
     float2 rdi;      // rho_i (u~_i - u_i, v~_i - v_i)
@@ -326,7 +331,7 @@ struct MixB {
     {
         const float dp = q.x - pi;
         sdp += dp;
-        if (SOLID && (tagj & 0x7f) != FLUID) return;
+        if (SOLID && !all_nb && (tagj & 0x7f) != FLUID) return;
         const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
         const float ir = inv_r_of(r2);
         const float F = a2h * dw_fast(r2 * ir * inv_h) * ir;   // gW = F r_ij
@@ -785,6 +790,7 @@ __device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th,
     const float4 q = d.Qf[k];
     const float4 b = d.Bf[k];
     MixB<SOLID> f;
+    if (SOLID) f.all_nb = drag_mode(ph, d.stag[k] & 0x7f) == 2;
     f.ui = f2(b.x, b.y);
     f.rdi = f2(q.z * b.z, q.z * b.w);
     f.pi = q.x; f.Vi2 = q.y * q.y; f.rhoi = q.z; f.rhoic2 = q.z * ph.c2f;
@@ -826,8 +832,9 @@ __device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th,
     const float G0 = f.gg_h.x + f.gg_l.x, G1 = f.gg_h.y + f.gg_l.y;
     const int N = d.snnb[k];
     // -sum c p~ gW = -sum c (pbar - p_i) gW + (p_avg - p_i) G   (with p_avg) or - p_i G;
-    // the solid force takes pbar_ij itself (no p_avg shift on its one-sided fluid sum)
-    const float corr = (ph.use_pavg && !SOLID) ? f.sdp / (float)N : -q.x;
+    // the solid force over its fluid neighbours takes pbar_ij itself (no p_avg shift on
+    // that one-sided sum)
+    const float corr = (ph.use_pavg && (!SOLID || f.all_nb)) ? f.sdp / (float)N : -q.x;
     const int s = d.order[k];
     if (SOLID) {
         d.fx[s] = f2d(fmaf(corr, G0, sx));
@@ -868,13 +875,13 @@ __device__ __forceinline__ void pass_b_tiled(const Dev &d, int bid)
         const int t = d.stag[th.i0 + ii] & 0x7f;
         if (t == FLUID || t == INLET)
             pass_b_particle<false>(d, th, fits, cy, cx0, ii, spos, sq, sb, stg, sgj);
-        else if ((t == WALL && ph.wall_drag[0]) || (t == SLIPWALL && ph.wall_drag[1]))
+        else if (drag_mode(ph, t))
             pass_b_particle<true>(d, th, fits, cy, cx0, ii, spos, sq, sb, stg, sgj);
     }
 }
 
 __global__ void __launch_bounds__(CT_TPB, 4) k_pass_b_tiled(Dev d) { pass_b_tiled(d, blockIdx.x); }
-__global__ void __launch_bounds__(CT_TPB, 4) k_pass_b_tiled_b(BatchGrid bg)
+__global__ void __launch_bounds__(CT_TPB) k_pass_b_tiled_b(BatchGrid bg)
 {
     run_member(bg, [](const Dev &d, int b, int) { pass_b_tiled(d, b); });
 }

@@ -770,7 +770,7 @@ __global__ void t_pass_b_f(Dev d, TDev t)
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int tag = d.stag[k] & 0x7f;
         const bool fl = (tag == FLUID || tag == INLET);
-        const bool solid = (tag == WALL && ph.wall_drag[0]) || (tag == SLIPWALL && ph.wall_drag[1]);
+        const bool solid = drag_mode(ph, tag) != 0;
         if (!fl && !solid) continue;
         const int i = d.order[k];
         const double2 xy = d.XY[k];

@@ -79,10 +79,13 @@ def coefficients(fx, fy, dt: float, D: float, U: float, rho0: float, t_from: flo
 
 def run(dx_over_d: float = 30.0, Re: float = 200.0, t_end: float = 75.0, t_from: float = None,
         precision: str = "mixed", chunk: int = 5000, device: str = "cuda:0",
-        diagnose: bool = False, outlet: str = "hybrid") -> dict:
+        diagnose: bool = False, outlet: str = "hybrid", drag_reading: int = 1) -> dict:
+    """drag_reading: 1 the solid force over fluid neighbours with the interpolated pressure,
+    2 Eq. tvf-momentum_solid as printed (every neighbour, p~_ij with the solid's p_avg)."""
     import torch
 
     case = paper_cylinder(dx_over_d, Re, outlet=outlet)
+    case.params.wall_drag = (drag_reading, 0)
     p = case.params
     D, U = p.drag_length, p.U
     nsteps = int(math.ceil(t_end * U / D / p.dt)) if D > 0 else 0
@@ -90,7 +93,7 @@ def run(dx_over_d: float = 30.0, Re: float = 200.0, t_end: float = 75.0, t_from:
                             max_history=nsteps + 16)
     torch.cuda.synchronize(torch.device(device))
     out = {"case": f"cylinder Re={Re:g}, 15D x 15D, dx=D/{dx_over_d:g}", "outlet": outlet,
-           "precision": precision,
+           "precision": precision, "drag_reading": drag_reading,
            "particles": case.n, "fluid": int(np.sum(case.tag == cases.FLUID)), "dt": p.dt}
     t0 = time.perf_counter()
     done = 0
@@ -191,6 +194,9 @@ def main():
     ap.add_argument("--diagnose", action="store_true",
                     help="record the per-tag field ranges after every chunk")
     ap.add_argument("--outlet", default="hybrid", choices=tuple(OUTLETS))
+    ap.add_argument("--drag-reading", type=int, default=1, choices=(1, 2),
+                    help="1: solid force over fluid neighbours with the interpolated pressure; "
+                         "2: Eq. tvf-momentum_solid as printed (every neighbour, with p_avg)")
     ap.add_argument("--problem", default=None, choices=("pulse2d", "ramp", "vortex"),
                     help="an outlet test problem of Sec. 4 instead of the cylinder: L2 errors "
                          "at the probe for every outlet against the long domain")
@@ -199,7 +205,7 @@ def main():
         print(json.dumps(outlet_problem_errors(a.problem, precision=a.precision)))
         return
     print(json.dumps(run(a.dx_over_d, a.re, a.t_end, a.t_from, a.precision, a.chunk,
-                         diagnose=a.diagnose, outlet=a.outlet)))
+                         diagnose=a.diagnose, outlet=a.outlet, drag_reading=a.drag_reading)))
 
 
 if __name__ == "__main__":

@@ -98,3 +98,17 @@ def test_binding_declares_the_argument_types_of_every_entry(lib):
     # ctypes converts floats and pointers only for declared signatures
     for name in binding.EXPORTS:
         assert getattr(lib, name).argtypes is not None, name
+
+
+def test_event_log_record_size_and_argument_checks(lib):
+    # edac_events_bytes is host-only arithmetic: one record is binding.EVENT_RECORD_BYTES
+    nb = C.c_size_t(0)
+    assert lib.edac_events_bytes(1, C.byref(nb)) == 0
+    assert nb.value == binding.EVENT_RECORD_BYTES
+    assert lib.edac_events_bytes(1000, C.byref(nb)) == 0
+    assert nb.value == 1000 * binding.EVENT_RECORD_BYTES
+    assert lib.edac_events_bytes(-1, C.byref(nb)) == 1
+    assert lib.edac_events_bytes(1, None) == 1
+    n = C.c_int(0)
+    assert lib.edac_read_events(None, 0, None, None, None, None, C.byref(n), None) == 1
+    assert lib.edac_events_enable(None, None, 0) == 1

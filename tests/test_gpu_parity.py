@@ -183,6 +183,107 @@ def test_cylinder_coarse_window(prec):
     s.close()
 
 
+def _solid_block(seed=11):
+    # every block particle has fluid neighbours at this spacing (r_c = 0.225 > 0.15)
+    c = cases.taylor_green(n=16, jitter=0.2, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    c.u[:] = rng.normal(0.0, 0.5, c.n)
+    c.v[:] = rng.normal(0.0, 0.5, c.n)
+    c.p[:] = rng.normal(0.0, 1.0, c.n)
+    blk = (np.abs(c.x - 0.5) < 0.2) & (np.abs(c.y - 0.5) < 0.15)
+    c.tag[blk] = cases.WALL
+    c.params.use_pavg = 1
+    return c
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+def test_literal_solid_force_matches_oracle(prec):
+    """count_in_drag 2, Eq. tvf-momentum_solid as printed (every neighbour, the solid
+    particle's own p_avg,i): the forces of one evaluation on a solid block in a periodic box
+    and on the cylinder, and the drag history of a 60-step cylinder window, against the
+    oracle.  The force is a diagnostic: the fluid's state is bitwise the one of the
+    fluid-only reading.  The derivative models take the fluid-only reading only."""
+    for make in (_solid_block, lambda: cases.cylinder(dx=1.0 / 8.0, Lx=6.0, H=4.0, xc=2.0)):
+        c = make()
+        c.params.wall_drag = (2, 0)
+        ref = oracle.OracleSim(c)
+        s = binding.Solver(c, precision=prec)
+        compare_eval(s, ref, prec)
+        s.close()
+    runs = {}
+    for drag in (1, 2):
+        c = cases.cylinder(dx=1.0 / 8.0, Lx=6.0, H=4.0, xc=2.0)
+        c.params.wall_drag = (drag, 0)
+        s = binding.Solver(c, precision=prec)
+        s.step(60)
+        runs[drag] = (s.state(("x", "y", "u", "v", "p")), s.history())
+        if drag == 2 and prec == "fp64":
+            with pytest.raises(binding.EdacError):
+                s.tangent_enable()
+        s.close()
+    for k in ("x", "y", "u", "v", "p"):
+        np.testing.assert_array_equal(runs[1][0][k], runs[2][0][k])
+    ref = oracle.OracleSim(c, neighbor_mode=1)
+    ref.step(60)
+    fx = np.array([x["fx"] for x in ref.history])
+    fy = np.array([x["fy"] for x in ref.history])
+    h = runs[2][1]
+    scale = max(np.abs(fx).max(), 1e-3)
+    assert np.abs(h["fx"] - fx).max() / scale < TOL[prec] * 10
+    assert np.abs(h["fy"] - fy).max() / scale < TOL[prec] * 10
+    # the two readings differ (by the solid-solid pairs' p_avg shift)
+    assert np.abs(runs[1][1]["fx"] - h["fx"]).max() > 1e-3 * scale
+
+
+def _assert_same_events(g, r):
+    assert g["dropped"] == r["dropped"]
+    for k in ("step", "kind"):
+        np.testing.assert_array_equal(g[k].astype(np.int64), r[k].astype(np.int64))
+    for k in ("id", "other"):
+        np.testing.assert_array_equal(g[k].astype(np.uint64), r[k].astype(np.uint64))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", ["channel", "cylinder"])
+def test_event_log_matches_the_oracle_event_by_event(prec, name):
+    """The recycling event log (edac_read_events) against the oracle's, record by record:
+    step, kind (deletion, fluid->outlet, spawn), id and parent id, over 200 steps of the pulse
+    channel and 60 of the coarse cylinder; reading empties the log; a log too small for a
+    step drops that step whole and counts its events, as the oracle's does."""
+    make, n = {"channel": (cases.channel, 200),
+               "cylinder": (lambda: cases.cylinder(dx=1.0 / 8.0, Lx=6.0, H=4.0, xc=2.0), 60)}[name]
+    c = make()
+    ref = oracle.OracleSim(c, neighbor_mode=1, max_events=20000)
+    s = binding.Solver(c, precision=prec)
+    s.events_enable(20000)
+    half = n // 2
+    s.step(half)
+    ref.step(half)
+    g1, r1 = s.events(), ref.events()
+    assert len(r1["id"]) > 0 and set(r1["kind"].tolist()) >= {1, 2}
+    _assert_same_events(g1, r1)
+    s.step(n - half)
+    ref.step(n - half)
+    _assert_same_events(s.events(), ref.events())
+    e = s.events()
+    assert len(e["id"]) == 0 and e["dropped"] == 0
+    # a log with room for 3 events
+    s.events_enable(3)
+    ref3 = oracle.OracleSim(c, neighbor_mode=1, max_events=3)
+    s3 = binding.Solver(c, precision=prec)
+    s3.events_enable(3)
+    s3.step(half)
+    ref3.step(half)
+    _assert_same_events(s3.events(), ref3.events())
+    s3.close()
+    s.events_enable(0)
+    with pytest.raises(binding.EdacError):
+        s.events()
+    s.close()
+
+
 OUTLET_KINDS = {"donothing": 1, "mod_donothing": 2, "characteristic": 3, "mirror": 4}
 
 
@@ -580,16 +681,19 @@ def test_fused_batch_matches_the_oracle_and_rejects_mixed_precisions():
     refused."""
     chans = cases.batch_channels(n=3, seed=7, n_min=1500, n_max=3000)
     mem = [binding.Solver(c, precision="mixed") for c in chans]
+    for s in mem:  # the members' event logs, set before the batch is made
+        s.events_enable(20000)
     b = binding.Batch(mem, fused=True)
     assert b.kernels_per_step() <= 24
     b.step(40)
     for s, c in zip(mem, chans):
-        ref = oracle.OracleSim(c)
+        ref = oracle.OracleSim(c, max_events=20000)
         ref.step(40)
         _compare_window(s, ref, "mixed")
         h = s.history(40)
         for k in ("n_active", "n_spawn", "n_delete", "n_to_outlet"):
             np.testing.assert_array_equal(h[k], [x[k] for x in ref.history])
+        _assert_same_events(s.events(), ref.events())
     b.close()
     other = binding.Solver(chans[0], precision="fp64")
     with pytest.raises(binding.EdacError) as e:

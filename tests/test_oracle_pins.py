@@ -220,6 +220,75 @@ def test_solid_force_balances_the_fluid_pressure_force():
     assert np.abs(o.field("fx")[sol]).sum() > 1e-2 * scale
 
 
+def _solid_block_case(seed, drag):
+    c = cases.taylor_green(n=16, jitter=0.3, seed=seed)
+    c.u[:] = 0.0
+    c.v[:] = 0.0
+    blk = (np.abs(c.x - 0.5) < 0.2) & (np.abs(c.y - 0.5) < 0.15)
+    c.tag[blk] = cases.WALL
+    c.params.use_pavg = 1
+    c.params.wall_drag = (drag, 0)
+    return c
+
+
+def test_literal_solid_force_vanishes_for_uniform_pressure():
+    """Eq. tvf-momentum_solid as printed (wall_drag 2): with p uniform (a power of two) on the
+    fluid, hence on the walls, and everything at rest, p_avg,i = p and p~_ij = 0 for every
+    pair, so the force is exactly zero on every solid particle; the fluid-only reading
+    (wall_drag 1) leaves -p sum_(j fluid) c_ij gW_ij on the surface particles."""
+    out = {}
+    for drag in (1, 2):
+        c = _solid_block_case(21, drag)
+        c.p[:] = 2.0
+        o = oracle.OracleSim(c)
+        sol = o.field("tag") == cases.WALL
+        np.testing.assert_array_equal(o.field("p")[sol], 2.0)
+        out[drag] = np.hypot(o.field("fx"), o.field("fy"))[sol]
+    assert np.all(out[2] == 0.0)
+    # about p times the surface element dx on the block's faces
+    assert out[1].max() > 0.5 * 2.0 * c.params.dx
+
+
+def test_literal_solid_force_sums_every_neighbour_with_its_own_pavg():
+    """wall_drag 2: F_i = sum over all j of c_ij [-p~_ij gW + viscous] with p~_ij of Eq.
+    tvf-p-ij-basa (the solid particle's p_avg,i over all its neighbours).  Fluid at rest,
+    random pressure, p_avg on: every pair term between fluid and solid particles is
+    antisymmetric except the p_avg,i shift, so
+        sum_fluid m (a - g) + sum_solid F = sum_(fluid and solid) p_avg,i G_i,
+    G_i = sum_j c_ij gW_ij over all neighbours (brute force here for the solid particles).
+    A fluid-only solid sum, or one without the shift, misses the solid part of the right."""
+    c = _solid_block_case(11, 2)
+    rng = np.random.default_rng(12)
+    c.p[:] = rng.normal(0.0, 1.0, c.n)
+    o = oracle.OracleSim(c)
+    start, idx = o.neighbors()
+    tag, p, m = o.field("tag"), o.field("p"), o.field("m")
+    x, y, V = o.field("x"), o.field("y"), o.field("V")
+    h = c.params.h
+    fl = tag == cases.FLUID
+    sol = tag == cases.WALL
+    pa = np.array([p[idx[start[i]:start[i + 1]]].mean() for i in range(c.n)])
+    Gs = np.zeros((c.n, 2))
+    for i in np.nonzero(sol)[0]:
+        for j in idx[start[i]:start[i + 1]]:
+            d = np.array([x[i] - x[j], y[i] - y[j]])
+            d = np.where(d > 0.5, d - 1.0, np.where(d < -0.5, d + 1.0, d))
+            r = np.hypot(*d)
+            if r > 0.0:
+                Gs[i] += (V[i] ** 2 + V[j] ** 2) * oracle.dWdr(r, h) * d / r
+    lhs = np.zeros(2)
+    rhs = np.zeros(2)
+    for k, (a, ab, f) in enumerate((("au", "abu", "fx"), ("av", "abv", "fy"))):
+        lhs[k] = np.sum(m[fl] * o.field(a)[fl]) + np.sum(o.field(f)[sol])
+        G = -m * o.field(ab) / c.params.pb
+        rhs[k] = np.sum(pa[fl] * G[fl]) + np.sum(pa[sol] * Gs[sol, k])
+    scale = np.sum(np.abs(m[fl] * o.field("au")[fl]))
+    np.testing.assert_allclose(lhs, rhs, rtol=0, atol=1e-10 * scale)
+    # the solid part of the right side is far above the tolerance: a reading without the
+    # shift or without the solid-solid pairs fails the identity
+    assert np.abs(np.sum(pa[sol, None] * Gs[sol], axis=0)).max() > 1e-5 * scale
+
+
 def _wall_and_one_fluid(r, dx=0.05):
     """A no-slip wall particle at the origin and one fluid particle at (r, 0)."""
     cs = 10.0
@@ -410,6 +479,57 @@ def test_recycling_counts_and_conversions():
     # new ids follow ascending parent order and are contiguous
     ids = np.sort(f["id"])
     assert ids[-1] == n0 + sp - 1
+
+
+def _events_from_states(a, b, step, L_in):
+    """The recycling events of one step read off the states before (a) and after (b) it, by
+    id: ids gone = deletions; FLUID -> OUTLET = conversions; new ids = spawns, each matched
+    to the INLET -> FLUID particle at its x + L_in and its y.  Kinds in that order, each in
+    ascending id."""
+    ia = {int(i): k for k, i in enumerate(a["id"])}
+    ib = {int(i): k for k, i in enumerate(b["id"])}
+    gone = sorted(i for i in ia if i not in ib)
+    conv = sorted(i for i in ia if i in ib and a["tag"][ia[i]] == FLUID and b["tag"][ib[i]] == OUTLET)
+    parents = sorted(i for i in ia if i in ib and a["tag"][ia[i]] == INLET and b["tag"][ib[i]] == FLUID)
+    new = sorted(i for i in ib if i not in ia)
+    assert len(new) == len(parents)
+    ev = [(step, 0, i, 0) for i in gone] + [(step, 1, i, 0) for i in conv]
+    for p_id, n_id in zip(parents, new):
+        kp, kn = ib[p_id], ib[n_id]
+        assert b["tag"][kn] == INLET
+        assert b["y"][kn] == b["y"][kp] and abs(b["x"][kn] - (b["x"][kp] - L_in)) < 1e-12
+        ev.append((step, 2, n_id, p_id))
+    return ev
+
+
+def test_event_log_is_the_state_transitions_of_each_step():
+    """The oracle's recycling event log (Sec. 3.4's transitions) against the events read off
+    consecutive states: deletions, fluid->outlet conversions and spawns (new id, parent id)
+    in that order, each in ascending id, with the step number; new ids ascend with the
+    parent ids.  A small log drops whole steps and counts them."""
+    c = cases.channel()
+    o = oracle.OracleSim(c, max_events=10000)
+    L_in = c.params.n_in_layers * c.params.dx
+    want = []
+    a = o.fields(("id", "tag", "x", "y"))
+    for k in range(1, 161):
+        o.step(1)
+        b = o.fields(("id", "tag", "x", "y"))
+        want += _events_from_states(a, b, k, L_in)
+        a = b
+    got = o.events()
+    assert got["dropped"] == 0
+    rows = list(zip(got["step"].tolist(), got["kind"].tolist(), got["id"].tolist(),
+                    got["other"].tolist()))
+    assert rows == want
+    kinds = {kd: sum(1 for r in rows if r[1] == kd) for kd in (0, 1, 2)}
+    assert min(kinds.values()) > 5, kinds  # every kind occurs
+    # a log too small for one step's events keeps nothing of that step and counts it
+    o2 = oracle.OracleSim(cases.channel(), max_events=1)
+    o2.step(160)
+    e2 = o2.events()
+    assert all(np.count_nonzero(e2["step"] == s) == 1 for s in np.unique(e2["step"]))
+    assert len(e2["step"]) + e2["dropped"] == len(rows)
 
 
 def test_acoustic_gate_freezes_time_average():
