@@ -79,7 +79,7 @@ def coefficients(fx, fy, dt: float, D: float, U: float, rho0: float, t_from: flo
 
 def run(dx_over_d: float = 30.0, Re: float = 200.0, t_end: float = 75.0, t_from: float = None,
         precision: str = "mixed", chunk: int = 5000, device: str = "cuda:0",
-        diagnose: bool = False, outlet: str = "hybrid", drag_reading: int = 1) -> dict:
+        diagnose: bool = False, outlet: str = "hybrid", drag_reading: int = 2) -> dict:
     """drag_reading: 1 the solid force over fluid neighbours with the interpolated pressure,
     2 Eq. tvf-momentum_solid as printed (every neighbour, p~_ij with the solid's p_avg)."""
     import torch
@@ -194,7 +194,7 @@ def main():
     ap.add_argument("--diagnose", action="store_true",
                     help="record the per-tag field ranges after every chunk")
     ap.add_argument("--outlet", default="hybrid", choices=tuple(OUTLETS))
-    ap.add_argument("--drag-reading", type=int, default=1, choices=(1, 2),
+    ap.add_argument("--drag-reading", type=int, default=2, choices=(1, 2),
                     help="1: solid force over fluid neighbours with the interpolated pressure; "
                          "2: Eq. tvf-momentum_solid as printed (every neighbour, with p_avg)")
     ap.add_argument("--problem", default=None, choices=("pulse2d", "ramp", "vortex"),
