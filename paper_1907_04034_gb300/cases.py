@@ -224,6 +224,47 @@ def outlet_problem(problem: str = "pulse2d", outlet: int = 0, long: bool = False
     return c
 
 
+def pressure_bump(outlet: int = 0, long: bool = False, dx: float = 0.005, t_end: float = 0.3,
+                  n_rows: int = 12, n_lay: int = 6, av_alpha: float = 0.1) -> Case:
+    """The 1D pressure bump of Sec. 4.1 (Eq. pressurebump): a fluid strip of length 1, periodic
+    across (n_rows particle rows), moving at U = 1 with the inlet at x = 0 and the outlet at
+    x = 1 (six layers each), initial p = 1 - 0.2 exp(-(x - 0.5)^2 / 0.001) Pa in the fluid and
+    1 Pa in the inlet and outlet, rho = 1000 kg/m^3; here rho0 = 1 and p in units of 1000 Pa
+    (so the characteristic outlet's reference (1 m/s, 1 Pa) is (U, 0.001)).  Readings: c = 10 U;
+    the artificial viscosity alpha = 0.1 the paper takes from its source is the kinematic
+    viscosity nu = alpha h c / 8 (the viscosity of Monaghan's term, the form of Eq. edac-nu);
+    the spacing is not given (dx = 0.005: the bump's width sqrt(0.001) spans ~6 particles).
+    The long-domain reference extends the fluid by (c + U) t_end downstream and (c - U) t_end
+    upstream, so that neither acoustic wave reaches an end before t_end."""
+    U, cs, hdx = 1.0, 10.0, 1.2
+    h = hdx * dx
+    rc = 3.0 * h
+    nu = av_alpha * h * cs / 8.0
+    W = n_rows * dx
+    x0 = -(cs - U) * t_end if long else 0.0
+    x1 = 1.0 + (cs + U) * t_end if long else 1.0
+    x0 = dx * math.floor(x0 / dx)
+    x1 = dx * math.ceil(x1 / dx)
+    nx = int(round((x1 - x0) / dx))
+    params = Params(x_min=x0 - n_lay * dx - rc, x_max=x1 + n_lay * dx + rc, y_min=0.0, y_max=W,
+                    periodic_y=1, dx=dx, hdx=hdx, rho0=1.0, U=U, nu=nu, cs=cs, pb=cs * cs,
+                    dt=default_dt(dx, hdx, cs, U, nu),
+                    has_inlet=1, x_in=x0, n_in_layers=n_lay, inlet_y0=0.0, inlet_h=W,
+                    has_outlet=1, x_out=x1, n_out_layers=n_lay, outlet_kind=int(outlet),
+                    moc_ref=(1.0, 1e-3), wall_drag=(0, 0))
+    fx, fy = _lattice(x0, nx, 0.0, n_rows, dx)
+    ix, iy = _lattice(x0 - n_lay * dx, n_lay, 0.0, n_rows, dx)
+    ox, oy = _lattice(x1, n_lay, 0.0, n_rows, dx)
+    c = _assemble("pressure_bump" + ("_long" if long else ""), params,
+                  [(fx, fy, FLUID), (ix, iy, INLET), (ox, oy, OUTLET)],
+                  capacity_extra=int((2.0 * U * t_end / dx + 4) * n_rows) + 64)
+    c.u[:] = U
+    c.p[:] = 1e-3
+    fl = c.tag == FLUID
+    c.p[fl] = 1e-3 * (1.0 - 0.2 * np.exp(-(c.x[fl] - 0.5) ** 2 / 0.001))
+    return c
+
+
 def batch_channels(n: int = 64, seed: int = 0, n_min: int = 2000, n_max: int = 60000,
                    dx_min: float = 0.005, dx_max: float = 0.03, re_min: float = 50.0,
                    re_max: float = 500.0, U: float = 1.0) -> list:

@@ -183,6 +183,59 @@ def outlet_problem_errors(problem: str, t_end: float = None, precision: str = "m
     return out
 
 
+def bump_profiles(case, times, precision: str = "mixed", device: str = "cuda:0") -> np.ndarray:
+    """The pressure of the 1D bump (Sec. 4.1) along x in [0, 1] at each of the times: the mean
+    over the fluid particles in each of the bins [k dx, (k + 1) dx) (all rows of the strip),
+    array (len(times), nbins); an empty bin holds NaN."""
+    p = case.params
+    dx = p.dx
+    nb = int(round(1.0 / dx))
+    steps = [int(round(t / p.dt)) for t in times]
+    s = binding.Solver(case, precision=precision, use_graphs=True, device=device,
+                       max_history=max(steps) + 16)
+    out = np.full((len(times), nb), np.nan)
+    done = 0
+    for i, n in enumerate(steps):
+        s.step(n - done)
+        done = n
+        st = s.state(("x", "p"))
+        fl = (st["tag"] == cases.FLUID) & (st["x"] >= 0.0) & (st["x"] < 1.0)
+        b = np.minimum((st["x"][fl] / dx).astype(np.int64), nb - 1)
+        cnt = np.bincount(b, minlength=nb)
+        tot = np.bincount(b, weights=st["p"][fl], minlength=nb)
+        out[i] = np.where(cnt > 0, tot / np.maximum(cnt, 1), np.nan)
+    s.close()
+    return out
+
+
+def pressure_bump_errors(times=(0.05, 0.1, 0.15, 0.2, 0.25, 0.3), precision: str = "mixed",
+                         outlets=("characteristic", "donothing", "hybrid", "mirror",
+                                  "mod_donothing")) -> dict:
+    """The 1D pressure bump (Sec. 4.1) with each outlet against the long domain: per outlet the
+    L2 error of the pressure profile over x in [0, 1], relative to the bump's depth
+    (0.2 Pa), at each time and over all, and the mean pressure excess over the long domain's
+    at the last time, over the domain and over its last tenth (same relative unit)."""
+    t_end = max(times)
+    depth = 0.2e-3
+    ref = bump_profiles(cases.pressure_bump(outlet=OUTLETS["hybrid"], long=True, t_end=t_end),
+                        times, precision)
+    out = {"times": list(times), "precision": precision, "errors": {}}
+    for name in outlets:
+        c = cases.pressure_bump(outlet=OUTLETS[name], t_end=t_end)
+        try:
+            h = bump_profiles(c, times, precision)
+        except binding.EdacError as e:
+            out["errors"][name] = {"error": str(e)}
+            continue
+        per_t = np.sqrt(np.nanmean((h - ref) ** 2, axis=1)) / depth
+        end = h.shape[1] - h.shape[1] // 10  # the last tenth, x in [0.9, 1)
+        out["errors"][name] = {"per_time": [float(v) for v in per_t],
+                               "all": float(np.sqrt(np.nanmean((h - ref) ** 2)) / depth),
+                               "mean_excess_last": float((np.nanmean(h[-1]) - np.nanmean(ref[-1])) / depth),
+                               "end_excess_last": float(np.nanmean(h[-1, end:] - ref[-1, end:]) / depth)}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--dx-over-d", type=float, default=30.0)
@@ -197,10 +250,13 @@ def main():
     ap.add_argument("--drag-reading", type=int, default=2, choices=(1, 2),
                     help="1: solid force over fluid neighbours with the interpolated pressure; "
                          "2: Eq. tvf-momentum_solid as printed (every neighbour, with p_avg)")
-    ap.add_argument("--problem", default=None, choices=("pulse2d", "ramp", "vortex"),
+    ap.add_argument("--problem", default=None, choices=("pulse2d", "ramp", "vortex", "bump1d"),
                     help="an outlet test problem of Sec. 4 instead of the cylinder: L2 errors "
                          "at the probe for every outlet against the long domain")
     a = ap.parse_args()
+    if a.problem == "bump1d":
+        print(json.dumps(pressure_bump_errors(precision=a.precision)))
+        return
     if a.problem:
         print(json.dumps(outlet_problem_errors(a.problem, precision=a.precision)))
         return
