@@ -392,6 +392,7 @@ struct TileHdr {
     int cstart[3][CT_NV + 1];  // shared index of each staged cell's first particle
     int gstart[3][CT_NV];      // global index of that particle (-1: no such cell)
     int H, i0, ni;
+    uint8_t cell[CT_HMAX];     // staged cell (r CT_NV + v) of each staged particle
 };
 
 // Warp 0 builds the header: lane l takes staged cells l and l + 32 (cell index r CT_NV + v),
@@ -458,6 +459,12 @@ __device__ __forceinline__ void tile_setup(const Dev &d, int cx0, int cy, TileHd
                                 : __shfl_sync(0xffffffffu, a1, lo_cell - 32);
     const int last = 3 * CT_NV - 1;
     const int H = __shfl_sync(0xffffffffu, last < 32 ? i0s : i1s, last & 31);
+    if (H <= CT_HMAX) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (cells[h] < 3 * CT_NV)
+                for (int t = incl[h] - cnt[h]; t < incl[h]; ++t) th.cell[t] = (uint8_t)cells[h];
+    }
     if (lane == 0) {
         th.H = H;
         th.i0 = i0;
@@ -467,10 +474,10 @@ __device__ __forceinline__ void tile_setup(const Dev &d, int cx0, int cy, TileHd
 
 // Stage positions relative to the tile origin (lower-left corner of cell (cx0, cy)):
 // x = (x - cell x0) + (v - 1) sx, y likewise.  The H staged particles are taken flat (staged
-// index t -> its row by the row starts, its cell v by a binary search of the row's cell
-// starts, then its global index), SB of them per thread at a time with all their loads
-// issued before the first store: a warp keeps SB x (loads per particle) requests in flight
-// with every lane busy, where one warp per cell kept ~13 lanes and one cell's loads.
+// index t -> its cell from the header's table, then its global index), SB of them per thread
+// at a time with all their loads issued before the first store: a warp keeps SB x (loads
+// per particle) requests in flight with every lane busy, where one warp per cell kept ~13
+// lanes and one cell's loads.
 // load(j) fetches the pass's fields of particle j, store(t, fields, P_j, v) writes them (v:
 // the staged cell's column, 0 .. CT_NV - 1).
 template <int SB, class Load, class Store>
@@ -489,13 +496,7 @@ __device__ __forceinline__ void tile_stage(const Dev &d, const TileHdr &th, floa
             const int t = base + u * blockDim.x;
             jj[u] = -1;
             if (t < H) {
-                const int r = (t >= th.cstart[1][0]) + (t >= th.cstart[2][0]);
-                // the last cell of the row starting at or before t holds t (cell starts
-                // do not decrease; empty cells after it start past t)
-                int v = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (v + step < CT_NV && th.cstart[r][v + step] <= t) v += step;
+                const int cell = th.cell[t], r = cell / CT_NV, v = cell - r * CT_NV;
                 const int j = th.gstart[r][v] + (t - th.cstart[r][v]);
                 jj[u] = j;
                 vv[u] = v;
@@ -561,8 +562,10 @@ __device__ __forceinline__ Win windows(const Dev &d, const TileHdr &th, const fl
             continue;
         }
         const float reach = sqrtf(reach2) + mrg;
-        const int lo = first_above(spos, a, b, pi.x - reach);
-        const int hi = first_above(spos, lo, b, pi.x + reach);
+        // the window starts in cell vi - 1 or vi (or at the start of vi + 1 when those hold
+        // nothing within reach) and ends after cell vi - 1: the cells are at least 3h wide
+        const int lo = first_above(spos, a, th.cstart[r][vi + 1], pi.x - reach);
+        const int hi = first_above(spos, max(lo, th.cstart[r][vi]), b, pi.x + reach);
         w.lo[r] = lo;
         w.n[r] = hi - lo;
     }
