@@ -936,7 +936,7 @@ def test_mean_drag_autograd_function(method):
         _, g, _ = gradient.drag_gradient_adjoint(c, a, 40, 10)
     np.testing.assert_allclose(at.grad.numpy(), g, rtol=1e-12, atol=0)
     L0, _ = gradient.drag_loss(c, a, 40)
-    assert float(L) == pytest.approx(L0, rel=1e-12)
+    assert float(L.detach()) == pytest.approx(L0, rel=1e-12)
 
 
 @pytest.mark.gpu
