@@ -341,7 +341,7 @@ def run_reference(args, rank, world, dist):
         return
     case = cases.cylinder(dx=args.dx)
     k = max(1, min(args.steps, args.cpu_steps))
-    w = min(args.warmup, 1)
+    w = min(args.warmup, 3)  # an oracle step of the workload takes ~0.5 s on 16 cores
     import oracle
     sim = oracle.OracleSim(case, neighbor_mode=1)
     if w:
