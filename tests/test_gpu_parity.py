@@ -877,6 +877,33 @@ def _grad_case():
 
 
 @pytest.mark.gpu
+def test_event_log_through_the_adjoint_and_the_tangent_model():
+    """The forward steps of edac_adjoint_run are logged once (its recomputations rewrite the
+    same records), and the tangent model's steps like plain steps: both logs equal the one of
+    40 plain fp64 steps of the same case."""
+    from paper_1907_04034_gb300 import gradient
+
+    c, a = _grad_case()
+    c = gradient._with_modes(c, a)
+    logs = {}
+    for how in ("plain", "adjoint", "tangent"):
+        s = binding.Solver(c, precision="fp64", use_graphs=False, max_history=64)
+        s.events_enable(20000)
+        if how == "plain":
+            s.step(40)
+        elif how == "adjoint":
+            s.adjoint(40, 10, w_fx=np.full(40, 1.0))
+        else:
+            s.tangent_enable()
+            s.step_tangent(40)
+        logs[how] = s.events()
+        s.close()
+    assert len(logs["plain"]["id"]) > 0
+    for how in ("adjoint", "tangent"):
+        _assert_same_events(logs[how], logs["plain"])
+
+
+@pytest.mark.gpu
 def test_tangent_gradient_matches_central_differences():
     """dL/da of the mean drag over 40 steps from the tangent-linear model against central
     differences of fp64 runs (eps = 1e-6) that took the same recycling events: agreement to
