@@ -709,11 +709,11 @@ edac_status edac_read_state(edac_ctx *ctx, int cap, uint64_t *h_id, uint8_t *h_t
             case EDAC_F_M: src[f] = d.m; break;
             case EDAC_F_RHO: src[f] = d.rho; break;
             case EDAC_F_VOL: src[f] = d.vol; break;
-            case EDAC_F_AU: src[f] = d.au; break;
-            case EDAC_F_AV: src[f] = d.av; break;
-            case EDAC_F_AP: src[f] = d.ap; break;
-            case EDAC_F_ABU: src[f] = d.abu; break;
-            case EDAC_F_ABV: src[f] = d.abv; break;
+            case EDAC_F_AU: src[f] = d.au; kind[f] = d.mixed ? 3 : 0; break;
+            case EDAC_F_AV: src[f] = d.av; kind[f] = d.mixed ? 3 : 0; break;
+            case EDAC_F_AP: src[f] = d.ap; kind[f] = d.mixed ? 3 : 0; break;
+            case EDAC_F_ABU: src[f] = d.abu; kind[f] = d.mixed ? 3 : 0; break;
+            case EDAC_F_ABV: src[f] = d.abv; kind[f] = d.mixed ? 3 : 0; break;
             case EDAC_F_FX: src[f] = d.fx; break;
             case EDAC_F_FY: src[f] = d.fy; break;
             case EDAC_F_UBAR: src[f] = d.ubar; break;

@@ -319,15 +319,22 @@ __device__ __forceinline__ void stage(const Dev &d, double tau, int bid, int nbl
             } else {
                 x0 = d.x0[s]; y0 = d.y0[s]; u0 = d.u0[s]; v0 = d.v0[s]; p0 = d.p0[s];
             }
-            const double un = u0 + tau * d.au[s];
-            const double vn = v0 + tau * d.av[s];
-            const double utn = un + tau * d.abu[s];
-            const double vtn = vn + tau * d.abv[s];
+            double au, av, ap, abu, abv;
+            if (MIXED) {
+                au = f2d(rate_f(d.au)[s]); av = f2d(rate_f(d.av)[s]); ap = f2d(rate_f(d.ap)[s]);
+                abu = f2d(rate_f(d.abu)[s]); abv = f2d(rate_f(d.abv)[s]);
+            } else {
+                au = d.au[s]; av = d.av[s]; ap = d.ap[s]; abu = d.abu[s]; abv = d.abv[s];
+            }
+            const double un = u0 + tau * au;
+            const double vn = v0 + tau * av;
+            const double utn = un + tau * abu;
+            const double vtn = vn + tau * abv;
             double xn = x0 + tau * utn;
             double yn = y0 + tau * vtn;
             if (g.px) { if (xn >= g.x_max) xn -= g.Lx; else if (xn < g.x_min) xn += g.Lx; }
             if (g.py) { if (yn >= g.y_max) yn -= g.Ly; else if (yn < g.y_min) yn += g.Ly; }
-            const double pn = p0 + tau * d.ap[s];
+            const double pn = p0 + tau * ap;
             d.u[s] = un; d.v[s] = vn; d.ut[s] = utn; d.vt[s] = vtn;
             d.x[s] = xn; d.y[s] = yn; d.p[s] = pn;
             if (COUNT) count_slot(d, s, xn, yn);
@@ -391,6 +398,16 @@ __device__ __forceinline__ void ring_fill(const Dev &d, int s)
     }
     d.rpos[s] = 0;
     d.ubar[s] = u; d.vbar[s] = v; d.pbar[s] = p; d.J2[s] = 0.0;
+}
+
+// Rates of slot s set to zero, in the path's storage (fp32 on the mixed path).
+__device__ __forceinline__ void zero_rates(const Dev &d, int s)
+{
+    if (d.mixed) {
+        rate_f(d.au)[s] = rate_f(d.av)[s] = rate_f(d.ap)[s] = rate_f(d.abu)[s] = rate_f(d.abv)[s] = 0.0f;
+    } else {
+        d.au[s] = d.av[s] = d.ap[s] = d.abu[s] = d.abv[s] = 0.0;
+    }
 }
 
 // Transitions of the end of Sec. 3.4, taken once per step after the outlet update:
@@ -540,7 +557,7 @@ __device__ __forceinline__ void end_step(const Dev &d, double *scratch_m)
         d.id[s] = id0 + (unsigned long long)r;
         if (logged)
             d.evlog[ev0 + n_del + n_out + r] = EventRec{id0 + (unsigned long long)r, d.ev_spawn_key[i], stepno, EV_SPAWN};
-        d.au[s] = d.av[s] = d.ap[s] = d.abu[s] = d.abv[s] = 0.0;
+        zero_rates(d, s);
         d.fx[s] = d.fy[s] = 0.0;
         d.rho[s] = d.vol[s] = 0.0;
         d.nnb[s] = 0;
@@ -588,7 +605,7 @@ __global__ void k_init(Dev d)
         d.J2p[s] = 0.0;
         d.redp[s] = 0;
         d.advp[s] = d.u[s];
-        d.au[s] = d.av[s] = d.ap[s] = d.abu[s] = d.abv[s] = 0.0;
+        zero_rates(d, s);
         d.fx[s] = d.fy[s] = 0.0;
         d.x0[s] = d.x[s]; d.y0[s] = d.y[s]; d.u0[s] = d.u[s]; d.v0[s] = d.v[s]; d.p0[s] = d.p[s];
     }
@@ -792,14 +809,15 @@ __global__ void k_free_stack(Dev d, int n)
 }
 
 // out[r] = src[live[r]] for the read-back in id order; kind 0: src is double, 1: int,
-// 2: byte (integer and byte fields are widened to double).
+// 2: byte, 3: float (integer, byte and float fields are widened to double).
 __global__ void k_permute(const void *src, int kind, const int *live, int n, double *out)
 {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const int s = live[r];
         out[r] = kind == 0 ? static_cast<const double *>(src)[s]
-                           : (kind == 1 ? (double)static_cast<const int *>(src)[s]
-                                        : (double)static_cast<const uint8_t *>(src)[s]);
+                 : kind == 1 ? (double)static_cast<const int *>(src)[s]
+                 : kind == 2 ? (double)static_cast<const uint8_t *>(src)[s]
+                             : (double)static_cast<const float *>(src)[s];
     }
 }
 

@@ -108,6 +108,8 @@ struct Dev {
     // master particle state, slot-indexed [cap]
     double *x, *y, *u, *v, *ut, *vt, *p, *m;
     double *x0, *y0, *u0, *v0, *p0;
+    // rates: fp64 on the fp64 path; on the mixed path (fp32 pair sums) au, av, ap, abu, abv
+    // hold fp32 values in the first half of each array (rate_f), half the bytes per step
     double *au, *av, *ap, *abu, *abv, *fx, *fy, *rho, *vol;
     int *nnb;
     uint8_t *tag;
@@ -158,6 +160,9 @@ struct Dev {
     double *probe_part;  // [PROBE_BLK][PROBE_MAX][8] per-block probe sums
     double *probe_out;   // [PROBE_MAX][4] probe values
 };
+
+// The mixed path's fp32 view of a rate array (au, av, ap, abu, abv).
+__host__ __device__ __forceinline__ float *rate_f(double *a) { return reinterpret_cast<float *>(a); }
 
 // Probe points (by value into the probe kernels).
 constexpr int PROBE_MAX = 8;

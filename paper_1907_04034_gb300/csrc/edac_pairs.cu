@@ -893,12 +893,12 @@ __device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th,
         d.fy[s] = f2d(fmaf(corr, G1, sy));
     } else {
         const float mi_inv = 1.0f / mk;
-        d.au[s] = f2d(fmaf(fmaf(corr, G0, sx), mi_inv, ph.gxf));
-        d.av[s] = f2d(fmaf(fmaf(corr, G1, sy), mi_inv, ph.gyf));
-        d.ap[s] = f2d(f.ap_hl.x + f.ap_hl.y);
+        rate_f(d.au)[s] = fmaf(fmaf(corr, G0, sx), mi_inv, ph.gxf);
+        rate_f(d.av)[s] = fmaf(fmaf(corr, G1, sy), mi_inv, ph.gyf);
+        rate_f(d.ap)[s] = f.ap_hl.x + f.ap_hl.y;
         const float pbm = -ph.pbf * mi_inv;
-        d.abu[s] = f2d(pbm * G0);
-        d.abv[s] = f2d(pbm * G1);
+        rate_f(d.abu)[s] = pbm * G0;
+        rate_f(d.abv)[s] = pbm * G1;
     }
 }
 
