@@ -726,29 +726,45 @@ __device__ __forceinline__ void windows_tested(const Dev &d, const float2 *spos,
     }
 }
 
-// Run body(t) over the set bits of a window mask (shared indices t): each row window's word
-// in two 32-bit halves, highest bit first (one leading-zero count and one exclusive-or per
-// neighbour), with fold() after each row, where the warp's lanes have reconverged.  Against a
-// single loop over all three words with a fold every 16 terms this issues 10% fewer
-// instructions in pass B (3% less time).
+// Run body(t) over the set bits of a window mask (shared indices t), with one leading-zero
+// count and one exclusive-or per neighbour on 32-bit words, highest bit first.  The particle's
+// own row first, its two halves one after the other, then a fold; then the rows below and
+// above in one walk, the next word taken when one runs out, with a fold every 16 terms and at
+// the end (where the warp's lanes have reconverged).  The own row's neighbour count varies
+// little between the lanes of a warp; the rows below and above vary with the particle's
+// height in its cell, in opposite directions, so their sum varies little too: walking those
+// two rows separately left 30% of the lanes idle.  (Pass B at D/100: 0.252 -> 0.221 ms.)
 template <class Body, class Fold>
 __device__ __forceinline__ void for_wmask(const WMask &m, Body &&body, Fold &&fold)
 {
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            unsigned w = (unsigned)(m.m[r] >> (32 * h));
-            const int base = m.lo[r] + 32 * h;
+    for (int h = 0; h < 2; ++h) {
+        unsigned w = (unsigned)(m.m[1] >> (32 * h));
+        const int base = m.lo[1] + 32 * h;
 #pragma unroll 1
-            while (w) {
-                const int b = 31 - __clz(w);
-                w ^= 1u << b;
-                body(base + b);
-            }
+        while (w) {
+            const int b = 31 - __clz(w);
+            w ^= 1u << b;
+            body(base + b);
         }
-        fold();
     }
+    fold();
+    unsigned w0 = (unsigned)m.m[0], w1 = (unsigned)(m.m[0] >> 32), w2 = (unsigned)m.m[2],
+             w3 = (unsigned)(m.m[2] >> 32);
+    int b0 = m.lo[0], b1 = m.lo[0] + 32, b2 = m.lo[2], b3 = m.lo[2] + 32;
+    const int n = __popcll(m.m[0]) + __popcll(m.m[2]);
+#pragma unroll 1
+    for (int it = 0; it < n; ++it) {
+        while (w0 == 0u) {
+            w0 = w1; w1 = w2; w2 = w3; w3 = 0u;
+            b0 = b1; b1 = b2; b2 = b3;
+        }
+        const int b = 31 - __clz(w0);
+        w0 ^= 1u << b;
+        body(b0 + b);
+        if ((it & 15) == 15) fold();
+    }
+    fold();
 }
 
 __device__ __forceinline__ void pass_a_tiled(const Dev &d, int bid)
