@@ -27,8 +27,9 @@ static_assert(edac::OUT_HYBRID == EDAC_OUTLET_HYBRID && edac::OUT_DONOTHING == E
 static_assert(edac::EV_DELETE == EDAC_EVENT_DELETE && edac::EV_TO_OUTLET == EDAC_EVENT_TO_OUTLET &&
                   edac::EV_SPAWN == EDAC_EVENT_SPAWN,
               "event kinds of the header and the kernels agree");
-static_assert(edac::FLUID == EDAC_FLUID && edac::INLET == EDAC_INLET && edac::OUTLET == EDAC_OUTLET &&
-                  edac::WALL == EDAC_WALL && edac::SLIPWALL == EDAC_SLIPWALL,
+static_assert((int)edac::FLUID == (int)EDAC_FLUID && (int)edac::INLET == (int)EDAC_INLET &&
+                  (int)edac::OUTLET == (int)EDAC_OUTLET && (int)edac::WALL == (int)EDAC_WALL &&
+                  (int)edac::SLIPWALL == (int)EDAC_SLIPWALL,
               "particle tags of the header and the kernels agree");
 
 using namespace edac;
