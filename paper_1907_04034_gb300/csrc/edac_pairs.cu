@@ -395,6 +395,13 @@ struct TileHdr {
     uint8_t cell[CT_HMAX];     // staged cell (r CT_NV + v) of each staged particle
 };
 
+// Global index of staged particle t (tiles that fit).
+__device__ __forceinline__ int staged_j(const TileHdr &th, int t)
+{
+    const int c = th.cell[t], r = c / CT_NV, v = c - r * CT_NV;
+    return th.gstart[r][v] + (t - th.cstart[r][v]);
+}
+
 // Warp 0 builds the header: lane l takes staged cells l and l + 32 (cell index r CT_NV + v),
 // and a warp scan of the cell counts gives the shared-memory offsets.
 __device__ __forceinline__ void tile_cell(const Dev &d, int cx0, int cy, int txe, int cell, int &a,
@@ -481,7 +488,7 @@ __device__ __forceinline__ void tile_setup(const Dev &d, int cx0, int cy, TileHd
 // load(j) fetches the pass's fields of particle j, store(t, fields, P_j, v) writes them (v:
 // the staged cell's column, 0 .. CT_NV - 1).
 template <int SB, class Load, class Store>
-__device__ __forceinline__ void tile_stage(const Dev &d, const TileHdr &th, float2 *spos, int *sgj,
+__device__ __forceinline__ void tile_stage(const Dev &d, const TileHdr &th, float2 *spos,
                                            Load &&load, Store &&store)
 {
     using T = decltype(load(0));
@@ -510,7 +517,6 @@ __device__ __forceinline__ void tile_stage(const Dev &d, const TileHdr &th, floa
             const int t = base + u * blockDim.x;
             if (jj[u] >= 0) {
                 spos[t] = make_float2(pp[u].x + oo[u].x, pp[u].y + oo[u].y);
-                sgj[t] = jj[u];
                 store(t, ff[u], pp[u], vv[u]);
             }
         }
@@ -646,7 +652,7 @@ __device__ __forceinline__ void global_neighbors(const Dev &d, int k, const floa
 // not compiled to predicated fp64 work on every candidate).  The sums are folded into the
 // compensated accumulators once per row.
 __device__ __forceinline__ WMask pass_a_windows(const Dev &d, int k, const float2 *spos,
-                                                const float *smass, const int *sgj, const Win &wn,
+                                                const float *smass, const TileHdr &th, const Win &wn,
                                                 float2 pi, MixA &f)
 {
     const float hi2 = d.g.rc2_hi, lo2 = d.g.rc2_lo, inv_h = f.inv_h;
@@ -690,7 +696,7 @@ __device__ __forceinline__ WMask pass_a_windows(const Dev &d, int k, const float
             while (bw) {
                 const int b = __ffsll((long long)bw) - 1;
                 bw &= bw - 1ull;
-                const double2 xy = d.XY[sgj[wn.lo[r] + b]];
+                const double2 xy = d.XY[staged_j(th, wn.lo[r] + b)];
                 double ex, ey;
                 if (!(exact_r2(d.g, q.x, q.y, xy.x, xy.y, ex, ey) < d.g.rc2)) wm.m[r] &= ~(1ull << b);
             }
@@ -703,7 +709,7 @@ __device__ __forceinline__ WMask pass_a_windows(const Dev &d, int k, const float
 // The candidates of the windows with the membership test (windows over WMAX candidates):
 // body(t) over the neighbours, fold() after each row.
 template <class Body, class Fold>
-__device__ __forceinline__ void windows_tested(const Dev &d, const float2 *spos, const int *sgj,
+__device__ __forceinline__ void windows_tested(const Dev &d, const float2 *spos, const TileHdr &th,
                                                const Win &wn, float2 pi, double qx, double qy,
                                                Body &&body, Fold &&fold)
 {
@@ -716,7 +722,7 @@ __device__ __forceinline__ void windows_tested(const Dev &d, const float2 *spos,
             const float r2 = fmaf(dd.x, dd.x, dd.y * dd.y);
             if (r2 >= d.g.rc2_hi) continue;
             if (r2 > d.g.rc2_lo) {
-                const double2 xj = d.XY[sgj[t]];
+                const double2 xj = d.XY[staged_j(th, t)];
                 double ex, ey;
                 if (!(exact_r2(d.g, qx, qy, xj.x, xj.y, ex, ey) < d.g.rc2)) continue;
             }
@@ -772,19 +778,14 @@ __device__ __forceinline__ void pass_a_tiled(const Dev &d, int bid)
     __shared__ TileHdr th;
     __shared__ float2 spos[CT_HMAX];
     __shared__ float smass[CT_HMAX];
-    __shared__ int sgj[CT_HMAX];
-    __shared__ uint8_t scell[CT_HMAX];
     int cx0, cy;
     if (!tile_of_block(d, bid, cx0, cy)) return;
     if (threadIdx.x < 32) tile_setup(d, cx0, cy, th);
     __syncthreads();
     const bool fits = th.H <= CT_HMAX;
     if (fits)
-        tile_stage<4>(d, th, spos, sgj, [](int) { return 0; },
-                      [&](int t, int, const float4 &pj, int v) {
-                          smass[t] = pj.z;
-                          scell[t] = (uint8_t)v;
-                      });
+        tile_stage<4>(d, th, spos, [](int) { return 0; },
+                      [&](int t, int, const float4 &pj, int) { smass[t] = pj.z; });
     __syncthreads();
     const float a2 = d.ph.a2f;
     for (int ii = threadIdx.x; ii < th.ni; ii += blockDim.x) {
@@ -798,15 +799,15 @@ __device__ __forceinline__ void pass_a_tiled(const Dev &d, int bid)
         if (fits) {
             const int ti = th.cstart[1][1] + ii;
             mk = smass[ti];
-            const int vi = scell[ti];
+            const int vi = th.cell[ti] - CT_NV;  // the own row's cells are row 1
             const float2 pi = spos[ti];
             const Win wn = windows(d, th, spos, vi, pi);
             if (wn.n[0] <= WMAX && wn.n[1] <= WMAX && wn.n[2] <= WMAX) {
                 // the neighbour mask over the windows (also pass B's input) and the sums
-                store_wmask(d.nbm, k, pass_a_windows(d, k, spos, smass, sgj, wn, pi, f));
+                store_wmask(d.nbm, k, pass_a_windows(d, k, spos, smass, th, wn, pi, f));
             } else {
                 const double2 xy = d.XY[k];
-                windows_tested(d, spos, sgj, wn, pi, xy.x, xy.y,
+                windows_tested(d, spos, th, wn, pi, xy.x, xy.y,
                                [&](int t) {
                                    const float2 pj = spos[t];
                                    f.add(__fadd2_rn(pi, f2(-pj.x, -pj.y)), smass[t]);
@@ -845,7 +846,7 @@ __global__ void __launch_bounds__(CT_TPB) k_pass_a_tiled_b(BatchGrid bg)
 template <bool SOLID>
 __device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th, bool fits, int cy,
                                                 int cx0, int ii, const float2 *spos, const float4 *sq,
-                                                const float4 *sb, const uint8_t *stg, const int *sgj)
+                                                const float4 *sb, const uint8_t *stg)
 {
     const Phys &ph = d.ph;
     const int k = th.i0 + ii;
@@ -881,7 +882,7 @@ __device__ __forceinline__ void pass_b_particle(const Dev &d, const TileHdr &th,
             const double2 xy = d.XY[k];
             const int vi = d.cellk[k] - cy * d.g.nx - cx0 + 1;
             const Win wn = windows(d, th, spos, vi, pi);
-            windows_tested(d, spos, sgj, wn, pi, xy.x, xy.y,
+            windows_tested(d, spos, th, wn, pi, xy.x, xy.y,
                            [&](int tj) {
                                if (tj != ti) body(tj);
                            },
@@ -927,7 +928,6 @@ __device__ __forceinline__ void pass_b_tiled(const Dev &d, int bid)
     __shared__ float4 sq[CT_HMAX];
     __shared__ float4 sb[CT_HMAX];
     __shared__ uint8_t stg[CT_HMAX];
-    __shared__ int sgj[CT_HMAX];
     const Phys &ph = d.ph;
     int cx0, cy;
     if (!tile_of_block(d, bid, cx0, cy)) return;
@@ -940,7 +940,7 @@ __device__ __forceinline__ void pass_b_tiled(const Dev &d, int bid)
     };
     if (fits)
         tile_stage<PB_SB>(
-            d, th, spos, sgj, [&](int j) { return Fields{d.Qf[j], d.Bf[j], d.stag[j]}; },
+            d, th, spos, [&](int j) { return Fields{d.Qf[j], d.Bf[j], d.stag[j]}; },
             [&](int t, const Fields &f, const float4 &, int) {
                 sq[t] = f.q;
                 sb[t] = f.b;
@@ -950,9 +950,9 @@ __device__ __forceinline__ void pass_b_tiled(const Dev &d, int bid)
     for (int ii = threadIdx.x; ii < th.ni; ii += blockDim.x) {
         const int t = (fits ? stg[th.cstart[1][1] + ii] : d.stag[th.i0 + ii]) & 0x7f;
         if (t == FLUID || t == INLET)
-            pass_b_particle<false>(d, th, fits, cy, cx0, ii, spos, sq, sb, stg, sgj);
+            pass_b_particle<false>(d, th, fits, cy, cx0, ii, spos, sq, sb, stg);
         else if (drag_mode(ph, t))
-            pass_b_particle<true>(d, th, fits, cy, cx0, ii, spos, sq, sb, stg, sgj);
+            pass_b_particle<true>(d, th, fits, cy, cx0, ii, spos, sq, sb, stg);
     }
 }
 
