@@ -747,7 +747,7 @@ __device__ __forceinline__ void for_wmask(const WMask &m, Body &&body, Fold &&fo
     for (int h = 0; h < 2; ++h) {
         unsigned w = (unsigned)(m.m[1] >> (32 * h));
         const int base = m.lo[1] + 32 * h;
-#pragma unroll 1
+#pragma unroll 2
         while (w) {
             const int b = 31 - __clz(w);
             w ^= 1u << b;
@@ -759,7 +759,7 @@ __device__ __forceinline__ void for_wmask(const WMask &m, Body &&body, Fold &&fo
              w3 = (unsigned)(m.m[2] >> 32);
     int b0 = m.lo[0], b1 = m.lo[0] + 32, b2 = m.lo[2], b3 = m.lo[2] + 32;
     const int n = __popcll(m.m[0]) + __popcll(m.m[2]);
-#pragma unroll 1
+#pragma unroll 2
     for (int it = 0; it < n; ++it) {
         while (w0 == 0u) {
             w0 = w1; w1 = w2; w2 = w3; w3 = 0u;
