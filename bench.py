@@ -40,7 +40,7 @@ FLOPS_PER_PAIR_B = 90
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the pair kernels,
 # measured with ncu on the 1.51M-particle workload itself.
-TRAFFIC = {"pass_a": 109.6e6, "pass_b": 148.6e6}
+TRAFFIC = {"pass_a": 109.4e6, "pass_b": 148.6e6}
 
 
 def parse():
