@@ -378,7 +378,8 @@ struct MixB {
 // binary searches).  Pass A tests the windows' candidates, sums its pair terms in the same
 // loop and records the neighbours as a 64-bit mask per row window; pass B iterates the set
 // bits of those masks instead of repeating the membership test.  Compensated sums are
-// folded once per row.  A tile whose halo exceeds CT_HMAX particles is processed from global
+// folded once per row window in pass A and as for_wmask says in pass B.  A tile whose halo
+// exceeds CT_HMAX particles is processed from global
 // memory instead (same membership test, same pair arithmetic), and a particle with a window
 // of more than 64 candidates repeats the test in pass B.
 constexpr int CT_TX = 16;         // most cells of a tile (default 11: ~143 particles at 13 a cell)
