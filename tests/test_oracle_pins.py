@@ -865,6 +865,42 @@ def test_slip_wall_keeps_tangential_flow_and_no_slip_wall_brakes_it():
 
 
 # ----------------------------------------- A-term, blue rule, time window, integrator order
+def test_pressure_bump_splits_into_waves_at_the_sound_speed():
+    """The 1D pressure bump of Sec. 4.1 (Eq. pressurebump) splits into two acoustic waves that,
+    in the fluid moving at U, travel at -c and +c (the EDAC pressure equation with the
+    momentum equation is the wave equation with speed c for small perturbations), each
+    carrying about half the depth; the pattern stays symmetric about the advected centre.
+    A wrong factor c^2 in dp/dt or a wrong sign of the pressure gradient fails."""
+    c = cases.pressure_bump(outlet=0)
+    o = oracle.OracleSim(c, neighbor_mode=1)
+    p = c.params
+    n = int(round(0.03 / p.dt))
+    o.step(n)
+    t = n * p.dt
+    f = o.fields(("x", "p", "tag"))
+    fl = f["tag"] == FLUID
+    dx = p.dx
+    nb = int(round(1.0 / dx))
+    b = np.minimum((f["x"][fl] / dx).astype(int), nb - 1)
+    prof = np.bincount(b, weights=f["p"][fl], minlength=nb) / np.maximum(np.bincount(b, minlength=nb), 1)
+    xs = (np.arange(nb) + 0.5) * dx
+    dev = (prof - 1e-3) / 0.2e-3  # in units of the bump's depth
+    centre = 0.5 + p.U * t
+    left, right = xs < centre, xs >= centre
+    xl = xs[left][np.argmin(dev[left])]
+    xr = xs[right][np.argmin(dev[right])]
+    # wave speeds relative to the fluid within 4% of c
+    assert abs((centre - xl) / t - p.cs) < 0.04 * p.cs, (xl, xr, t)
+    assert abs((xr - centre) / t - p.cs) < 0.04 * p.cs, (xl, xr, t)
+    # symmetric about the advected centre, each wave about half the depth
+    assert abs((centre - xl) - (xr - centre)) <= 1.01 * dx
+    dl, dr = dev[left].min(), dev[right].min()
+    assert abs(dl - dr) < 0.02 * abs(dl)
+    assert -0.55 < dl < -0.35 and -0.55 < dr < -0.35
+    # and the centre has relaxed toward the undisturbed pressure
+    assert abs(dev[np.argmin(abs(xs - centre))]) < 0.1
+
+
 def test_A_term_is_the_divergence_of_rho_u_times_the_shift():
     """The A-term of Eq. tvf-momentum, 1/2 (A_i + A_j).gW with A = rho u (x) (u~ - u), is the
     SPH form of div(A)/rho.  With u = (U, 0), p = 0 and u~ - u = (0, gamma y) that is
