@@ -197,7 +197,8 @@ __device__ __forceinline__ void gather_one(const Dev &d, int s, int k, int c)
     const float rx = d2f(xs - __ldg(d.org_x + cx));
     const float ry = d2f(ys - __ldg(d.org_y + cy));
     const double ms = d.m[s];
-    d.P[k] = make_float4(rx, ry, d2f(ms), 0.0f);
+    // P.w: the fp32 pressure on the mixed path (pass A completes Qf from it), 0 on the other
+    d.P[k] = make_float4(rx, ry, d2f(ms), MIXED ? d2f(d.p[s]) : 0.0f);
     d.XY[k] = make_double2(xs, ys);
     const uint8_t t = d.tag[s];
     d.stag[k] = (uint8_t)(t | ((t == OUTLET && d.redp[s]) ? TAG_REDP : 0));
@@ -206,7 +207,6 @@ __device__ __forceinline__ void gather_one(const Dev &d, int s, int k, int c)
     const double dus = d.ut[s] - us, dvs = d.vt[s] - vs;
     if (MIXED) {
         d.Bf[k] = make_float4(d2f(us), d2f(vs), d2f(dus), d2f(dvs));
-        d.Qf[k] = make_float4(d2f(d.p[s]), 0.0f, 0.0f, 0.0f);
     } else {
         d.UV[k] = make_double2(us, vs);
         d.DUV[k] = make_double2(dus, dvs);

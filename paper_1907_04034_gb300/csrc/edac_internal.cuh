@@ -130,7 +130,7 @@ struct Dev {
     int *scan_part;    // per-block partial sums of the cell-count scan
     int *cellk;        // cell of k
     uint8_t *stag;     // tag of k (| TAG_REDP)
-    float4 *P;         // (x - cell x0, y - cell y0, m, 0) fp32, both paths
+    float4 *P;         // (x - cell x0, y - cell y0, m, p (mixed path) | 0) fp32, both paths
     double2 *XY;       // fp64 position
     double2 *AUX;      // (J2 of fluid | J2 of outlet previous step, outlet advection velocity)
     int *snnb;         // neighbour count N_k

@@ -793,7 +793,7 @@ __device__ __forceinline__ void pass_a_tiled(const Dev &d, int bid)
         const int k = th.i0 + ii;
         // the epilogue's loads first: their latency passes during the pair loop
         const int s = d.order[k];
-        const float pk_p = d.Qf[k].x;
+        const float pk_p = d.P[k].w;
         float mk;
         MixA f;
         f.inv_h = d.ph.inv_hf;
