@@ -1305,7 +1305,9 @@ def test_crossing_and_spawned_particles_take_their_stated_values():
     """End of Sec. 3.4 (as read): a fluid particle entering the hybrid outlet takes its time
     averages (u, v, p) = (u_bar, v_bar, p_bar) and advects with u_bar; a particle spawned at the
     inlet when its parent becomes fluid starts one inlet length behind the parent with the
-    parent's pressure and mass and the prescribed inlet velocity."""
+    parent's pressure and mass and the prescribed inlet velocity, and the parent, now fluid,
+    starts its time window (Eq. timeevg) from its current values.  No particle is left on the
+    wrong side of its line after a step."""
     c = _channel_with_events()
     o = oracle.OracleSim(c, max_events=100000)
     nconv = nspawn = 0
@@ -1315,7 +1317,8 @@ def test_crossing_and_spawned_particles_take_their_stated_values():
     for _ in range(45):
         o.step(1)
         ev = o.events()
-        f = o.fields(("x", "y", "u", "v", "p", "m", "tag", "id", "ubar", "vbar", "pbar", "advp"))
+        f = o.fields(("x", "y", "u", "v", "p", "m", "tag", "id", "ubar", "vbar", "pbar", "advp",
+                      "rpos", "J2"))
         pos = {int(i): k for k, i in enumerate(f["id"])}
         ring = o.a["ring"].reshape(-1, oracle.NAVG_MAX, 3)[:, :navg]
         for i in ev["id"][ev["kind"] == 1]:
@@ -1334,7 +1337,19 @@ def test_crossing_and_spawned_particles_take_their_stated_values():
             assert f["p"][k] == f["p"][q] and f["m"][k] == f["m"][q] and f["y"][k] == f["y"][q]
             assert f["x"][k] == pytest.approx(f["x"][q] - L_in, abs=1e-15)
             assert f["u"][k] == c.params.U and f["v"][k] == 0.0
+            # the parent, fluid from now on, starts its time window from its current values
+            assert f["rpos"][q] == 0 and f["J2"][q] == 0.0
+            for a, b in (("u", "ubar"), ("v", "vbar"), ("p", "pbar")):
+                assert f[a][q] == f[b][q]
+            assert np.all(ring[q, :, 0] == f["u"][q]) and np.all(ring[q, :, 2] == f["p"][q])
             nspawn += 1
+        # every crossing is taken in the step it happens (the lines are x_in, x_out and
+        # x_out + L_out)
+        assert np.all(f["x"][f["tag"] == INLET] < c.params.x_in)
+        fl = f["tag"] == FLUID
+        assert np.all((f["x"][fl] >= c.params.x_in) & (f["x"][fl] < c.params.x_out))
+        L_out = c.params.n_out_layers * c.params.dx
+        assert np.all(f["x"][f["tag"] == OUTLET] < c.params.x_out + L_out)
     assert nconv > 20 and nspawn > 20
     assert spread > 1e-3  # the window's samples differ: its mean is not the crossing value
 
@@ -1373,3 +1388,93 @@ def test_mirror_sums_are_quadratures_with_the_particle_volumes():
     assert np.abs(a[1] - b[1]).max() < 0.1 * gscale
     assert np.abs(a[2] - b[2]).max() < 0.1 * gscale
     assert np.abs(a[0] - b[0]).max() < 0.03 * np.abs(a[0]).max()
+
+
+def test_the_scheme_is_invariant_under_a_change_of_density_scale():
+    """The equations hold in any unit of mass: with rho0, the masses, the pressures and p_b all
+    multiplied by 1000 (the same fluid in other units: p/rho, nu, c and the geometry unchanged),
+    every velocity, position, gate decision and recycling event stays the same and the
+    pressures and densities scale by 1000.  This pins each place a density multiplies a term:
+    the dynamic viscosities of both diffusion terms, rho_i/rho_j, the A-term's densities,
+    the acoustic intensity and its threshold (Eq. acouinten), rho0 c in J2 (Eq.
+    characteristic-vars) and in its inversion (Eq. acou).  The pulse is strong enough for the
+    gate to close near it."""
+    runs = {}
+    for k in (1.0, 1000.0):
+        c = cases.channel(pulse_amp=1.0, jitter=0.05, seed=3)
+        c.params.rho0 *= k
+        c.params.pb *= k
+        c.m = c.m * k
+        c.p = c.p * k
+        o = oracle.OracleSim(c)
+        o.step(25)
+        runs[k] = o.fields(("x", "y", "u", "v", "ut", "vt", "p", "rho", "V", "tag", "id", "rpos",
+                            "ubar", "pbar", "J2", "au", "ap"))
+    a, b = runs[1.0], runs[1000.0]
+    for key in ("tag", "id", "rpos"):
+        assert np.array_equal(a[key], b[key]), key
+    assert len(np.unique(a["rpos"][a["tag"] == FLUID])) > 1  # some rings were gated
+    for key in ("x", "y"):
+        np.testing.assert_allclose(b[key], a[key], rtol=0, atol=1e-13)
+    for key in ("u", "v", "ut", "vt", "ubar", "V", "au"):
+        np.testing.assert_allclose(b[key], a[key], rtol=0, atol=1e-10 * np.abs(a[key]).max())
+    for key in ("p", "rho", "pbar", "J2", "ap"):
+        np.testing.assert_allclose(b[key], 1000.0 * a[key], rtol=0,
+                                   atol=1e-10 * 1000.0 * np.abs(a[key]).max())
+    assert np.abs(a["J2"]).max() > 1e-4
+
+
+def _fluid_row(p0=0.7, dx=0.05):
+    n = 21
+    x = (np.arange(n) - 10) * dx
+    prm = cases.Params(x_min=-2.0, x_max=2.0, y_min=-2.0, y_max=2.0, dx=dx, hdx=1.2, nu=0.01,
+                       cs=10.0, pb=0.0, dt=1e-4, use_pavg=0, wall_drag=(0, 0))
+    c = cases.Case("row", prm, x, np.zeros(n), np.zeros(n), np.zeros(n), np.full(n, p0),
+                   np.full(n, dx * dx), np.full(n, FLUID, dtype=np.uint8),
+                   np.arange(n, dtype=np.uint64), capacity=n + 8)
+    return oracle.OracleSim(c)
+
+
+def test_mirror_without_fluid_or_with_a_singular_system():
+    """Readings of Sec. 3.2's mirror: a point with no fluid in reach gets p = 0 and no gradient;
+    a point whose fluid neighbours lie on one line (the 3x3 system of Eq. matform is
+    singular: no y moments) gets the Shepard value sum p W V / sum W V and no gradient, which
+    for a constant field is that constant."""
+    o = _fluid_row()
+    pk, gx, gy = o.mirror_points(np.array([0.013, 0.0]), np.array([0.0, 1.5]))
+    assert pk[0] == pytest.approx(0.7, rel=1e-14) and gx[0] == 0.0 and gy[0] == 0.0
+    assert pk[1] == 0.0 and gx[1] == 0.0 and gy[1] == 0.0
+
+
+def test_inlet_profile_modes_at_their_special_heights():
+    """Sec. 3's inlet profile u(y) = U + sum_k a_k sin(k pi (y - y0) / H) with y0 = -0.15 and
+    H = 0.8 on the channel's inlet: mode 1 adds a_1 at mid-height y0 + H/2 = 0.25 and
+    a_1 / sqrt(2) at the quarter heights 0.05 and 0.45; mode 2 adds nothing at mid-height,
+    +a_2 at 0.05 and -a_2 at 0.45; v = 0."""
+    for modes, want in (((0.3,), {0.25: 0.3, 0.05: 0.3 / math.sqrt(2), 0.45: 0.3 / math.sqrt(2)}),
+                        ((0.0, 0.2), {0.25: 0.0, 0.05: 0.2, 0.45: -0.2})):
+        c = cases.channel(jitter=0.0, pulse_amp=0.0)
+        c.params.inlet_modes = modes
+        c.params.inlet_y0 = -0.15
+        c.params.inlet_h = 0.8
+        o = oracle.OracleSim(c)
+        o.step(1)
+        f = o.fields(("y", "u", "v", "tag"))
+        inl = f["tag"] == INLET
+        assert np.all(f["v"][inl] == 0.0)
+        for y, du in want.items():
+            at = inl & (np.abs(f["y"] - y) < 1e-9)
+            assert np.count_nonzero(at) >= 3
+            np.testing.assert_allclose(f["u"][at], c.params.U + du, rtol=0, atol=1e-12)
+
+
+def test_ramp_inlet_holds_the_free_stream_after_the_ramp():
+    """Sec. 4.3's ramp u = U min(t / T, 1): after t = T the inlet velocity stays at U."""
+    c = cases.outlet_problem("ramp")
+    T = 5 * c.params.dt
+    c.params.inlet_prm = (T,)
+    o = oracle.OracleSim(c, neighbor_mode=1)
+    o.step(20)
+    f = o.fields(("u", "tag"))
+    assert o.t > 3 * T
+    assert np.all(f["u"][f["tag"] == INLET] == c.params.U)
