@@ -1478,3 +1478,127 @@ def test_ramp_inlet_holds_the_free_stream_after_the_ramp():
     f = o.fields(("u", "tag"))
     assert o.t > 3 * T
     assert np.all(f["u"][f["tag"] == INLET] == c.params.U)
+
+
+def test_new_ids_continue_from_the_largest_id_in_ascending_parent_order():
+    """Recycling hands out ids after the largest id in use, one per spawn, in ascending order of
+    the parents' ids (the canonical order that makes runs comparable); with input ids that
+    are neither contiguous nor in array order, the array order would give another
+    assignment."""
+    c = cases.channel()
+    rng = np.random.default_rng(8)
+    c.id = (10 * rng.permutation(c.n) + 7).astype(np.uint64)
+    nxt = int(c.id.max()) + 1
+    o = oracle.OracleSim(c, max_events=100000)
+    nsp = 0
+    for _ in range(60):
+        o.step(1)
+        ev = o.events()
+        sp = ev["kind"] == 2
+        new, par = ev["id"][sp].astype(np.int64), ev["other"][sp].astype(np.int64)
+        np.testing.assert_array_equal(new, nxt + np.arange(len(new)))
+        assert np.all(np.diff(par) > 0)
+        nxt += len(new)
+        nsp += len(new)
+    assert nsp > 20
+
+
+def test_force_history_is_the_sum_over_the_counted_solids():
+    """The drag/lift record of a step (Sec. 4.6's c_d, c_l) sums fx and fy of the solid
+    particles counted in the drag, as evaluated at the end of the step."""
+    c = cases.cylinder(dx=1.0 / 8.0, Lx=6.0, H=4.0, xc=2.0)
+    o = oracle.OracleSim(c, neighbor_mode=1)
+    o.step(3)
+    h = o.history[-1]
+    f = o.fields(("fx", "fy", "tag"))
+    counted = f["tag"] == WALL  # the cylinder; the slip walls are not counted
+    assert np.abs(f["fy"][counted]).max() > 0.0
+    assert h["fx"] == pytest.approx(f["fx"][counted].sum(), rel=1e-12)
+    assert h["fy"] == pytest.approx(f["fy"][counted].sum(), rel=1e-12, abs=1e-15)
+    assert np.all(f["fx"][f["tag"] == SLIPWALL] == 0.0)
+
+
+def test_rates_are_computed_for_fluid_and_inlet_particles_only():
+    """Eq. tvf-momentum and Eq. p-edac hold for the fluid and for the inlet particles (an inlet
+    particle that becomes fluid starts from the rates computed for it): the inlet particles'
+    rates, with the pressure the mirror gave them, are those they get as fluid particles of
+    the same state.  Outlet and wall particles carry no rates, and a wall's transport
+    velocity is its ghost velocity (no A-term from it)."""
+    c = cases.channel(jitter=0.0, pulse_amp=0.0, n_in=6)
+    c.p[:] = np.where(c.tag == FLUID, 0.1 * (1.0 - c.x), 0.0)
+    o = oracle.OracleSim(c)
+    f = o.fields(("tag", "x", "y", "au", "av", "ap", "u", "v", "p"))
+    inl = f["tag"] == INLET
+    assert np.abs(f["au"][inl]).max() > 0.01 and np.abs(f["ap"][inl]).max() > 0.01
+    as_fluid = cases.channel(jitter=0.0, pulse_amp=0.0, n_in=6)
+    assert np.array_equal(as_fluid.x, f["x"]) and np.array_equal(as_fluid.y, f["y"])
+    as_fluid.tag = np.where(as_fluid.tag == INLET, FLUID, as_fluid.tag).astype(np.uint8)
+    as_fluid.p, as_fluid.u, as_fluid.v = f["p"].copy(), f["u"].copy(), f["v"].copy()
+    g = oracle.OracleSim(as_fluid).fields(("au", "av", "ap"))
+    for key in ("au", "av", "ap"):
+        np.testing.assert_array_equal(g[key][inl], f[key][inl])
+    for t in (OUTLET, WALL, SLIPWALL):
+        sel = f["tag"] == t
+        assert np.all(f["au"][sel] == 0.0) and np.all(f["ap"][sel] == 0.0)
+    cy = cases.poiseuille(n=10)
+    cy.u[:] = np.where(cy.tag == FLUID, 0.4, 0.0)
+    w = oracle.OracleSim(cy).fields(("tag", "u", "v", "ut", "vt"))
+    wl = w["tag"] == WALL
+    assert np.array_equal(w["ut"][wl], w["u"][wl]) and np.array_equal(w["vt"][wl], w["v"][wl])
+    assert np.abs(w["u"][wl]).max() > 0.1
+    sw = cases.poiseuille(n=10)
+    sw.u[:] = np.where(sw.tag == FLUID, 0.4, 0.0)
+    sw.params.wall_drag = (0, 0)
+    ow = oracle.OracleSim(sw).fields(("tag", "au", "ap"))
+    assert np.all(ow["au"][ow["tag"] == WALL] == 0.0)
+
+
+@pytest.mark.parametrize("kind", ["mod_donothing", "characteristic", "mirror"])
+def test_blue_rules_of_the_other_outlets(kind):
+    """Where the Shepard interpolation of the fluid does not reach (Sec. 3.4's blue particles):
+    the modified do-nothing outlet (Sec. 3.1.1) advects a blue particle with the mean previous
+    advection velocity of its previously red neighbours, else with its frozen u average; the
+    characteristic outlet (Sec. 3.3) takes J2 as their mean previous J2 and advects with that
+    mean velocity, else (J2 = 0) with its own u = u_ref; the mirrored outlet (Sec. 3.2) keeps
+    no red flags or J2.  Previous values, flags and frozen averages are planted at random."""
+    c = cases.channel(jitter=0.0, pulse_amp=0.0, n_in=4, n_out=12)
+    c.params.outlet_kind = OUTLET_KINDS[kind]
+    o = oracle.OracleSim(c)
+    n = o.n
+    rng = np.random.default_rng(33)
+    out = o.a["tag"][:n] == OUTLET
+    J2p0 = np.where(out, rng.normal(0.0, 0.02, n), 0.0)
+    adv0 = np.where(out, rng.uniform(0.8, 1.2, n), o.a["advp"][:n])
+    # red flags in the first outlet layers only, so that the deepest blue particles have none
+    front = o.a["x"][:n] < c.params.x_out + 5 * c.params.dx
+    red0 = np.where(out & front, rng.integers(0, 2, n), 0).astype(np.int32)
+    o.a["ubar"][:n] = np.where(out, rng.uniform(0.9, 1.1, n), o.a["ubar"][:n])
+    o.a["J2p"][:n] = J2p0
+    o.a["advp"][:n] = adv0
+    o.a["redp"][:n] = red0
+    o.step(1)
+    f = o.fields(("tag", "u", "J2p", "advp", "redp", "ubar"))
+    out = f["tag"] == OUTLET
+    if kind == "mirror":
+        assert np.all(f["redp"][out] == 0) and np.all(f["J2p"][out] == 0.0)
+        return
+    start, idx = o.neighbors()
+    rho_c = c.params.rho0 * c.params.cs
+    nblue = nnone = 0
+    for k in np.nonzero(out)[0]:
+        nb = idx[start[k]:start[k + 1]]
+        if np.any(f["tag"][nb] == FLUID):
+            continue
+        nblue += 1
+        prev = nb[(f["tag"][nb] == OUTLET) & (red0[nb] == 1)]
+        nnone += len(prev) == 0
+        if kind == "mod_donothing":
+            want = adv0[prev].mean() if len(prev) else f["ubar"][k]
+            assert f["advp"][k] == pytest.approx(want, rel=1e-13)
+        else:
+            J2 = J2p0[prev].mean() if len(prev) else 0.0
+            assert f["J2p"][k] == pytest.approx(J2, rel=1e-13, abs=1e-16)
+            assert f["u"][k] == pytest.approx(c.params.U + J2 / (2 * rho_c), rel=1e-13)
+            want = adv0[prev].mean() if len(prev) else f["u"][k]
+            assert f["advp"][k] == pytest.approx(want, rel=1e-13)
+    assert nblue > 50 and nnone > 5
