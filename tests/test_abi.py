@@ -112,3 +112,72 @@ def test_event_log_record_size_and_argument_checks(lib):
     n = C.c_int(0)
     assert lib.edac_read_events(None, 0, None, None, None, None, C.byref(n), None) == 1
     assert lib.edac_events_enable(None, None, 0) == 1
+
+
+@pytest.fixture
+def host_ctx(lib):
+    """A context made on the host only: edac_create carves the workspace without touching it, so
+    an aligned address that is never dereferenced stands in for device memory."""
+    p = _params()
+    need = C.c_size_t(0)
+    assert lib.edac_workspace_bytes(C.byref(p), C.byref(need)) == 0
+    ctx = C.c_void_p()
+    assert lib.edac_create(C.byref(p), C.c_void_p(1 << 30), need.value, C.byref(ctx)) == 0
+    yield ctx
+    lib.edac_destroy(ctx)
+
+
+EDAC_E_INVALID, EDAC_E_STATE = 1, 6
+
+
+def test_setters_validate_their_arguments_on_the_host(lib, host_ctx):
+    nan = float("nan")
+    modes = (C.c_double * 17)(0.01, -0.02)
+    ok = lib.edac_set_inlet(host_ctx, 0.0, 3, 2, modes, 0.0, 0.5)
+    assert ok == 0
+    for args in ((nan, 3, 2, modes, 0.0, 0.5), (0.0, 0, 2, modes, 0.0, 0.5),
+                 (0.0, 3, 17, modes, 0.0, 0.5), (0.0, 3, 2, None, 0.0, 0.5),
+                 (0.0, 3, 2, modes, 0.0, 0.0), (0.0, 3, -1, modes, 0.0, 0.5)):
+        assert lib.edac_set_inlet(host_ctx, *args) == EDAC_E_INVALID, args
+    assert b"inlet" in lib.edac_last_error(host_ctx)
+    assert lib.edac_set_outlet(host_ctx, 1.0, 5, 0, 6, -1.0) == 0
+    for args in ((1.0, 5, 7, 6, -1.0), (1.0, 5, -1, 6, -1.0), (1.0, 0, 0, 6, -1.0),
+                 (1.0, 5, 0, 0, -1.0), (1.0, 5, 0, 9, -1.0), (nan, 5, 0, 6, -1.0),
+                 (1.0, 5, 0, 6, nan)):
+        assert lib.edac_set_outlet(host_ctx, *args) == EDAC_E_INVALID, args
+    pulse = (C.c_double * 4)(0.1, 0.2, 0.5, 0.01)
+    assert lib.edac_set_inlet_transient(host_ctx, 1, 4, pulse) == 0
+    bad_pulse = (C.c_double * 4)(0.1, 0.5, 0.2, 0.01)  # t1 <= t0
+    ramp0 = (C.c_double * 1)(0.0)
+    for args in ((1, 3, pulse), (1, 4, bad_pulse), (2, 1, ramp0), (2, 1, None), (4, 0, None)):
+        assert lib.edac_set_inlet_transient(host_ctx, *args) == EDAC_E_INVALID, args
+    assert lib.edac_set_inlet_transient(host_ctx, 0, 0, None) == 0
+    assert lib.edac_set_wall(host_ctx, 3, 0, 0.5, 0.0, 2) == 0
+    for args in ((0, 0, 0.0, 0.0, 1), (3, 0, 0.0, 0.0, 3), (4, 1, nan, 0.0, 0), (3, 0, 0.0, 0.0, -1)):
+        assert lib.edac_set_wall(host_ctx, *args) == EDAC_E_INVALID, args
+    assert lib.edac_set_tiling(host_ctx, 8, 128) == 0
+    for args in ((0, 128), (17, 128), (8, 100), (8, 32), (8, 288)):
+        assert lib.edac_set_tiling(host_ctx, *args) == EDAC_E_INVALID, args
+
+
+def test_calls_out_of_order_are_state_errors(lib, host_ctx):
+    n = C.c_int(-1)
+    assert lib.edac_step(host_ctx, 1) == EDAC_E_STATE
+    assert b"edac_set_particles" in lib.edac_last_error(host_ctx)
+    assert lib.edac_evaluate(host_ctx) == EDAC_E_STATE
+    assert lib.edac_get_count(host_ctx, C.byref(n)) == EDAC_E_STATE
+    assert lib.edac_step(host_ctx, -1) == EDAC_E_INVALID
+
+
+def test_derivative_workspaces_are_sized_on_the_host(lib, host_ctx):
+    t = C.c_size_t(0)
+    assert lib.edac_tangent_workspace_bytes(host_ctx, C.byref(t)) == 0 and t.value > 0
+    a = {}
+    for nsteps, k in ((400, 50), (800, 50), (400, 25)):
+        b = C.c_size_t(0)
+        assert lib.edac_adjoint_workspace_bytes(host_ctx, nsteps, k, C.byref(b)) == 0
+        a[nsteps, k] = b.value
+    assert a[800, 50] > a[400, 50] > 0
+    b = C.c_size_t(0)
+    assert lib.edac_adjoint_workspace_bytes(host_ctx, 0, 50, C.byref(b)) == EDAC_E_INVALID
+    assert lib.edac_adjoint_workspace_bytes(host_ctx, 400, 0, C.byref(b)) == EDAC_E_INVALID
