@@ -181,3 +181,18 @@ def test_derivative_workspaces_are_sized_on_the_host(lib, host_ctx):
     b = C.c_size_t(0)
     assert lib.edac_adjoint_workspace_bytes(host_ctx, 0, 50, C.byref(b)) == EDAC_E_INVALID
     assert lib.edac_adjoint_workspace_bytes(host_ctx, 400, 0, C.byref(b)) == EDAC_E_INVALID
+
+
+def test_product_fails_loudly_without_its_library(tmp_path):
+    """No fallback: with the library missing, loading it (and so making a solver) raises."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1907_04034_gb300 import binding\n"
+            "binding.LIB = %r\n"
+            "try:\n    binding.load()\nexcept RuntimeError as e:\n    print('raised:', e)\n"
+            % (os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+               str(tmp_path / "libedac.so")))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert "raised:" in r.stdout and "build()" in r.stdout
