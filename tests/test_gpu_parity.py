@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 from paper_1907_04034_gb300 import binding, cases
-from paper_1907_04034_gb300.cases import FLUID, INLET, OUTLET, WALL, SLIPWALL
+from paper_1907_04034_gb300.cases import FLUID, OUTLET, WALL
 
 TOL = {"fp64": 1e-10, "mixed": 1e-4}
 PRECS = ("fp64", "mixed")
