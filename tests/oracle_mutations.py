@@ -460,6 +460,63 @@ MUTATIONS = {
         ('        S->t = (double)S->nstep * P->dt;',
          '        S->t = (double)(S->nstep - 1) * P->dt;'),
     ],
+    # ---- which tags take part, gate threshold, time levels, ill-conditioned mirror
+    'inlet_mirror_all_tags': [
+        ('            qy[nq] = S->y[i];\n            nq++;\n        }\n    nlist L;\n    build_lists(P, S, nq, qx, qy, 1u << ORC_FLUID, &L);\n#pragma omp parallel for schedule(static)\n    for (int t = 0; t < nq; t++) {\n        int o = who[t];\n        double pk',
+         '            qy[nq] = S->y[i];\n            nq++;\n        }\n    nlist L;\n    build_lists(P, S, nq, qx, qy, 0xFFu, &L);\n#pragma omp parallel for schedule(static)\n    for (int t = 0; t < nq; t++) {\n        int o = who[t];\n        double pk'),
+    ],
+    'walls_see_inlet': [
+        ('        for (int t = L->start[i]; t < L->start[i + 1]; t++) {\n            int j = L->idx[t];\n            if (S->tag[j] != ORC_FLUID) continue;\n            double r = sqrt(sep(P, S->x[i], S->y[i], S->x[j], S->y[j], &dx, &dy));\n            double w = orc_W(r, h);\n            sw += w;\n            sp += S->p[j] * w;',
+         '        for (int t = L->start[i]; t < L->start[i + 1]; t++) {\n            int j = L->idx[t];\n            if (S->tag[j] != ORC_FLUID && S->tag[j] != ORC_OUTLET) continue;\n            double r = sqrt(sep(P, S->x[i], S->y[i], S->x[j], S->y[j], &dx, &dy));\n            double w = orc_W(r, h);\n            sw += w;\n            sp += S->p[j] * w;'),
+    ],
+    'red_by_inlet_too': [
+        ('            if (S->tag[j] == ORC_FLUID) {\n                double r = sqrt(sep(P, S->x[o], S->y[o], S->x[j], S->y[j], &dx, &dy));',
+         '            if (S->tag[j] == ORC_FLUID || S->tag[j] == ORC_WALL) {\n                double r = sqrt(sep(P, S->x[o], S->y[o], S->x[j], S->y[j], &dx, &dy));'),
+    ],
+    'i_thresh_zero_ignored': [
+        ('    if (P->i_thresh >= 0.0) return P->i_thresh;',
+         '    if (P->i_thresh > 0.0) return P->i_thresh;'),
+    ],
+    'ring_for_outlet_too': [
+        ('        if (S->tag[i] != ORC_FLUID) continue;\n        if (P->outlet_kind == ORC_OUT_CHARACTERISTIC) {',
+         '        if (S->tag[i] != ORC_FLUID && S->tag[i] != ORC_OUTLET) continue;\n        if (P->outlet_kind == ORC_OUT_CHARACTERISTIC) {'),
+    ],
+    'no_wrap_y': [
+        ('            S->y[i] = wrap(S->y0[i] + tau * S->vt[i], P->periodic_y, P->y_min, P->y_max);',
+         '            S->y[i] = S->y0[i] + tau * S->vt[i];'),
+    ],
+    'init_advp_zero': [
+        ('        S->advp[i] = S->u[i];\n        if (S->id[i] >= S->next_id)',
+         '        S->advp[i] = 0.0;\n        if (S->id[i] >= S->next_id)'),
+    ],
+    'spawn_velocity_previous_time': [
+        ('        inlet_velocity(P, ny_[k], S->t, &uin, &vin);',
+         '        inlet_velocity(P, ny_[k], S->t - P->dt, &uin, &vin);'),
+    ],
+    'singular_threshold_loose': [
+        ('    int singular = fabs(d) <= 1e-9 * fabs(M[0][0] * M[1][1] * M[2][2]);',
+         '    int singular = fabs(d) <= 1e-1 * fabs(M[0][0] * M[1][1] * M[2][2]);'),
+    ],
+    'inlet_profile_at_current_y': [
+        ('            inlet_velocity(P, S->y0[i], S->t + tau, &uin, &vin);',
+         '            inlet_velocity(P, S->y0[i] + 0.5 * P->dx, S->t + tau, &uin, &vin);'),
+    ],
+    'pass_a_skips_walls': [
+        ('    for (int i = 0; i < S->n; i++) {\n        double sw = 0.0, rho = 0.0, dx, dy;',
+         '    for (int i = 0; i < S->n; i++) {\n        if (is_wall(S->tag[i])) continue;\n        double sw = 0.0, rho = 0.0, dx, dy;'),
+    ],
+    'probe_fluid_and_outlet': [
+        ('            if (S->tag[j] != ORC_FLUID) continue;\n            double r2 = sep(P, qx[t], qy[t], S->x[j], S->y[j], &dx, &dy);',
+         '            if (S->tag[j] != ORC_FLUID && S->tag[j] != ORC_OUTLET) continue;\n            double r2 = sep(P, qx[t], qy[t], S->x[j], S->y[j], &dx, &dy);'),
+    ],
+    'blue_adv_ignores_red_flag': [
+        ('            } else if (S->tag[j] == ORC_OUTLET && S->redp[j]) {',
+         '            } else if (S->tag[j] == ORC_OUTLET) {'),
+    ],
+    'gate_sample_p_only': [
+        ('            rg[3 * k + 0] = S->u[i];\n            rg[3 * k + 1] = S->v[i];\n            rg[3 * k + 2] = S->p[i];\n            S->rpos[i] = (k + 1) % P->n_avg;',
+         '            rg[3 * k + 2] = S->p[i];\n            S->rpos[i] = (k + 1) % P->n_avg;'),
+    ],
 }
 
 # Mistakes with no observable effect: the forces of walls not counted in the drag are zero

@@ -1602,3 +1602,109 @@ def test_blue_rules_of_the_other_outlets(kind):
             want = adv0[prev].mean() if len(prev) else f["u"][k]
             assert f["advp"][k] == pytest.approx(want, rel=1e-13)
     assert nblue > 50 and nnone > 5
+
+
+@pytest.mark.parametrize("other", [INLET, OUTLET, WALL])
+def test_wall_values_come_from_the_fluid_alone(other):
+    """A wall's Shepard projection runs over its fluid neighbours only: a neighbour of another
+    kind, whatever its pressure and velocity, changes nothing."""
+    dx = 0.05
+    h = 1.2 * dx
+    prm = cases.Params(x_min=-1.0, x_max=1.0, y_min=-1.0, y_max=1.0, dx=dx, hdx=1.2, nu=0.01,
+                       cs=10.0, pb=0.0, dt=1e-4, wall_drag=(0, 0), has_inlet=1, x_in=-0.5,
+                       has_outlet=1, x_out=-0.5)
+    c = cases.Case("wall_other", prm, np.array([0.0, 0.5 * h, -0.5 * h]), np.zeros(3),
+                   np.array([0.0, 0.3, 2.0]), np.array([0.0, 0.1, -1.0]),
+                   np.array([0.0, 1.0, 5.0]), np.full(3, dx * dx),
+                   np.array([WALL, FLUID, other], dtype=np.uint8), np.arange(3, dtype=np.uint64),
+                   capacity=8)
+    o = oracle.OracleSim(c)
+    f = o.fields(("p", "u", "v"))
+    assert f["p"][0] == 1.0 and f["u"][0] == -0.3 and f["v"][0] == -0.1
+
+
+def test_outlet_particles_are_red_only_through_fluid_and_keep_their_frozen_averages():
+    """An outlet particle is red when fluid is in reach (Sec. 3.4): a wall in reach does not make
+    it red.  And the outlet's time averages are frozen at the crossing: the outlet particles'
+    u_bar, v_bar, p_bar do not change from step to step while their u and p do."""
+    c = cases.channel(jitter=0.02, n_in=4, n_out=8)
+    c.p[:] = np.where(c.tag == FLUID, c.p + 0.02 * np.sin(7.0 * c.y), c.p)
+    far = (c.tag == OUTLET) & (c.x > c.params.x_out + 6.5 * c.params.dx)
+    c.tag = np.where(far & (c.y < 0.1), WALL, c.tag).astype(np.uint8)  # walls among blue ones
+    c.params.wall_drag = (0, 0)
+    o = oracle.OracleSim(c)
+    o.step(2)
+    f0 = o.fields(("id", "tag", "x", "ubar", "vbar", "pbar", "u", "p", "redp"))
+    start, idx = o.neighbors()
+    walled = 0
+    for k in np.nonzero(f0["tag"] == OUTLET)[0]:
+        nb = idx[start[k]:start[k + 1]]
+        if not np.any(f0["tag"][nb] == FLUID) and np.any(f0["tag"][nb] == WALL):
+            assert f0["redp"][k] == 0
+            walled += 1
+    assert walled > 5
+    o.step(3)
+    f1 = o.fields(("id", "tag", "ubar", "vbar", "pbar", "u", "p"))
+    pos = {int(i): k for k, i in enumerate(f1["id"])}
+    both = [(k, pos[int(i)]) for k, i in enumerate(f0["id"])
+            if f0["tag"][k] == OUTLET and int(i) in pos]
+    assert len(both) > 100
+    a, b = np.array([q[0] for q in both]), np.array([q[1] for q in both])
+    for key in ("ubar", "vbar", "pbar"):
+        assert np.array_equal(f0[key][a], f1[key][b]), key
+    assert np.abs(f0["p"][a] - f1["p"][b]).max() > 1e-6
+
+
+def test_a_zero_intensity_threshold_closes_the_gate_for_any_pressure():
+    """edac_set_outlet's i_thresh >= 0 replaces Eq. acouinten's threshold; 0 admits only samples
+    of exactly zero pressure: every fluid particle of the pulse channel keeps its window."""
+    c = cases.channel()
+    c.params.i_thresh = 0.0
+    o = oracle.OracleSim(c)
+    o.step(1)
+    f = o.fields(("tag", "p", "rpos"))
+    fl = f["tag"] == FLUID
+    assert np.all(f["p"][fl] != 0.0)
+    assert np.all(f["rpos"][fl] == 0)
+
+
+def test_spawned_inlet_particles_take_the_inlet_velocity_at_the_end_of_the_step():
+    """A particle spawned at the end of a step takes the inlet velocity at the new time level
+    t^(n+1): during the ramp of Sec. 4.3, u = U t^(n+1) / T."""
+    c = cases.outlet_problem("ramp")
+    o = oracle.OracleSim(c, neighbor_mode=1, max_events=100000)
+    T = c.params.inlet_prm[0]
+    nsp = 0
+    while nsp < 20 and o.t < 0.9 * T:
+        o.step(1)
+        ev = o.events()
+        f = o.fields(("id", "u"))
+        pos = {int(i): k for k, i in enumerate(f["id"])}
+        for i in ev["id"][ev["kind"] == 2]:
+            assert f["u"][pos[int(i)]] == pytest.approx(c.params.U * o.t / T, rel=1e-13)
+            nsp += 1
+    assert nsp >= 20
+
+
+def test_mirror_solves_ill_conditioned_systems_that_are_not_singular():
+    """The Shepard fallback of the mirror is for singular systems only: with the fluid in two rows
+    at one and two smoothing lengths from the mirror point (a one-sided support: the system
+    of Eq. matform is ill-conditioned, |det M| / |M00 M11 M22| ~ 0.05, but regular), the
+    Taylor solve still returns a linear field's value and gradient exactly."""
+    dx = 0.05
+    h = 1.2 * dx
+    xs = (np.arange(21) - 10) * dx
+    x = np.r_[xs, xs]
+    y = np.r_[np.full(21, h), np.full(21, 2 * h)]
+    n = len(x)
+    p = 0.3 + 2.0 * x - 1.5 * y
+    prm = cases.Params(x_min=-2.0, x_max=2.0, y_min=-2.0, y_max=2.0, dx=dx, hdx=1.2, nu=0.01,
+                       cs=10.0, pb=0.0, dt=1e-4, use_pavg=0, wall_drag=(0, 0))
+    c = cases.Case("two_rows", prm, x, y, np.zeros(n), np.zeros(n), p, np.full(n, dx * dx),
+                   np.full(n, FLUID, dtype=np.uint8), np.arange(n, dtype=np.uint64), capacity=n + 8)
+    o = oracle.OracleSim(c)
+    qx = np.array([0.013, -0.021])
+    pk, gx, gy = o.mirror_points(qx, np.zeros(2))
+    np.testing.assert_allclose(pk, 0.3 + 2.0 * qx, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(gx, 2.0, rtol=0, atol=1e-7)
+    np.testing.assert_allclose(gy, -1.5, rtol=0, atol=1e-7)
