@@ -517,6 +517,55 @@ MUTATIONS = {
         ('            rg[3 * k + 0] = S->u[i];\n            rg[3 * k + 1] = S->v[i];\n            rg[3 * k + 2] = S->p[i];\n            S->rpos[i] = (k + 1) % P->n_avg;',
          '            rg[3 * k + 2] = S->p[i];\n            S->rpos[i] = (k + 1) % P->n_avg;'),
     ],
+    # ---- inlet signals' amplitudes and signs, records, window fill, length scales
+    'pulse_amplitude_half': [
+        ('*u += q[0] * cos(M_PI * (y - P->inlet_y0) / 12.0)',
+         '*u += 0.5 * q[0] * cos(M_PI * (y - P->inlet_y0) / 12.0)'),
+    ],
+    'vortex_G_u_sign': [
+        ('        *u = P->U + q[0] * yr / den;',
+         '        *u = P->U - q[0] * yr / den;'),
+    ],
+    'ramp_half': [
+        ('        *u = P->U * (t < q[0] ? t / q[0] : 1.0);',
+         '        *u = P->U * (t < q[0] ? 0.5 * t / q[0] : 1.0);'),
+    ],
+    'I_thr_q_full': [
+        ('    double q = 0.5 * P->rho0 * P->U * P->U;\n    return q * q',
+         '    double q = P->rho0 * P->U * P->U;\n    return q * q'),
+    ],
+    'n_active_before_spawn': [
+        ('    H->n_active = S->n;',
+         '    H->n_active = S->n - made;'),
+    ],
+    'n_delete_zero': [
+        ('    H->n_delete = ndel;',
+         '    H->n_delete = 0;'),
+    ],
+    'vortex_xr_sign': [
+        ('        double xr = P->U * (q[2] - t), yr = y - q[3];',
+         '        double xr = P->U * (t - q[2]), yr = y - q[3];'),
+    ],
+    'modes_H': [
+        ('sin((double)(k + 1) * M_PI * (y - P->inlet_y0) / P->inlet_h)',
+         'sin((double)(k + 1) * M_PI * (y - P->inlet_y0) / (2.0 * P->inlet_h))'),
+    ],
+    'ring_fill_p_zero': [
+        ('        rg[3 * k + 2] = S->p[i];\n    }\n    S->rpos[i] = 0;',
+         '        rg[3 * k + 2] = 0.0;\n    }\n    S->rpos[i] = 0;'),
+    ],
+    'ubar_from_u_at_fill': [
+        ('    S->pbar[i] = S->p[i];\n    S->J2[i] = 0.0;\n}',
+         '    S->pbar[i] = 0.0;\n    S->J2[i] = 0.0;\n}'),
+    ],
+    'edac_h_in_nu': [
+        ('    const double nu_edac = P->alpha * h * P->cs / 8.0;',
+         '    const double nu_edac = P->alpha * P->dx * P->cs / 8.0;'),
+    ],
+    'eh2_uses_dx': [
+        ('    const double eh2 = P->eta_reg * h * h;',
+         '    const double eh2 = P->eta_reg * P->dx * P->dx;'),
+    ],
 }
 
 # Mistakes with no observable effect: the forces of walls not counted in the drag are zero

@@ -472,6 +472,9 @@ def test_recycling_counts_and_conversions():
     # inlet count is conserved (each conversion spawns one), fluid count follows the flux
     assert np.count_nonzero(f["tag"] == INLET) == c.count(INLET)
     assert np.count_nonzero(f["tag"] == FLUID) == nf0 + sp - to
+    # each record's particle count is the count after that step's recycling
+    counts = n0 + np.cumsum([h["n_spawn"] - h["n_delete"] for h in hist])
+    assert [h["n_active"] for h in hist] == counts.tolist() and counts[-1] == o.n
     # mass flux history equals the mass of the converted particles per unit time
     m = c.params.rho0 * c.params.dx ** 2
     for h in hist:
@@ -728,6 +731,11 @@ def test_vortex_inlet_velocity_is_antisymmetric_about_the_centre_line():
     ymin = np.min(np.abs(y - yc))
     k = np.argmin(np.abs(y - yc))
     assert v[k] == pytest.approx(-G * xr / (xr * xr + ymin * ymin + core), rel=1e-12)
+    # the sense of rotation: with G > 0, u exceeds U above the centre line (u - U = G y_r / ...)
+    top = np.argmax(y - yc)
+    yr = y[top] - yc
+    assert G > 0 and yr > 0
+    assert u[top] - 1.0 == pytest.approx(G * yr / (xr * xr + yr * yr + core), rel=1e-12)
 
 
 def test_pulse_inlet_is_quiet_outside_its_window():
