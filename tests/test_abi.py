@@ -196,3 +196,32 @@ def test_product_fails_loudly_without_its_library(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert "raised:" in r.stdout and "build()" in r.stdout
+
+
+def test_binding_struct_layout_is_the_headers(tmp_path):
+    """The ctypes mirror of edac_params has the C header's size and field offsets (compiled
+    here with the host C compiler), and make_params fills every field from a case."""
+    import subprocess
+    fields = [f for f, _ in binding.Params._fields_]
+    src = tmp_path / "layout.c"
+    body = "\n".join(f'    printf("%s %zu\\n", "{f}", offsetof(edac_params, {f}));' for f in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "edac.h"\n'
+                   "int main(void) {\n"
+                   '    printf("sizeof %zu\\n", sizeof(edac_params));\n' + body + "\n    return 0;\n}\n")
+    exe = tmp_path / "layout"
+    inc = os.path.dirname(HEADER)
+    r = subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True,
+                                                        text=True).stdout.splitlines())
+    assert int(out["sizeof"]) == C.sizeof(binding.Params)
+    for f in fields:
+        assert int(out[f]) == getattr(binding.Params, f).offset, f
+    c = cases.channel()
+    p = binding.make_params(c.params, binding.EDAC_MIXED, 1234, 99, True, 0)
+    for f in ("x_min", "x_max", "y_min", "y_max", "dx", "hdx", "rho0", "U", "nu", "cs", "alpha",
+              "pb", "eta_reg", "gx", "gy", "dt", "periodic_x", "periodic_y", "use_pavg"):
+        assert getattr(p, f) == getattr(c.params, f), f
+    assert (p.precision, p.capacity, p.max_history, p.use_graphs) == (binding.EDAC_MIXED, 1234, 99, 1)
+    assert not p.cuda_stream
