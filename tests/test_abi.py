@@ -225,3 +225,52 @@ def test_binding_struct_layout_is_the_headers(tmp_path):
         assert getattr(p, f) == getattr(c.params, f), f
     assert (p.precision, p.capacity, p.max_history, p.use_graphs) == (binding.EDAC_MIXED, 1234, 99, 1)
     assert not p.cuda_stream
+
+
+def test_binding_constants_are_the_headers(tmp_path):
+    """Field ids, kernel ids, statuses, precisions, event kinds, peak kinds and the particle
+    tags of the binding and of the cases module are the header's values (compiled here)."""
+    import subprocess
+    names = (["EDAC_F_" + f.upper() for f in binding.FIELDS] + ["EDAC_NUM_FIELDS"]
+             + ["EDAC_K_" + k.upper() for k in binding.KERNELS]
+             + list(binding.STATUS.values())
+             + ["EDAC_FP64", "EDAC_MIXED", "EDAC_EVENT_DELETE", "EDAC_EVENT_TO_OUTLET",
+                "EDAC_EVENT_SPAWN", "EDAC_PEAK_FP32", "EDAC_PEAK_FP64", "EDAC_FLUID",
+                "EDAC_INLET", "EDAC_OUTLET", "EDAC_WALL", "EDAC_SLIPWALL",
+                "EDAC_OUTLET_HYBRID", "EDAC_OUTLET_DONOTHING", "EDAC_OUTLET_MOD_DONOTHING",
+                "EDAC_OUTLET_CHARACTERISTIC", "EDAC_OUTLET_MIRROR", "EDAC_INLET_MODES",
+                "EDAC_INLET_PULSE", "EDAC_INLET_RAMP", "EDAC_INLET_VORTEX"])
+    src = tmp_path / "consts.c"
+    body = "\n".join(f'    printf("%s %d\\n", "{n}", (int)({n}));' for n in names)
+    src.write_text('#include <stdio.h>\n#include "edac.h"\nint main(void) {\n' + body +
+                   "\n    return 0;\n}\n")
+    exe = tmp_path / "consts"
+    r = subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    v = {a: int(b) for a, b in (ln.split() for ln in subprocess.run(
+        [str(exe)], capture_output=True, text=True).stdout.splitlines())}
+    for i, f in enumerate(binding.FIELDS):
+        assert v["EDAC_F_" + f.upper()] == binding.FIELD_ID[f] == i, f
+    assert v["EDAC_NUM_FIELDS"] == len(binding.FIELDS)
+    for k, i in binding.KERNELS.items():
+        assert v["EDAC_K_" + k.upper()] == i, k
+    for code, name in binding.STATUS.items():
+        assert v[name] == code, name
+    assert (v["EDAC_FP64"], v["EDAC_MIXED"]) == (binding.EDAC_FP64, binding.EDAC_MIXED)
+    assert (v["EDAC_EVENT_DELETE"], v["EDAC_EVENT_TO_OUTLET"], v["EDAC_EVENT_SPAWN"]) == (
+        binding.EVENT_DELETE, binding.EVENT_TO_OUTLET, binding.EVENT_SPAWN)
+    assert (v["EDAC_PEAK_FP32"], v["EDAC_PEAK_FP64"]) == (binding.EDAC_PEAK_FP32, binding.EDAC_PEAK_FP64)
+    assert [v[n] for n in ("EDAC_FLUID", "EDAC_INLET", "EDAC_OUTLET", "EDAC_WALL",
+                           "EDAC_SLIPWALL")] == [cases.FLUID, cases.INLET, cases.OUTLET,
+                                                 cases.WALL, cases.SLIPWALL]
+    # the outlet kinds of the cases module (Params.outlet_kind) and of the physics driver
+    from paper_1907_04034_gb300 import validate
+    assert validate.OUTLETS == {"hybrid": v["EDAC_OUTLET_HYBRID"],
+                                "donothing": v["EDAC_OUTLET_DONOTHING"],
+                                "mod_donothing": v["EDAC_OUTLET_MOD_DONOTHING"],
+                                "characteristic": v["EDAC_OUTLET_CHARACTERISTIC"],
+                                "mirror": v["EDAC_OUTLET_MIRROR"]}
+    assert cases.Params(0.0, 1.0, 0.0, 1.0).outlet_kind == v["EDAC_OUTLET_HYBRID"]
+    assert [v[n] for n in ("EDAC_INLET_MODES", "EDAC_INLET_PULSE", "EDAC_INLET_RAMP",
+                           "EDAC_INLET_VORTEX")] == [0, 1, 2, 3]
