@@ -566,8 +566,59 @@ MUTATIONS = {
         ('    const double eh2 = P->eta_reg * h * h;',
          '    const double eh2 = P->eta_reg * P->dx * P->dx;'),
     ],
+    # ---- velocities each term takes, event order, stage lengths, more p~ and c_ij forms
+    'A_j_uses_u_i': [
+        ('            double Ajx = Aj * S->u[j], Ajy = Aj * S->v[j];',
+         '            double Ajx = Aj * S->u[i], Ajy = Aj * S->v[i];'),
+    ],
+    'div_uses_transport_velocity': [
+        ('            sp_rate += (S->m[j] * rhoi / rhoj) * c2 * (uij * gx + vij * gy)',
+         '            sp_rate += (S->m[j] * rhoi / rhoj) * c2 * ((S->ut[i] - S->ut[j]) * gx + (S->vt[i] - S->vt[j]) * gy)'),
+    ],
+    'visc_uses_transport_velocity': [
+        ('                sx += cij * (-ptil * gx + visc * uij);\n                sy += cij * (-ptil * gy + visc * vij);\n                continue;',
+         '                sx += cij * (-ptil * gx + visc * (S->ut[i] - S->u[j]));\n                sy += cij * (-ptil * gy + visc * (S->vt[i] - S->v[j]));\n                continue;'),
+    ],
+    'events_kinds_reordered': [
+        ('        if (k < nd) {\n            e[1] = 0; e[2] = del[k].id; e[3] = 0;',
+         '        if (k < nd) {\n            e[1] = 0; e[2] = del[nd - 1 - k].id; e[3] = 0;'),
+    ],
+    'mirror_outlet_v_from_u': [
+        ('        S->v[o] = fo[3 * t + 2];',
+         '        S->v[o] = fo[3 * t + 1];'),
+    ],
+    'inlet_stage_x_dt': [
+        ('            S->x[i] = S->x0[i] + tau * uin;\n',
+         '            S->x[i] = S->x0[i] + P->dt * uin;\n'),
+    ],
+    'ptil_pavg_of_j': [
+        ('double ptil = (rhoj * (S->p[i] - pavg) + rhoi * (S->p[j] - pavg)) / (rhoi + rhoj);',
+         'double ptil = (rhoj * (S->p[i] - pavg) + rhoi * (S->p[j])) / (rhoi + rhoj);'),
+    ],
+    'cij_vi_only': [
+        ('            double cij = Vi * Vi + Vj * Vj;',
+         '            double cij = 2.0 * Vi * Vi;'),
+    ],
+    'edac_diffusion_gdotr_abs': [
+        ('+ (cij / mi) * etile * (S->p[i] - S->p[j]) * gdotr / (r2 + eh2);',
+         '+ (cij / mi) * etile * (S->p[i] - S->p[j]) * fabs(gdotr) / (r2 + eh2);'),
+    ],
+    'wall_p_gravity_term': [
+        ('                pw = sp / sw;',
+         '                pw = sp / sw + P->gx;'),
+    ],
+    'outlet_ut_zero': [
+        ('        S->ut[o] = S->u[o];\n        S->vt[o] = S->v[o];\n    }\n    for (int o = 0; o < n; o++) {',
+         '        S->ut[o] = 0.0;\n        S->vt[o] = S->v[o];\n    }\n    for (int o = 0; o < n; o++) {'),
+    ],
+    'mass_in_abg': [
+        ('            S->abu[i] = -P->pb / mi * bx;\n            S->abv[i] = -P->pb / mi * by;',
+         '            S->abu[i] = -P->pb * bx;\n            S->abv[i] = -P->pb * by;'),
+    ],
 }
 
 # Mistakes with no observable effect: the forces of walls not counted in the drag are zero
-# by construction, so summing every wall into the force record changes nothing.
-EQUIVALENT = {"drag_all_walls"}
+# by construction, so summing every wall into the force record changes nothing; and a wall's
+# transport velocity is its ghost velocity, so the solid force's viscous term cannot tell them
+# apart.
+EQUIVALENT = {"drag_all_walls", "visc_uses_transport_velocity"}
